@@ -1,0 +1,270 @@
+"""Throughput of the two-fluid kinetic step (GLUPS = 1e9 r-node updates / s).
+
+Workload: Kolmogorov flow on 4096 x 4096 r-nodes, N_Q = 32 Q-nodes (6 x 6 grid
+masked to R = 3), Re 10, Wi 1, beta 0.2, forcing wavelength 64 nodes, FP32
+storage; synthetic seeded perturbation. One step = pull-stream, moments,
+collision and write-back of all 9 + 25 N_Q populations of every node.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank advances its own independent run (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_BYTES = 129e6
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="tfkt_clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.out,
+                stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.close()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(smax), "samples": len(sm),
+                "power_w_max": max(power), "reasons": sorted(reasons)}
+
+
+def oracle_sample(W, target_s: float = 12.0):
+    """Time the CPU oracle on a bounded sample of the workload: 256 x 256 r-nodes
+    with the same lattice parameters (forcing wavelength 64 nodes), N_Q = 32."""
+    from oracle import oracle as O
+    from paper_2201_10132_gb300.inputs import perturbation
+    n = 256
+    kp = W.k_periods * n // W.ny
+    cores = O.set_threads(os.cpu_count() or 1)
+    lat = O.map_params(n, n, W.q_side, W.q_radius, W.re, W.wi, W.beta, W.u0, kp, W.tau2)
+    o = O.Oracle(lat)
+    o.init(perturbation(n, n, W.seed, W.amp, W.u0), W.ic_mode)
+    t0 = time.perf_counter()
+    o.step(1)
+    t1 = time.perf_counter()
+    steps = max(1, int(target_s / max(t1 - t0, 1e-6)))
+    t1 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t1
+    return {"value": n * n * steps / dt / 1e9, "unit": "GLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"{n}x{n} r-nodes, N_Q={o.nq}, {steps} steps, FP64, same lattice "
+                      f"parameters as the workload, {dt:.1f} s"}
+
+
+def run_reference(args, W):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    per_step = []
+    total_nodes = 0
+    from oracle import oracle as O  # noqa: F401  (the oracle is the reference arm)
+    for k in range(args.warmup + args.steps):
+        r = oracle_sample(W, target_s=max(2.0, 60.0 / max(1, args.steps + args.warmup)))
+        if k >= args.warmup:
+            per_step.append(r)
+    value = sum(r["value"] for r in per_step) / len(per_step)
+    line = {"impl": "reference", "metric": "GLUPS (1e9 r-node updates/s), 4096^2 two-fluid step",
+            "value": value, "unit": "GLUPS", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": W.name, "sample": per_step[-1]["sample"]},
+            "cpu_baseline": {"value": value, "unit": "GLUPS", "cores": per_step[-1]["cores"],
+                             "kind": "oracle", "sample": per_step[-1]["sample"]},
+            "e2e": {"value": value, "unit": "GLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="kolmogorov-4096x4096-nq32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    from paper_2201_10132_gb300.inputs import WORKLOADS
+    W = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, W)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    cpu_base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu_base = oracle_sample(W)
+
+    import numpy as np
+    import torch
+    from paper_2201_10132_gb300 import tfkt
+    from paper_2201_10132_gb300.inputs import perturbation
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    p = tfkt.Params.from_workload(W, tfkt.FP32)
+    nodes = W.nx * W.ny
+    ws = torch.empty(tfkt.required_bytes(p), dtype=torch.uint8, device="cuda")
+    pert = torch.from_numpy(perturbation(W.nx, W.ny, W.seed + rank, W.amp, W.u0)).pin_memory()
+    stream = torch.cuda.Stream()
+    solver = tfkt.Solver(p, pert.numpy(), workspace=ws, stream=stream.cuda_stream)
+    info = solver.info
+    solver.step(args.warmup)
+    solver.sync()
+
+    kms = np.zeros(len(tfkt.KERNELS))
+    launches = np.zeros(len(tfkt.KERNELS), np.int64)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    solver.step_profiled(args.steps, kms, launches)
+    e1.record(stream)
+    e1.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    diag = solver.diagnostics()
+    assert all(math.isfinite(v) for v in diag.values()), diag
+    solver.close()
+
+    # end to end through the C-ABI with pinned host buffers: create from the host
+    # perturbation, per step a step and a diagnostics read-back, then the velocity
+    # and density fields back to the host
+    out_diag = torch.zeros(len(tfkt.DIAGS), dtype=torch.float64).pin_memory()
+    names = ["rho_s", "ux", "uy"]
+    host_f = torch.empty((len(names), W.ny, W.nx), dtype=torch.float64).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    s2 = tfkt.Solver(p, pert.numpy(), workspace=ws, stream=stream.cuda_stream)
+    for _ in range(args.steps):
+        s2.step(1)
+        s2.diagnostics_into(out_diag.numpy())
+    s2.moments_into(tfkt.field_mask(names), host_f.numpy())
+    s2.close()
+    t_e2e = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    h2d = pert.numel() * 8 / args.steps
+    d2h = (args.steps * out_diag.numel() * 8 + host_f.numel() * 8) / args.steps
+
+    if rank == 0:
+        hbm_peak, peak_kind = _peaks()
+        s = 4  # bytes per stored value (FP32)
+        npl, nm = 9 + 25 * info["nq"], info["nq"] + 6
+        step_bytes = nodes * (2 * npl + nm) * s        # read + write populations, read moments
+        mom_bytes = nodes * (npl + nm) * s             # read populations, write moments
+        step_ms = kms[1] / max(launches[1], 1)
+        mom_ms = kms[0] / max(launches[0], 1)
+        value = world * nodes * args.steps / (ms / 1e3) / 1e9
+        line = {
+            "metric": "GLUPS (1e9 r-node updates/s), 4096^2 two-fluid step",
+            "value": value, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": W.name, "nx": W.nx, "ny": W.ny, "nq": info["nq"],
+                       "re": W.re, "wi": W.wi, "beta": W.beta, "k_periods": W.k_periods,
+                       "storage": "fp32 deviations from rest",
+                       "l2": "inputs larger than L2 (populations 54 GB per buffer)",
+                       "parallelism": f"{world} independent runs"},
+            "roofline": {"bound": "hbm", "kernel": "step_kernel",
+                         "achieved": step_bytes / (step_ms / 1e3) / 1e9, "peak": hbm_peak,
+                         "unit": "GB/s", "frac": step_bytes / (step_ms / 1e3) / 1e9 / hbm_peak,
+                         "peak_kind": peak_kind, "traffic": None,
+                         "bytes_per_launch": step_bytes, "ms_per_launch": step_ms,
+                         "moments_kernel": {"ms_per_launch": mom_ms, "bytes_per_launch": mom_bytes,
+                                            "achieved": mom_bytes / (mom_ms / 1e3) / 1e9}},
+            "e2e": {"value": world * nodes * args.steps / t_e2e / 1e9, "unit": "GLUPS",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches.sum()),
+            "clocks": clocks,
+            "cpu_baseline": cpu_base,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

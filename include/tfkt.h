@@ -1,0 +1,178 @@
+/*
+ * tfkt — two-fluid kinetic step for dilute polymer solutions on one GB300 GPU.
+ *
+ * C-ABI of the library libtfkt.so. It advances the discrete two-fluid kinetic
+ * scheme of Singh, Subramanian & Ansumali, "Two-fluid kinetic theory for
+ * dilute polymer solutions" (arXiv 2201.10132):
+ *   - solvent: D2Q9 populations with the two-relaxation (tau1 / tau2)
+ *     quasi-equilibrium collision about the solvent velocity u_S and the
+ *     mixture velocity U (Sec. VI-A, Eq. dis_sol, Eq. dis_eq);
+ *   - polymer dumbbells: D4Q25 populations on the 4-D (r_x, r_y, Q_x, Q_y)
+ *     hyper-lattice (Sec. VI-B, Table dis_vel) with linear equilibria about
+ *     the imposed velocities of Eq. poly_imposed_vel (Eqs. feq_rq_space,
+ *     fstar_rq_space), bounce-back at the edge of the Q-disk (Sec. VI-D);
+ *   - time stepping by the trapezoidal rule made explicit through the
+ *     auxiliary population g = f - (dt/2) Omega (Sec. VI-C, Eqs. eq1, aux);
+ *   - the Kolmogorov body force of Sec. VII, a0 sin(2 pi k_periods y / ny).
+ * Lattice units: dt = dr = 1, c_s^2 = 1/3 on both lattices.
+ *
+ * Conventions shared by every call:
+ *   - All functions return tfkt_status; nothing throws across the ABI.
+ *   - A context owns one CUDA stream (the caller's, or the legacy default
+ *     stream when NULL is passed); all device work of the context is
+ *     enqueued on it. A context is not thread-safe.
+ *   - After a CUDA error the context is poisoned: every later call except
+ *     tfkt_destroy returns TFKT_ESTATE. tfkt_last_error() gives the text.
+ *   - Grids are periodic, node (x, y) at row-major index y * nx + x.
+ *   - Q-nodes: the S x S cell-centred grid Q = (i - (S-1)/2, j - (S-1)/2)
+ *     (Q lattice units), keeping |Q| <= R, numbered row-major over (j, i).
+ */
+#ifndef TFKT_H
+#define TFKT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TFKT_OK = 0,
+  TFKT_EINVAL = 1,  /* invalid argument; nothing was allocated or launched */
+  TFKT_ENOMEM = 2,  /* device allocation failed, or the workspace is too small */
+  TFKT_ECUDA = 3,   /* a CUDA call failed; the context is now poisoned */
+  TFKT_ENAN = 4,    /* diagnostics found a non-finite value; state kept */
+  TFKT_ESTATE = 5   /* the context was poisoned by an earlier CUDA error */
+} tfkt_status;
+
+typedef enum {
+  TFKT_FP64 = 0,    /* populations stored and updated in double */
+  TFKT_FP32 = 1     /* populations stored as float deviations from rest, updated in float */
+} tfkt_precision;
+
+/* Physical description of one Kolmogorov run (Sec. VII definitions:
+   Re = U0 l / nu, Wi = U0 lambda_H / l, beta = eta_s / (eta_s + eta_p),
+   l = ny / (2 pi k_periods), forcing amplitude nu U0 / l^2). */
+typedef struct {
+  int32_t nx, ny;        /* r-grid, periodic; 1 <= nx, ny */
+  int32_t q_side;        /* S: Q-grid side, 1 <= S <= 64 */
+  double q_radius;       /* R: disk radius in Q lattice units, > 0 */
+  double re, wi, beta;   /* Re > 0; Wi >= 0 (Wi = 0 only with beta = 1); 0 < beta <= 1 */
+  double u0;             /* laminar peak velocity, 0 < u0 <= 0.2 */
+  int32_t k_periods;     /* forcing periods across ny, >= 1 */
+  double tau2;           /* momentum relaxation time; <= 0 selects tau2 = tau1; else >= tau1 */
+  double ell;            /* Q-lattice spacing in r-lengths; <= 0 selects sqrt(2) */
+  int32_t ic_mode;       /* 0: start from rest; 1: start from the laminar profile */
+  int32_t precision;     /* tfkt_precision */
+} tfkt_params;
+
+/* Derived lattice parameters and layout of a context. */
+typedef struct {
+  int32_t nx, ny, nq, precision;
+  double tau1, tau2;     /* stress and momentum relaxation times */
+  double H, kappa;       /* spring constant; Q-drift rate kappa = 2 H tau2 */
+  double ell, psi_tot;   /* Q spacing; sum_q psi per r-node (psi counts beads) */
+  double sigma_q2;       /* variance of the initial Gaussian in Q (Q lattice units) */
+  double a0, kf;         /* forcing amplitude and wavenumber */
+  double nu, nu_s, eta_p, lambda_h;
+  int64_t step;          /* steps taken since tfkt_create */
+  size_t workspace_bytes;
+  size_t pitch;          /* elements per stored row (>= nx, multiple of 32) */
+  size_t bytes_per_node_step; /* algorithmic HBM bytes of one node update, fused model */
+} tfkt_info;
+
+typedef struct tfkt_ctx tfkt_ctx;
+
+/* Kernels timed by tfkt_step_profiled. */
+enum {
+  TFKT_K_MOMENTS = 0,  /* pull-read of all populations -> moment planes */
+  TFKT_K_STEP,         /* pull, collide and write of all populations */
+  TFKT_NKERNELS
+};
+
+/* Macroscopic fields for tfkt_moments (bit i of the mask selects field i;
+   fields are written in increasing bit order, ny * nx doubles each). */
+enum {
+  TFKT_F_RHO_S = 0,   /* solvent density */
+  TFKT_F_PSI_TOT,     /* sum_q psi */
+  TFKT_F_UX, TFKT_F_UY,          /* mixture velocity U of f (Sec. VI-C) */
+  TFKT_F_CXX, TFKT_F_CXY, TFKT_F_CYY,   /* conformation ell^2 sum psi QQ / psi_tot */
+  TFKT_F_THXX, TFKT_F_THXY, TFKT_F_THYY, /* stress (H ell^2 / 2) sum psi QQ */
+  TFKT_F_QRMS,        /* sqrt(<psi Q^2> / <psi>) in r-lengths (Sec. VII) */
+  TFKT_F_VORT,        /* d_x U_y - d_y U_x, central differences */
+  TFKT_NFIELDS
+};
+
+/* Global diagnostics of tfkt_diagnostics (FP64 sums over all r-nodes). */
+enum {
+  TFKT_D_MASS_S = 0, TFKT_D_MASS_P, TFKT_D_PX, TFKT_D_PY, TFKT_D_KE,
+  TFKT_D_ENSTROPHY, TFKT_D_QRMS_MEAN, TFKT_D_EY2, TFKT_NDIAG
+};
+
+/* Device bytes that tfkt_create needs for these parameters (two population
+   buffers, the moment fields, scratch). EINVAL for invalid parameters. */
+tfkt_status tfkt_required_bytes(const tfkt_params* p, size_t* bytes);
+
+/* Create a context and its initial state (Sec. VI-D initial condition with
+   Hookean dumbbells: psi is the discretely normalised Gaussian in Q, g = f^eq).
+   perturb: host array [2][ny][nx] of the initial velocity perturbation
+            (u'_x plane then u'_y plane), or NULL; copied during the call.
+   dev_workspace: device memory of at least tfkt_required_bytes bytes, owned
+            by the caller and kept alive until tfkt_destroy; or NULL, and the
+            library allocates (and frees in tfkt_destroy).
+   stream:  cudaStream_t for all work of the context, or NULL.
+   On success *out is the new context; on failure *out is NULL. */
+tfkt_status tfkt_create(const tfkt_params* p, const double* perturb, void* dev_workspace,
+                        size_t workspace_bytes, void* stream, tfkt_ctx** out);
+
+/* Advance n >= 0 time steps (stream, moments, collide). Asynchronous on the
+   context stream. */
+tfkt_status tfkt_step(tfkt_ctx* ctx, int64_t n);
+
+/* Same as tfkt_step, with CUDA events recorded on the context stream around
+   every kernel launch; synchronises at the end and adds the elapsed time of
+   each kernel kind, in milliseconds, to kernel_ms[TFKT_NKERNELS] (host) and
+   the launch counts to launches[TFKT_NKERNELS] (host, may be NULL). */
+tfkt_status tfkt_step_profiled(tfkt_ctx* ctx, int64_t n, double* kernel_ms, int64_t* launches);
+
+/* Macroscopic fields of the current state (see TFKT_F_*), as doubles.
+   dst: device pointer if dst_is_device, else host pointer; bytes is its size
+   and must hold popcount(field_mask) * ny * nx doubles. Synchronises the
+   stream when dst is host memory. */
+tfkt_status tfkt_moments(tfkt_ctx* ctx, uint32_t field_mask, double* dst, size_t bytes,
+                         int dst_is_device);
+
+/* psi(x, q) of the current state as doubles, layout [ny][nx][nq]. */
+tfkt_status tfkt_psi(tfkt_ctx* ctx, double* dst, size_t bytes, int dst_is_device);
+
+/* Global diagnostics into host out[TFKT_NDIAG]; synchronises. TFKT_ENAN if
+   any is not finite. */
+tfkt_status tfkt_diagnostics(tfkt_ctx* ctx, double* out);
+
+/* The stored (post-collision, not yet streamed) populations g' as doubles in
+   host memory, layout [plane][ny][nx]: planes 0..8 solvent (tfkt_lattice
+   order), then plane 9 + 25 q + i for the polymer. Synchronises. */
+tfkt_status tfkt_populations(tfkt_ctx* ctx, double* host_dst, size_t bytes);
+
+tfkt_status tfkt_get_info(const tfkt_ctx* ctx, tfkt_info* info);
+
+/* Velocity ordering of the library: c9[9][2] (D2Q9), c25[25][4] (D4Q25 on
+   r_x, r_y, Q_x, Q_y). Either pointer may be NULL. */
+tfkt_status tfkt_lattice(int32_t* c9, int32_t* c25);
+
+/* Wait for all work of the context. */
+tfkt_status tfkt_sync(tfkt_ctx* ctx);
+
+/* Release the context (and the workspace if the library allocated it).
+   Synchronises first. NULL is accepted. */
+tfkt_status tfkt_destroy(tfkt_ctx* ctx);
+
+const char* tfkt_status_string(tfkt_status s);
+/* Text of the last error seen by this thread ("" if none). */
+const char* tfkt_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

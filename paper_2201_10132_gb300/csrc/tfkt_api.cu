@@ -1,0 +1,633 @@
+// Host side of libtfkt: parameter mapping, lattice tables, workspace layout
+// and the extern "C" entry points declared in include/tfkt.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "tfkt_internal.cuh"
+
+namespace tfkt {
+namespace {
+
+thread_local std::string g_last_error;
+
+tfkt_status fail(tfkt_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+tfkt_status cuda_fail(Ctx* c, cudaError_t e, const char* where) {
+  if (c) c->poisoned = true;
+  return fail(TFKT_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define TFKT_CUDA(ctx, call)                                     \
+  do {                                                           \
+    cudaError_t e_ = (call);                                     \
+    if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);   \
+  } while (0)
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Physical -> lattice parameters (Sec. VII definitions Re = U0 l / nu,
+// Wi = U0 lambda_H / l, beta = eta_s / (eta_s + eta_p), F = eta U0 / l^2):
+// nu_s = c_s^2 tau1 (trapezoidal scheme), lambda_H = zeta / (4 H) with
+// zeta = m_B / tau2 (Appendix A), Q-drift 2 H / zeta = kappa, Q spacing
+// ell = sqrt(2) from the Q-diffusivity 2 kT / zeta of Eq. Smoluchowski_new11,
+// and psi_tot from eta_p = (H ell^2 / 2) psi_tot sigma_Q^2 lambda_H
+// (psi counts beads).
+tfkt_status map_params(const tfkt_params* p, Lattice* L) {
+  if (!p) return fail(TFKT_EINVAL, "params is NULL");
+  if (p->nx < 1 || p->ny < 1) return fail(TFKT_EINVAL, "nx and ny must be >= 1");
+  if (p->q_side < 1 || p->q_side > 64) return fail(TFKT_EINVAL, "q_side must be in [1, 64]");
+  if (!(p->q_radius > 0)) return fail(TFKT_EINVAL, "q_radius must be > 0");
+  if (!(p->re > 0)) return fail(TFKT_EINVAL, "re must be > 0");
+  if (!(p->beta > 0) || p->beta > 1) return fail(TFKT_EINVAL, "beta must be in (0, 1]");
+  if (!(p->u0 > 0) || p->u0 > 0.2) return fail(TFKT_EINVAL, "u0 must be in (0, 0.2]");
+  if (p->k_periods < 1) return fail(TFKT_EINVAL, "k_periods must be >= 1");
+  if (!(p->wi >= 0)) return fail(TFKT_EINVAL, "wi must be >= 0");
+  if (p->wi == 0 && p->beta < 1) return fail(TFKT_EINVAL, "wi = 0 needs beta = 1 (no polymer)");
+  if (p->precision != TFKT_FP64 && p->precision != TFKT_FP32)
+    return fail(TFKT_EINVAL, "unknown precision");
+  if (p->ic_mode != 0 && p->ic_mode != 1) return fail(TFKT_EINVAL, "ic_mode must be 0 or 1");
+  Lattice l;
+  l.nx = p->nx;
+  l.ny = p->ny;
+  l.S = p->q_side;
+  l.q_radius = p->q_radius;
+  l.ic_mode = p->ic_mode;
+  l.precision = p->precision;
+  const double kf = 2.0 * M_PI * p->k_periods / p->ny;
+  const double len = 1.0 / kf;
+  l.kf = kf;
+  l.u0 = p->u0;
+  l.nu = p->u0 * len / p->re;
+  l.nu_s = p->beta * l.nu;
+  l.tau1 = 3.0 * l.nu_s;
+  l.tau2 = p->tau2 > 0 ? p->tau2 : l.tau1;
+  if (l.tau2 < l.tau1) return fail(TFKT_EINVAL, "tau2 must be >= tau1 (tau1 = 3 beta nu)");
+  l.ell = p->ell > 0 ? p->ell : std::sqrt(2.0);
+  l.eta_p = (1.0 - p->beta) * l.nu;
+  l.a0 = l.nu * p->u0 * kf * kf;
+  if (p->wi > 0) {
+    l.lambda_h = p->wi * len / p->u0;
+    l.H = 1.0 / (4.0 * l.lambda_h * l.tau2);
+    l.kappa = 2.0 * l.H * l.tau2;
+    l.sigma_q2 = l.tau2 / (3.0 * l.kappa);
+    l.psi_tot = l.eta_p / (0.5 * l.H * l.ell * l.ell * l.sigma_q2 * l.lambda_h);
+  } else {
+    l.lambda_h = 0;
+    l.H = 0;
+    l.kappa = 0;
+    l.sigma_q2 = 1.0;
+    l.psi_tot = 0;
+  }
+  // Q-disk nodes
+  int nq = 0;
+  const double R2 = p->q_radius * p->q_radius + 1e-9;
+  for (int j = 0; j < l.S; ++j)
+    for (int i = 0; i < l.S; ++i) {
+      const double qx = i - 0.5 * (l.S - 1), qy = j - 0.5 * (l.S - 1);
+      if (qx * qx + qy * qy <= R2) ++nq;
+    }
+  if (nq < 1) return fail(TFKT_EINVAL, "the Q-disk holds no node");
+  l.nq = nq;
+  l.pitch = align_up((size_t)l.nx, 32);
+  l.plane = (size_t)l.ny * l.pitch;
+  l.npl = 9 + 25 * nq;
+  l.nm = nq + M_NSCALAR;
+  *L = l;
+  return TFKT_OK;
+}
+
+size_t real_size(const Lattice& L) { return L.precision == TFKT_FP64 ? 8 : 4; }
+
+int diag_blocks_for(const Lattice& L) {
+  const size_t N = (size_t)L.nx * L.ny;
+  const size_t want = (N + DIAG_THREADS - 1) / DIAG_THREADS;
+  return (int)(want < 608 ? want : 608);
+}
+
+// Workspace layout; returns the total size.
+size_t layout(const Lattice& L, Workspace* w) {
+  const size_t sz = real_size(L), A = 256;
+  size_t o = 0;
+  const size_t pop = (size_t)L.npl * L.plane * sz;
+  w->off_pop[0] = o;
+  o = align_up(o + pop, A);
+  w->off_pop[1] = o;
+  o = align_up(o + pop, A);
+  w->off_M = o;
+  o = align_up(o + (size_t)L.nm * L.plane * sz, A);
+  w->off_U = o;
+  o = align_up(o + 2 * L.plane * sz, A);
+  w->off_tab = o;
+  const size_t tab = (3 * (size_t)L.nq + 25 * (size_t)L.nq + 2 * (size_t)L.ny) * sz +
+                     25 * (size_t)L.nq * sizeof(int) + 8 * A;
+  o = align_up(o + tab, A);
+  w->off_part = o;
+  o = align_up(o + (size_t)diag_blocks_for(L) * TFKT_NDIAG * sizeof(double), A);
+  w->off_diag = o;
+  o = align_up(o + TFKT_NDIAG * sizeof(double), A);
+  return o;
+}
+
+struct HostTables {
+  std::vector<double> qx, qy, psi0, delta, arow, urow;
+  std::vector<int> pull;
+};
+
+int opposite25(int i) {
+  const V4 c = c25(i);
+  for (int j = 0; j < 25; ++j) {
+    const V4 d = c25(j);
+    if (d.rx == -c.rx && d.ry == -c.ry && d.qx == -c.qx && d.qy == -c.qy) return j;
+  }
+  return -1;
+}
+
+// Q-nodes (cell-centred S x S grid inside the disk |Q| <= R, Sec. VI-D),
+// the initial Gaussian psi0(q) (Hookean equilibrium, normalised on the
+// masked grid to psi_tot), the pull table with bounce-back at the disk edge,
+// the forcing a(y) = a0 sin(kf y) (Sec. VII) and the initial base flow.
+HostTables build_tables(const Lattice& L) {
+  HostTables t;
+  std::vector<int> qmap((size_t)L.S * L.S, -1), gi, gj;
+  const double R2 = L.q_radius * L.q_radius + 1e-9;
+  for (int j = 0; j < L.S; ++j)
+    for (int i = 0; i < L.S; ++i) {
+      const double qx = i - 0.5 * (L.S - 1), qy = j - 0.5 * (L.S - 1);
+      if (qx * qx + qy * qy <= R2) {
+        qmap[(size_t)j * L.S + i] = (int)t.qx.size();
+        t.qx.push_back(qx);
+        t.qy.push_back(qy);
+        gi.push_back(i);
+        gj.push_back(j);
+      }
+    }
+  double gsum = 0;
+  for (int q = 0; q < L.nq; ++q) {
+    const double g = std::exp(-(t.qx[q] * t.qx[q] + t.qy[q] * t.qy[q]) / (2.0 * L.sigma_q2));
+    t.psi0.push_back(g);
+    gsum += g;
+  }
+  for (double& v : t.psi0) v = gsum > 0 ? L.psi_tot * v / gsum : 0.0;
+  t.pull.resize((size_t)L.nq * 25);
+  t.delta.resize((size_t)L.nq * 25);
+  for (int q = 0; q < L.nq; ++q)
+    for (int i = 0; i < 25; ++i) {
+      const V4 c = c25(i);
+      const int si = gi[q] - c.qx, sj = gj[q] - c.qy;
+      const int sq = (si >= 0 && si < L.S && sj >= 0 && sj < L.S) ? qmap[(size_t)sj * L.S + si] : -1;
+      if (sq >= 0) {
+        t.pull[(size_t)q * 25 + i] = 9 + 25 * sq + i;
+        t.delta[(size_t)q * 25 + i] = w25(i) * (t.psi0[sq] - t.psi0[q]);
+      } else {
+        t.pull[(size_t)q * 25 + i] = ~(9 + 25 * q + opposite25(i));
+        t.delta[(size_t)q * 25 + i] = 0.0;
+      }
+    }
+  for (int y = 0; y < L.ny; ++y) {
+    t.arow.push_back(L.a0 * std::sin(L.kf * y));
+    t.urow.push_back(L.ic_mode == 1 ? L.u0 * std::sin(L.kf * y) : 0.0);
+  }
+  return t;
+}
+
+template <typename real>
+KernelArgs<real> make_args(const Ctx* c, const HostTables* ht = nullptr) {
+  const Lattice& L = c->L;
+  char* base = (char*)c->ws.base;
+  KernelArgs<real> a{};
+  a.src = (const real*)(base + c->ws.off_pop[c->cur]);
+  a.dst = (real*)(base + c->ws.off_pop[c->cur ^ 1]);
+  a.M = (real*)(base + c->ws.off_M);
+  a.U = (real*)(base + c->ws.off_U);
+  a.perturb = nullptr;
+  a.nx = L.nx;
+  a.ny = L.ny;
+  a.nq = L.nq;
+  a.pitch = L.pitch;
+  a.plane = L.plane;
+  const double b = 1.0 / (2.0 * L.tau1 + 1.0);
+  a.tau2 = (real)L.tau2;
+  a.c2 = (real)(2.0 * L.tau2);
+  a.inv_c2p1 = (real)(1.0 / (2.0 * L.tau2 + 1.0));
+  a.om2b = (real)(1.0 - 2.0 * b);
+  a.tb = (real)(2.0 * b);
+  a.omb = (real)(1.0 - b);
+  a.r = (real)(L.tau1 / L.tau2);
+  a.omr = (real)(1.0 - L.tau1 / L.tau2);
+  a.kappa = (real)L.kappa;
+  a.hl2h = (real)(0.5 * L.H * L.ell * L.ell);
+  a.rho0 = (real)(1.0 + L.psi_tot);
+  a.psi_tot0 = (real)L.psi_tot;
+  a.l2 = (real)(L.ell * L.ell);
+  a.H = (real)L.H;
+  // tables
+  char* tb = base + c->ws.off_tab;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    char* p = tb + o;
+    o = align_up(o + bytes, 256);
+    return p;
+  };
+  const size_t nq = L.nq;
+  a.tab.qx = (const real*)take(nq * sizeof(real));
+  a.tab.qy = (const real*)take(nq * sizeof(real));
+  a.tab.psi0 = (const real*)take(nq * sizeof(real));
+  a.tab.pull = (const int*)take(nq * 25 * sizeof(int));
+  a.tab.delta = (const real*)take(nq * 25 * sizeof(real));
+  a.tab.arow = (const real*)take((size_t)L.ny * sizeof(real));
+  a.tab.urow = (const real*)take((size_t)L.ny * sizeof(real));
+  (void)ht;
+  return a;
+}
+
+template <typename real>
+tfkt_status upload_tables(Ctx* c, const HostTables& t) {
+  KernelArgs<real> a = make_args<real>(c);
+  auto put = [&](const void* dptr, const std::vector<double>& v) -> cudaError_t {
+    std::vector<real> h(v.begin(), v.end());
+    return cudaMemcpy((void*)dptr, h.data(), h.size() * sizeof(real), cudaMemcpyHostToDevice);
+  };
+  TFKT_CUDA(c, put(a.tab.qx, t.qx));
+  TFKT_CUDA(c, put(a.tab.qy, t.qy));
+  TFKT_CUDA(c, put(a.tab.psi0, t.psi0));
+  TFKT_CUDA(c, cudaMemcpy((void*)a.tab.pull, t.pull.data(), t.pull.size() * sizeof(int),
+                          cudaMemcpyHostToDevice));
+  TFKT_CUDA(c, put(a.tab.delta, t.delta));
+  TFKT_CUDA(c, put(a.tab.arow, t.arow));
+  TFKT_CUDA(c, put(a.tab.urow, t.urow));
+  return TFKT_OK;
+}
+
+template <typename real>
+tfkt_status init_state(Ctx* c, const double* perturb) {
+  const Lattice& L = c->L;
+  KernelArgs<real> a = make_args<real>(c);
+  // The buffer that the first step writes is free now: stage the perturbation there.
+  double* dpert = nullptr;
+  if (perturb) {
+    dpert = (double*)((char*)c->ws.base + c->ws.off_pop[1]);
+    TFKT_CUDA(c, cudaMemcpyAsync(dpert, perturb, sizeof(double) * 2 * (size_t)L.nx * L.ny,
+                                 cudaMemcpyHostToDevice, c->stream));
+  }
+  a.perturb = dpert;
+  a.dst = (real*)((char*)c->ws.base + c->ws.off_pop[0]);
+  TFKT_CUDA(c, launch_init<real>(a, c->stream));
+  c->cur = 0;
+  KernelArgs<real> m = make_args<real>(c);
+  TFKT_CUDA(c, launch_moments<real>(m, c->stream));
+  c->m_valid = true;
+  TFKT_CUDA(c, cudaStreamSynchronize(c->stream));
+  return TFKT_OK;
+}
+
+template <typename real>
+tfkt_status ensure_moments(Ctx* c) {
+  if (c->m_valid) return TFKT_OK;
+  KernelArgs<real> a = make_args<real>(c);
+  TFKT_CUDA(c, launch_moments<real>(a, c->stream));
+  c->m_valid = true;
+  return TFKT_OK;
+}
+
+template <typename real>
+tfkt_status do_step(Ctx* c, int64_t n) {
+  for (int64_t k = 0; k < n; ++k) {
+    tfkt_status s = ensure_moments<real>(c);
+    if (s != TFKT_OK) return s;
+    KernelArgs<real> a = make_args<real>(c);
+    TFKT_CUDA(c, launch_step<real>(a, c->stream));
+    c->cur ^= 1;
+    c->m_valid = false;
+    ++c->step;
+  }
+  return TFKT_OK;
+}
+
+// tfkt_step with an event pair around each launch (profiling only).
+template <typename real>
+tfkt_status do_step_profiled(Ctx* c, int64_t n, double* ms, int64_t* launches) {
+  cudaEvent_t ev[2 * 2];
+  for (auto& e : ev) TFKT_CUDA(c, cudaEventCreate(&e));
+  struct Guard {
+    cudaEvent_t* e;
+    ~Guard() {
+      for (int k = 0; k < 4; ++k) cudaEventDestroy(e[k]);
+    }
+  } guard{ev};
+  double acc[TFKT_NKERNELS] = {0, 0};
+  int64_t cnt[TFKT_NKERNELS] = {0, 0};
+  auto timed = [&](int kind, auto&& launch) -> tfkt_status {
+    TFKT_CUDA(c, cudaEventRecord(ev[2 * kind], c->stream));
+    TFKT_CUDA(c, launch());
+    TFKT_CUDA(c, cudaEventRecord(ev[2 * kind + 1], c->stream));
+    TFKT_CUDA(c, cudaEventSynchronize(ev[2 * kind + 1]));
+    float t = 0;
+    TFKT_CUDA(c, cudaEventElapsedTime(&t, ev[2 * kind], ev[2 * kind + 1]));
+    acc[kind] += t;
+    ++cnt[kind];
+    return TFKT_OK;
+  };
+  for (int64_t k = 0; k < n; ++k) {
+    if (!c->m_valid) {
+      KernelArgs<real> a = make_args<real>(c);
+      tfkt_status s = timed(TFKT_K_MOMENTS, [&] { return launch_moments<real>(a, c->stream); });
+      if (s != TFKT_OK) return s;
+      c->m_valid = true;
+    }
+    KernelArgs<real> a = make_args<real>(c);
+    tfkt_status s = timed(TFKT_K_STEP, [&] { return launch_step<real>(a, c->stream); });
+    if (s != TFKT_OK) return s;
+    c->cur ^= 1;
+    c->m_valid = false;
+    ++c->step;
+  }
+  for (int j = 0; j < TFKT_NKERNELS; ++j) {
+    ms[j] += acc[j];
+    if (launches) launches[j] += cnt[j];
+  }
+  return TFKT_OK;
+}
+
+template <typename real>
+tfkt_status do_fields(Ctx* c, uint32_t mask, double* dst, int dst_is_device) {
+  const Lattice& L = c->L;
+  tfkt_status s = ensure_moments<real>(c);
+  if (s != TFKT_OK) return s;
+  KernelArgs<real> a = make_args<real>(c);
+  TFKT_CUDA(c, launch_velocity<real>(a, c->stream));
+  const size_t nf = (size_t)__builtin_popcount(mask);
+  const size_t bytes = nf * (size_t)L.nx * L.ny * sizeof(double);
+  // Host destination: stage in the population buffer that the next step overwrites.
+  double* out = dst_is_device ? dst : (double*)a.dst;
+  TFKT_CUDA(c, launch_fields<real>(a, mask, out, c->stream));
+  if (!dst_is_device) {
+    TFKT_CUDA(c, cudaMemcpyAsync(dst, out, bytes, cudaMemcpyDeviceToHost, c->stream));
+    TFKT_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
+  return TFKT_OK;
+}
+
+template <typename real>
+tfkt_status do_psi(Ctx* c, double* dst, int dst_is_device) {
+  const Lattice& L = c->L;
+  tfkt_status s = ensure_moments<real>(c);
+  if (s != TFKT_OK) return s;
+  KernelArgs<real> a = make_args<real>(c);
+  const size_t bytes = (size_t)L.nq * L.nx * L.ny * sizeof(double);
+  double* out = dst_is_device ? dst : (double*)a.dst;
+  TFKT_CUDA(c, launch_psi<real>(a, out, c->stream));
+  if (!dst_is_device) {
+    TFKT_CUDA(c, cudaMemcpyAsync(dst, out, bytes, cudaMemcpyDeviceToHost, c->stream));
+    TFKT_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
+  return TFKT_OK;
+}
+
+template <typename real>
+tfkt_status do_populations(Ctx* c, double* host) {
+  const Lattice& L = c->L;
+  KernelArgs<real> a = make_args<real>(c);
+  const size_t N = (size_t)L.nx * L.ny;
+  double* tmp = nullptr;
+  TFKT_CUDA(c, cudaMallocAsync((void**)&tmp, (size_t)L.npl * N * sizeof(double), c->stream));
+  cudaError_t e = launch_populations<real>(a, tmp, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(host, tmp, (size_t)L.npl * N * sizeof(double), cudaMemcpyDeviceToHost,
+                        c->stream);
+  cudaError_t f = cudaFreeAsync(tmp, c->stream);
+  if (e == cudaSuccess) e = f;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "populations");
+  return TFKT_OK;
+}
+
+template <typename real>
+tfkt_status do_diag(Ctx* c, double* out) {
+  tfkt_status s = ensure_moments<real>(c);
+  if (s != TFKT_OK) return s;
+  KernelArgs<real> a = make_args<real>(c);
+  TFKT_CUDA(c, launch_velocity<real>(a, c->stream));
+  double* part = (double*)((char*)c->ws.base + c->ws.off_part);
+  double* dout = (double*)((char*)c->ws.base + c->ws.off_diag);
+  TFKT_CUDA(c, launch_diag<real>(a, part, c->diag_blocks, dout, c->stream));
+  TFKT_CUDA(c, cudaMemcpyAsync(out, dout, TFKT_NDIAG * sizeof(double), cudaMemcpyDeviceToHost,
+                               c->stream));
+  TFKT_CUDA(c, cudaStreamSynchronize(c->stream));
+  for (int j = 0; j < TFKT_NDIAG; ++j)
+    if (!std::isfinite(out[j])) return fail(TFKT_ENAN, "non-finite diagnostic");
+  return TFKT_OK;
+}
+
+#define DISPATCH(c, fn, ...) \
+  ((c)->L.precision == TFKT_FP64 ? fn<double>(__VA_ARGS__) : fn<float>(__VA_ARGS__))
+
+tfkt_status check_ctx(const Ctx* c) {
+  if (!c) return fail(TFKT_EINVAL, "context is NULL");
+  if (c->poisoned) return fail(TFKT_ESTATE, "context poisoned by an earlier CUDA error");
+  return TFKT_OK;
+}
+
+}  // namespace
+}  // namespace tfkt
+
+using namespace tfkt;
+
+struct tfkt_ctx : public Ctx {};
+
+extern "C" {
+
+tfkt_status tfkt_required_bytes(const tfkt_params* p, size_t* bytes) {
+  if (!bytes) return fail(TFKT_EINVAL, "bytes is NULL");
+  Lattice L;
+  tfkt_status s = map_params(p, &L);
+  if (s != TFKT_OK) return s;
+  Workspace w;
+  *bytes = layout(L, &w);
+  return TFKT_OK;
+}
+
+tfkt_status tfkt_create(const tfkt_params* p, const double* perturb, void* dev_workspace,
+                        size_t workspace_bytes, void* stream, tfkt_ctx** out) {
+  if (!out) return fail(TFKT_EINVAL, "out is NULL");
+  *out = nullptr;
+  Lattice L;
+  tfkt_status s = map_params(p, &L);
+  if (s != TFKT_OK) return s;
+  tfkt_ctx* c = new (std::nothrow) tfkt_ctx();
+  if (!c) return fail(TFKT_ENOMEM, "host allocation failed");
+  c->L = L;
+  c->stream = (cudaStream_t)stream;
+  const size_t need = layout(L, &c->ws);
+  c->diag_blocks = diag_blocks_for(L);
+  if (dev_workspace) {
+    if (workspace_bytes < need) {
+      delete c;
+      return fail(TFKT_ENOMEM, "workspace too small: need " + std::to_string(need) + " bytes");
+    }
+    if (((uintptr_t)dev_workspace) % 256 != 0) {
+      delete c;
+      return fail(TFKT_EINVAL, "workspace must be 256-byte aligned");
+    }
+    c->ws.base = dev_workspace;
+    c->ws.owned = false;
+  } else {
+    cudaError_t e = cudaMalloc(&c->ws.base, need);
+    if (e != cudaSuccess) {
+      delete c;
+      cudaGetLastError();
+      return fail(TFKT_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    c->ws.owned = true;
+  }
+  c->ws.bytes = need;
+  HostTables t = build_tables(L);
+  s = L.precision == TFKT_FP64 ? upload_tables<double>(c, t) : upload_tables<float>(c, t);
+  if (s == TFKT_OK) s = DISPATCH(c, init_state, c, perturb);
+  if (s != TFKT_OK) {
+    if (c->ws.owned) cudaFree(c->ws.base);
+    delete c;
+    return s;
+  }
+  *out = c;
+  return TFKT_OK;
+}
+
+tfkt_status tfkt_step(tfkt_ctx* c, int64_t n) {
+  tfkt_status s = check_ctx(c);
+  if (s != TFKT_OK) return s;
+  if (n < 0) return fail(TFKT_EINVAL, "n must be >= 0");
+  return DISPATCH(c, do_step, c, n);
+}
+
+tfkt_status tfkt_step_profiled(tfkt_ctx* c, int64_t n, double* kernel_ms, int64_t* launches) {
+  tfkt_status s = check_ctx(c);
+  if (s != TFKT_OK) return s;
+  if (n < 0 || !kernel_ms) return fail(TFKT_EINVAL, "n must be >= 0 and kernel_ms non-NULL");
+  return DISPATCH(c, do_step_profiled, c, n, kernel_ms, launches);
+}
+
+tfkt_status tfkt_moments(tfkt_ctx* c, uint32_t mask, double* dst, size_t bytes, int dst_is_device) {
+  tfkt_status s = check_ctx(c);
+  if (s != TFKT_OK) return s;
+  if (!dst) return fail(TFKT_EINVAL, "dst is NULL");
+  if (mask == 0 || (mask >> TFKT_NFIELDS) != 0) return fail(TFKT_EINVAL, "bad field mask");
+  const size_t need = (size_t)__builtin_popcount(mask) * c->L.nx * c->L.ny * sizeof(double);
+  if (bytes < need) return fail(TFKT_EINVAL, "dst too small");
+  return DISPATCH(c, do_fields, c, mask, dst, dst_is_device);
+}
+
+tfkt_status tfkt_psi(tfkt_ctx* c, double* dst, size_t bytes, int dst_is_device) {
+  tfkt_status s = check_ctx(c);
+  if (s != TFKT_OK) return s;
+  if (!dst) return fail(TFKT_EINVAL, "dst is NULL");
+  if (bytes < (size_t)c->L.nq * c->L.nx * c->L.ny * sizeof(double))
+    return fail(TFKT_EINVAL, "dst too small");
+  return DISPATCH(c, do_psi, c, dst, dst_is_device);
+}
+
+tfkt_status tfkt_diagnostics(tfkt_ctx* c, double* out) {
+  tfkt_status s = check_ctx(c);
+  if (s != TFKT_OK) return s;
+  if (!out) return fail(TFKT_EINVAL, "out is NULL");
+  return DISPATCH(c, do_diag, c, out);
+}
+
+tfkt_status tfkt_populations(tfkt_ctx* c, double* host_dst, size_t bytes) {
+  tfkt_status s = check_ctx(c);
+  if (s != TFKT_OK) return s;
+  if (!host_dst) return fail(TFKT_EINVAL, "dst is NULL");
+  if (bytes < (size_t)c->L.npl * c->L.nx * c->L.ny * sizeof(double))
+    return fail(TFKT_EINVAL, "dst too small");
+  return DISPATCH(c, do_populations, c, host_dst);
+}
+
+tfkt_status tfkt_get_info(const tfkt_ctx* c, tfkt_info* info) {
+  if (!c || !info) return fail(TFKT_EINVAL, "NULL argument");
+  const Lattice& L = c->L;
+  tfkt_info i{};
+  i.nx = L.nx;
+  i.ny = L.ny;
+  i.nq = L.nq;
+  i.precision = L.precision;
+  i.tau1 = L.tau1;
+  i.tau2 = L.tau2;
+  i.H = L.H;
+  i.kappa = L.kappa;
+  i.ell = L.ell;
+  i.psi_tot = L.psi_tot;
+  i.sigma_q2 = L.sigma_q2;
+  i.a0 = L.a0;
+  i.kf = L.kf;
+  i.nu = L.nu;
+  i.nu_s = L.nu_s;
+  i.eta_p = L.eta_p;
+  i.lambda_h = L.lambda_h;
+  i.step = c->step;
+  i.workspace_bytes = c->ws.bytes;
+  i.pitch = L.pitch;
+  // each population read once and written once, each moment plane read and written once
+  i.bytes_per_node_step = (size_t)L.npl * 2 * real_size(L) + (size_t)L.nm * 2 * real_size(L);
+  *info = i;
+  return TFKT_OK;
+}
+
+tfkt_status tfkt_lattice(int32_t* c9, int32_t* c25v) {
+  if (c9)
+    for (int i = 0; i < 9; ++i) {
+      c9[2 * i] = c9x(i);
+      c9[2 * i + 1] = c9y(i);
+    }
+  if (c25v)
+    for (int i = 0; i < 25; ++i) {
+      const V4 c = c25(i);
+      c25v[4 * i] = c.rx;
+      c25v[4 * i + 1] = c.ry;
+      c25v[4 * i + 2] = c.qx;
+      c25v[4 * i + 3] = c.qy;
+    }
+  return TFKT_OK;
+}
+
+tfkt_status tfkt_sync(tfkt_ctx* c) {
+  tfkt_status s = check_ctx(c);
+  if (s != TFKT_OK) return s;
+  TFKT_CUDA(c, cudaStreamSynchronize(c->stream));
+  return TFKT_OK;
+}
+
+tfkt_status tfkt_destroy(tfkt_ctx* c) {
+  if (!c) return TFKT_OK;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (c->ws.owned && c->ws.base) {
+    cudaError_t f = cudaFree(c->ws.base);
+    if (e == cudaSuccess) e = f;
+  }
+  delete c;
+  if (e != cudaSuccess) return fail(TFKT_ECUDA, std::string("destroy: ") + cudaGetErrorString(e));
+  return TFKT_OK;
+}
+
+const char* tfkt_status_string(tfkt_status s) {
+  switch (s) {
+    case TFKT_OK: return "ok";
+    case TFKT_EINVAL: return "invalid argument";
+    case TFKT_ENOMEM: return "out of device memory";
+    case TFKT_ECUDA: return "CUDA error";
+    case TFKT_ENAN: return "non-finite value";
+    case TFKT_ESTATE: return "context poisoned";
+  }
+  return "unknown status";
+}
+
+const char* tfkt_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

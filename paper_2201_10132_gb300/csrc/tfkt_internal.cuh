@@ -1,0 +1,147 @@
+// Internal declarations of libtfkt: lattice tables, context layout, kernel
+// arguments and launchers. Not part of the C-ABI (include/tfkt.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include "tfkt.h"
+
+namespace tfkt {
+
+// ---------------------------------------------------------------- lattices
+// D2Q9 (Sec. VI-A): rest, the four axis velocities, the four diagonals.
+// The paper's printed angle formula mixes axes and diagonals for i = 1..4;
+// the standard set is used.
+__host__ __device__ constexpr int c9x(int i) {
+  return i == 1 || i == 5 || i == 8 ? 1 : (i == 3 || i == 6 || i == 7 ? -1 : 0);
+}
+__host__ __device__ constexpr int c9y(int i) {
+  return i == 2 || i == 5 || i == 6 ? 1 : (i == 4 || i == 7 || i == 8 ? -1 : 0);
+}
+__host__ __device__ constexpr double w9(int i) {
+  return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+}
+
+// D4Q25 on (r_x, r_y, Q_x, Q_y) (Sec. VI-B, Table dis_vel), grouped by the
+// r-displacement so that a block of velocities shares one pull offset:
+//   0        rest
+//   1..4     (+-1, +-1, 0, 0)   r-diagonals, Q at rest
+//   5..8     (+-1, 0, +-1, 0)   9..12  (+-1, 0, 0, +-1)
+//   13..16   (0, +-1, +-1, 0)   17..20 (0, +-1, 0, +-1)
+//   21..24   (0, 0, +-1, +-1)   Q-diagonals, r at rest
+// Weights 1/3 (rest) and 1/36, c_sP^2 = 1/3.
+struct V4 {
+  int rx, ry, qx, qy;
+};
+__host__ __device__ constexpr V4 c25(int i) {
+  // sign pattern of the four members of each group: (+,+), (+,-), (-,+), (-,-)
+  // for the mixed groups; the two diagonal groups follow the D2Q9 diagonal order.
+  return i == 0 ? V4{0, 0, 0, 0}
+       : i <= 4 ? V4{c9x(i + 4), c9y(i + 4), 0, 0}
+       : i <= 8 ? V4{(i - 5) < 2 ? 1 : -1, 0, ((i - 5) & 1) ? -1 : 1, 0}
+       : i <= 12 ? V4{(i - 9) < 2 ? 1 : -1, 0, 0, ((i - 9) & 1) ? -1 : 1}
+       : i <= 16 ? V4{0, (i - 13) < 2 ? 1 : -1, ((i - 13) & 1) ? -1 : 1, 0}
+       : i <= 20 ? V4{0, (i - 17) < 2 ? 1 : -1, 0, ((i - 17) & 1) ? -1 : 1}
+                 : V4{0, 0, c9x(i - 16), c9y(i - 16)};
+}
+__host__ __device__ constexpr double w25(int i) { return i == 0 ? 1.0 / 3.0 : 1.0 / 36.0; }
+
+// Index of the pull offset for a source displaced by (sx, sy) in {-1,0,1}^2.
+__host__ __device__ constexpr int shift_index(int sx, int sy) { return (sy + 1) * 3 + (sx + 1); }
+
+// --------------------------------------------------------------- contexts
+// Derived lattice parameters (lattice units).
+struct Lattice {
+  int nx = 0, ny = 0, S = 0, nq = 0;
+  double q_radius = 0;
+  double tau1 = 0, tau2 = 0, H = 0, kappa = 0, ell = 0, psi_tot = 0, sigma_q2 = 0;
+  double a0 = 0, kf = 0, u0 = 0, nu = 0, nu_s = 0, eta_p = 0, lambda_h = 0;
+  int ic_mode = 0, precision = 0;
+  size_t pitch = 0;   // elements per stored row
+  size_t plane = 0;   // elements per plane (ny * pitch)
+  int npl = 0;        // population planes: 9 + 25 nq
+  int nm = 0;         // moment planes: nq + 6
+};
+
+// Moment field planes (M): delta psi(q) for q < nq, then these.
+enum { M_DRHO = 0, M_JX, M_JY, M_THXX, M_THXY, M_THYY, M_NSCALAR };
+
+// Device tables of a context (one copy per precision in use).
+template <typename real>
+struct Tables {
+  const real* qx;        // [nq] Q_x (Q lattice units)
+  const real* qy;        // [nq]
+  const real* psi0;      // [nq] storage shift of the polymer: w_i psi0(q)
+  const int* pull;       // [nq*25]: >= 0 source plane (shifted by -c_r); < 0: ~plane, bounce-back
+  const real* delta;     // [nq*25]: w_i (psi0(q - Qdot_i) - psi0(q)), 0 for bounce-back
+  const real* arow;      // [ny] forcing a(y)
+  const real* urow;      // [ny] initial base flow U_x(y)
+};
+
+template <typename real>
+struct KernelArgs {
+  const real* __restrict__ src;  // populations read (pull)
+  real* __restrict__ dst;        // populations written
+  real* M;                       // moment planes
+  real* U;                       // scratch: 2 planes (U_x, U_y)
+  const double* perturb;         // [2][ny][nx] (init only)
+  int nx, ny, nq;
+  size_t pitch, plane;
+  real tau2, c2, inv_c2p1;       // tau2, 2 tau2, 1 / (2 tau2 + 1)
+  real om2b, tb, omb;            // 1 - 2 beta, 2 beta, 1 - beta
+  real r, omr;                   // tau1 / tau2, 1 - tau1 / tau2
+  real kappa, hl2h;              // kappa, H ell^2 / 2
+  real rho0;                     // 1 + psi_tot: total density of the rest state
+  real theta0[3];                // (H ell^2 / 2) sum_q psi0 Q Q
+  real psi_tot0;
+  real l2, H;
+  Tables<real> tab;
+};
+
+struct Workspace {
+  void* base = nullptr;
+  size_t bytes = 0;
+  bool owned = false;
+  size_t off_pop[2] = {0, 0};
+  size_t off_M = 0, off_U = 0, off_tab = 0, off_part = 0, off_diag = 0;
+};
+
+struct Ctx {
+  Lattice L;
+  Workspace ws;
+  cudaStream_t stream = nullptr;
+  int cur = 0;            // population buffer holding the state
+  bool m_valid = false;   // M holds the moments of the current state
+  bool poisoned = false;
+  int64_t step = 0;
+  int diag_blocks = 0;
+};
+
+// Launchers (tfkt_kernels.cu). Each returns the launch status.
+template <typename real>
+cudaError_t launch_init(const KernelArgs<real>& a, cudaStream_t s);
+template <typename real>
+cudaError_t launch_moments(const KernelArgs<real>& a, cudaStream_t s);
+template <typename real>
+cudaError_t launch_step(const KernelArgs<real>& a, cudaStream_t s);
+template <typename real>
+cudaError_t launch_velocity(const KernelArgs<real>& a, cudaStream_t s);
+template <typename real>
+cudaError_t launch_fields(const KernelArgs<real>& a, uint32_t mask, double* out, cudaStream_t s);
+template <typename real>
+cudaError_t launch_psi(const KernelArgs<real>& a, double* out, cudaStream_t s);
+template <typename real>
+cudaError_t launch_populations(const KernelArgs<real>& a, double* out, cudaStream_t s);
+template <typename real>
+cudaError_t launch_diag(const KernelArgs<real>& a, double* partials, int nblocks, double* out,
+                        cudaStream_t s);
+
+constexpr int TX = 32;   // tile width (one warp along x)
+constexpr int TY = 8;    // tile height
+constexpr int DIAG_THREADS = 256;
+
+}  // namespace tfkt

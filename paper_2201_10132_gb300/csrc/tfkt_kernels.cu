@@ -1,0 +1,495 @@
+// Device kernels of the two-fluid kinetic step (arXiv 2201.10132, Sec. VI-VII).
+//
+// Storage: structure-of-arrays planes of ny rows x pitch elements, x fastest.
+// Population planes 0..8 hold the solvent (D2Q9), plane 9 + 25 q + i the
+// polymer velocity i at Q-node q (D4Q25). A buffer holds post-collision g'
+// values that have not been streamed yet, stored as deviations from rest:
+// g' - w_i (solvent, rho_0 = 1) and g' - w_i psi0(q) (polymer). The pull at
+// node r reads g'_i(r - c_r, q - Qdot_i), or g'_{-i}(r, q) when q - Qdot_i
+// leaves the Q-disk (bounce-back), and adds the shift difference delta(q, i).
+//
+// Moment planes M: delta psi(q) (q < nq), then delta rho (total), J_x, J_y
+// (total momentum of g), and delta Theta_xx, xy, yy = (H ell^2 / 2) sum_q
+// delta psi Q Q, all of the pulled (pre-collision) state.
+#include "tfkt_internal.cuh"
+
+namespace tfkt {
+
+namespace {
+
+__device__ __forceinline__ int wrapi(int v, int n) {
+  v %= n;
+  return v < 0 ? v + n : v;
+}
+
+// The nine pull offsets of node (x, y): source displaced by (sx, sy).
+struct Offsets {
+  size_t o[9];
+};
+
+__device__ __forceinline__ Offsets node_offsets(int x, int y, int nx, int ny, size_t pitch) {
+  const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+  const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+  const size_t rm = (size_t)ym * pitch, r0 = (size_t)y * pitch, rp = (size_t)yp * pitch;
+  Offsets f;
+  f.o[0] = rm + xm; f.o[1] = rm + x; f.o[2] = rm + xp;
+  f.o[3] = r0 + xm; f.o[4] = r0 + x; f.o[5] = r0 + xp;
+  f.o[6] = rp + xm; f.o[7] = rp + x; f.o[8] = rp + xp;
+  return f;
+}
+
+// Mixture velocity U of f at node n (Sec. VI-C, moments of f): summing the
+// g -> f momentum relations over both species with the body force applied
+// by the same half-step rule gives rho U = J(g) + (E + rho a) / 2, where the
+// elastic force E = div Theta (Sec. III, Eq. IDef) by central differences.
+template <typename real>
+__device__ __forceinline__ void mixture_velocity(const KernelArgs<real>& a, int x, int y,
+                                                 real& ux, real& uy, real& rho) {
+  const int nq = a.nq;
+  const size_t P = a.plane;
+  const int xm = x == 0 ? a.nx - 1 : x - 1, xp = x == a.nx - 1 ? 0 : x + 1;
+  const int ym = y == 0 ? a.ny - 1 : y - 1, yp = y == a.ny - 1 ? 0 : y + 1;
+  const size_t n = (size_t)y * a.pitch + x;
+  const size_t nxm = (size_t)y * a.pitch + xm, nxp = (size_t)y * a.pitch + xp;
+  const size_t nym = (size_t)ym * a.pitch + x, nyp = (size_t)yp * a.pitch + x;
+  const real* M = a.M;
+  const real* Txx = M + (size_t)(nq + M_THXX) * P;
+  const real* Txy = M + (size_t)(nq + M_THXY) * P;
+  const real* Tyy = M + (size_t)(nq + M_THYY) * P;
+  rho = a.rho0 + M[(size_t)(nq + M_DRHO) * P + n];
+  const real jx = M[(size_t)(nq + M_JX) * P + n];
+  const real jy = M[(size_t)(nq + M_JY) * P + n];
+  const real ex = real(0.5) * (Txx[nxp] - Txx[nxm]) + real(0.5) * (Txy[nyp] - Txy[nym]);
+  const real ey = real(0.5) * (Txy[nxp] - Txy[nxm]) + real(0.5) * (Tyy[nyp] - Tyy[nym]);
+  const real f = a.tab.arow[y];
+  ux = (jx + real(0.5) * (ex + rho * f)) / rho;
+  uy = (jy + real(0.5) * ey) / rho;
+}
+
+// ------------------------------------------------------------------ init
+// g = f^eq of the initial fields (Sec. VI-D): rho_S = 1, psi = psi0(q),
+// U = base flow + perturbation, J^r_eq = psi U, J^Q_eq = psi (Q . grad U -
+// kappa Q) (grad_r psi = 0). Each value is written to the slot that the
+// first pull reads for it, so the first step starts from exactly this state.
+template <typename real>
+__global__ void __launch_bounds__(256) init_kernel(KernelArgs<real> a) {
+  const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
+  if (x >= a.nx || y >= a.ny) return;
+  const int nx = a.nx, ny = a.ny;
+  auto U0 = [&](int xx, int yy, real& ux, real& uy) {
+    const size_t k = (size_t)yy * nx + xx;
+    ux = a.tab.urow[yy] + (a.perturb ? real(a.perturb[k]) : real(0));
+    uy = a.perturb ? real(a.perturb[(size_t)nx * ny + k]) : real(0);
+  };
+  const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+  const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+  real ux, uy, uxa, uya, uxb, uyb;
+  U0(x, y, ux, uy);
+  U0(xp, y, uxa, uya);
+  U0(xm, y, uxb, uyb);
+  const real G00 = real(0.5) * (uxa - uxb), G01 = real(0.5) * (uya - uyb);
+  U0(x, yp, uxa, uya);
+  U0(x, ym, uxb, uyb);
+  const real G10 = real(0.5) * (uxa - uxb), G11 = real(0.5) * (uya - uyb);
+  const Offsets off = node_offsets(x, y, nx, ny, a.pitch);
+  const size_t P = a.plane;
+  const real usq = ux * ux + uy * uy;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const real cu = real(c9x(i)) * ux + real(c9y(i)) * uy;
+    const real h = real(w9(i)) * (real(3) * cu + real(4.5) * cu * cu - real(1.5) * usq);
+    a.dst[(size_t)i * P + off.o[shift_index(-c9x(i), -c9y(i))]] = h;
+  }
+  for (int q = 0; q < a.nq; ++q) {
+    const real Qx = a.tab.qx[q], Qy = a.tab.qy[q], psi = a.tab.psi0[q];
+    const real jrx = psi * ux, jry = psi * uy;
+    const real jqx = psi * (Qx * G00 + Qy * G10 - a.kappa * Qx);
+    const real jqy = psi * (Qx * G01 + Qy * G11 - a.kappa * Qy);
+#pragma unroll
+    for (int i = 0; i < 25; ++i) {
+      const V4 c = c25(i);
+      const real h = real(w25(i)) * real(3) *
+                     (jrx * real(c.rx) + jry * real(c.ry) + jqx * real(c.qx) + jqy * real(c.qy));
+      const int e = a.tab.pull[q * 25 + i];
+      const size_t o = e >= 0 ? off.o[shift_index(-c.rx, -c.ry)] : off.o[4];
+      const int p = e >= 0 ? e : ~e;
+      a.dst[(size_t)p * P + o] = h - a.tab.delta[q * 25 + i];
+    }
+  }
+}
+
+// --------------------------------------------------------------- moments
+// Pull-read every population of node (x, y) and write its moments to M
+// (Sec. VI-A / VI-B moment definitions; Theta of Sec. III for Hookean springs).
+template <typename real>
+__global__ void __launch_bounds__(256) moments_kernel(KernelArgs<real> a) {
+  const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
+  if (x >= a.nx || y >= a.ny) return;
+  const Offsets off = node_offsets(x, y, a.nx, a.ny, a.pitch);
+  const size_t P = a.plane;
+  const size_t n = off.o[4];
+  const real* __restrict__ src = a.src;
+  real drho = 0, jx = 0, jy = 0;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const real h = src[(size_t)i * P + off.o[shift_index(-c9x(i), -c9y(i))]];
+    drho += h;
+    jx += real(c9x(i)) * h;
+    jy += real(c9y(i)) * h;
+  }
+  real txx = 0, txy = 0, tyy = 0;
+  for (int q = 0; q < a.nq; ++q) {
+    real dpsi = 0, rx = 0, ry = 0;
+#pragma unroll
+    for (int i = 0; i < 25; ++i) {
+      const V4 c = c25(i);
+      const int e = a.tab.pull[q * 25 + i];
+      const size_t o = e >= 0 ? off.o[shift_index(-c.rx, -c.ry)] : off.o[4];
+      const int p = e >= 0 ? e : ~e;
+      const real h = src[(size_t)p * P + o] + a.tab.delta[q * 25 + i];
+      dpsi += h;
+      rx += real(c.rx) * h;
+      ry += real(c.ry) * h;
+    }
+    a.M[(size_t)q * P + n] = dpsi;
+    drho += dpsi;
+    jx += rx;
+    jy += ry;
+    const real Qx = a.tab.qx[q], Qy = a.tab.qy[q];
+    txx += dpsi * Qx * Qx;
+    txy += dpsi * Qx * Qy;
+    tyy += dpsi * Qy * Qy;
+  }
+  const int nq = a.nq;
+  a.M[(size_t)(nq + M_DRHO) * P + n] = drho;
+  a.M[(size_t)(nq + M_JX) * P + n] = jx;
+  a.M[(size_t)(nq + M_JY) * P + n] = jy;
+  a.M[(size_t)(nq + M_THXX) * P + n] = a.hl2h * txx;
+  a.M[(size_t)(nq + M_THXY) * P + n] = a.hl2h * txy;
+  a.M[(size_t)(nq + M_THYY) * P + n] = a.hl2h * tyy;
+}
+
+// ------------------------------------------------------------------ step
+// One collision of the pulled state, written unstreamed to dst:
+//   U from M (tile + 1-node halo in shared memory), grad U by central
+//   differences; solvent J_S(f) = (2 tau2 J_S(g) + rho_S U + tau2 rho a) /
+//   (2 tau2 + 1), u_S = J_S(f) / rho_S; polymer J^r_eq = psi U + tau2 D,
+//   D = (H ell^2 / 2) Q (Q . grad_r psi), J^Q_eq = psi (Q . grad U - kappa Q),
+//   J(f) = (2 tau2 J(g) + J_eq) / (2 tau2 + 1);
+//   g' = (1 - 2 beta) g + 2 beta [(1 - tau1/tau2) f* + (tau1/tau2) f^eq]
+//        + (1 - beta) S_i,   beta = 1 / (2 tau1 + 1)
+// with the quadratic solvent equilibria (Eq. dis_eq), the linear polymer
+// equilibria (Eqs. feq_rq_space, fstar_rq_space) and the Guo source S_i of the
+// force density rho a (solvent only).
+template <typename real>
+__global__ void __launch_bounds__(256) step_kernel(KernelArgs<real> a) {
+  __shared__ real sUx[TY + 2][TX + 2];
+  __shared__ real sUy[TY + 2][TX + 2];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  for (int k = tid; k < (TX + 2) * (TY + 2); k += TX * TY) {
+    const int hx = k % (TX + 2), hy = k / (TX + 2);
+    const int gx = wrapi(x0 - 1 + hx, a.nx), gy = wrapi(y0 - 1 + hy, a.ny);
+    real ux, uy, rho;
+    mixture_velocity(a, gx, gy, ux, uy, rho);
+    sUx[hy][hx] = ux;
+    sUy[hy][hx] = uy;
+  }
+  __syncthreads();
+  const int x = x0 + tx, y = y0 + ty;
+  if (x >= a.nx || y >= a.ny) return;
+  const real Ux = sUx[ty + 1][tx + 1], Uy = sUy[ty + 1][tx + 1];
+  const real G00 = real(0.5) * (sUx[ty + 1][tx + 2] - sUx[ty + 1][tx]);  // d_x U_x
+  const real G01 = real(0.5) * (sUy[ty + 1][tx + 2] - sUy[ty + 1][tx]);  // d_x U_y
+  const real G10 = real(0.5) * (sUx[ty + 2][tx + 1] - sUx[ty][tx + 1]);  // d_y U_x
+  const real G11 = real(0.5) * (sUy[ty + 2][tx + 1] - sUy[ty][tx + 1]);  // d_y U_y
+
+  const Offsets off = node_offsets(x, y, a.nx, a.ny, a.pitch);
+  const size_t P = a.plane;
+  const size_t n = off.o[4];
+  const int nq = a.nq;
+  const real rho = a.rho0 + a.M[(size_t)(nq + M_DRHO) * P + n];
+  const real force = rho * a.tab.arow[y];
+  const real* __restrict__ src = a.src;
+  real* __restrict__ dst = a.dst;
+
+  // ---- solvent
+  {
+    real h[9];
+    real drs = 0, jsx = 0, jsy = 0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      h[i] = src[(size_t)i * P + off.o[shift_index(-c9x(i), -c9y(i))]];
+      drs += h[i];
+      jsx += real(c9x(i)) * h[i];
+      jsy += real(c9y(i)) * h[i];
+    }
+    const real rs = real(1) + drs;
+    const real jfx = (a.c2 * jsx + rs * Ux + a.tau2 * force) * a.inv_c2p1;
+    const real jfy = (a.c2 * jsy + rs * Uy) * a.inv_c2p1;
+    const real usx = jfx / rs, usy = jfy / rs;
+    const real vx = a.omr * usx + a.r * Ux, vy = a.omr * usy + a.r * Uy;
+    const real sq = a.omr * (usx * usx + usy * usy) + a.r * (Ux * Ux + Uy * Uy);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const real cx = real(c9x(i)), cy = real(c9y(i));
+      const real cus = cx * usx + cy * usy, cu = cx * Ux + cy * Uy;
+      const real feq_dev =
+          real(w9(i)) * (drs + rs * (real(3) * (cx * vx + cy * vy) +
+                                     real(4.5) * (a.omr * cus * cus + a.r * cu * cu) -
+                                     real(1.5) * sq));
+      const real srcterm = real(w9(i)) * (real(3) * (cx - Ux) + real(9) * cu * cx) * force;
+      dst[(size_t)i * P + n] = a.om2b * h[i] + a.tb * feq_dev + a.omb * srcterm;
+    }
+  }
+
+  // ---- polymer, one Q-node at a time
+  const size_t nxm = off.o[3], nxp = off.o[5], nym = off.o[1], nyp = off.o[7];
+  for (int q = 0; q < nq; ++q) {
+    const real* Mq = a.M + (size_t)q * P;
+    const real dpx = real(0.5) * (Mq[nxp] - Mq[nxm]);
+    const real dpy = real(0.5) * (Mq[nyp] - Mq[nym]);
+    real h[25];
+    real dpsi = 0, rx = 0, ry = 0, qx = 0, qy = 0;
+#pragma unroll
+    for (int i = 0; i < 25; ++i) {
+      const V4 c = c25(i);
+      const int e = a.tab.pull[q * 25 + i];
+      const size_t o = e >= 0 ? off.o[shift_index(-c.rx, -c.ry)] : off.o[4];
+      const int p = e >= 0 ? e : ~e;
+      h[i] = src[(size_t)p * P + o] + a.tab.delta[q * 25 + i];
+      dpsi += h[i];
+      rx += real(c.rx) * h[i];
+      ry += real(c.ry) * h[i];
+      qx += real(c.qx) * h[i];
+      qy += real(c.qy) * h[i];
+    }
+    const real Qx = a.tab.qx[q], Qy = a.tab.qy[q];
+    const real psi = a.tab.psi0[q] + dpsi;
+    const real qg = Qx * dpx + Qy * dpy;
+    const real jrex = psi * Ux + a.tau2 * a.hl2h * Qx * qg;
+    const real jrey = psi * Uy + a.tau2 * a.hl2h * Qy * qg;
+    const real jqex = psi * (Qx * G00 + Qy * G10 - a.kappa * Qx);
+    const real jqey = psi * (Qx * G01 + Qy * G11 - a.kappa * Qy);
+    // mixture (1 - r) J(f) + r J_eq of the two equilibria's momenta
+    const real mrx = a.omr * (a.c2 * rx + jrex) * a.inv_c2p1 + a.r * jrex;
+    const real mry = a.omr * (a.c2 * ry + jrey) * a.inv_c2p1 + a.r * jrey;
+    const real mqx = a.omr * (a.c2 * qx + jqex) * a.inv_c2p1 + a.r * jqex;
+    const real mqy = a.omr * (a.c2 * qy + jqey) * a.inv_c2p1 + a.r * jqey;
+    real* dq = dst + (size_t)(9 + 25 * q) * P + n;
+#pragma unroll
+    for (int i = 0; i < 25; ++i) {
+      const V4 c = c25(i);
+      const real fdev = real(w25(i)) * (dpsi + real(3) * (mrx * real(c.rx) + mry * real(c.ry) +
+                                                           mqx * real(c.qx) + mqy * real(c.qy)));
+      dq[(size_t)i * P] = a.om2b * h[i] + a.tb * fdev;
+    }
+  }
+}
+
+// ------------------------------------------------------------- observers
+template <typename real>
+__global__ void __launch_bounds__(256) velocity_kernel(KernelArgs<real> a) {
+  const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
+  if (x >= a.nx || y >= a.ny) return;
+  real ux, uy, rho;
+  mixture_velocity(a, x, y, ux, uy, rho);
+  const size_t n = (size_t)y * a.pitch + x;
+  a.U[n] = ux;
+  a.U[a.plane + n] = uy;
+}
+
+// Per-node observables (Sec. VII): rho_S, psi_tot, U, C, Theta, Q_rms, vorticity.
+template <typename real>
+__device__ void node_fields(const KernelArgs<real>& a, int x, int y, double f[TFKT_NFIELDS]) {
+  const size_t P = a.plane;
+  const size_t n = (size_t)y * a.pitch + x;
+  const int nq = a.nq;
+  double pt = 0, sxx = 0, sxy = 0, syy = 0;
+  for (int q = 0; q < nq; ++q) {
+    const double p = double(a.tab.psi0[q]) + double(a.M[(size_t)q * P + n]);
+    const double Qx = a.tab.qx[q], Qy = a.tab.qy[q];
+    pt += p;
+    sxx += p * Qx * Qx;
+    sxy += p * Qx * Qy;
+    syy += p * Qy * Qy;
+  }
+  const double rho = double(a.rho0) + double(a.M[(size_t)(nq + M_DRHO) * P + n]);
+  const double l2 = a.l2, hh = 0.5 * double(a.H) * l2;
+  f[TFKT_F_RHO_S] = rho - pt;
+  f[TFKT_F_PSI_TOT] = pt;
+  f[TFKT_F_UX] = a.U[n];
+  f[TFKT_F_UY] = a.U[P + n];
+  const double cxx = pt != 0 ? l2 * sxx / pt : 0, cxy = pt != 0 ? l2 * sxy / pt : 0,
+               cyy = pt != 0 ? l2 * syy / pt : 0;
+  f[TFKT_F_CXX] = cxx;
+  f[TFKT_F_CXY] = cxy;
+  f[TFKT_F_CYY] = cyy;
+  f[TFKT_F_THXX] = hh * sxx;
+  f[TFKT_F_THXY] = hh * sxy;
+  f[TFKT_F_THYY] = hh * syy;
+  f[TFKT_F_QRMS] = sqrt(cxx + cyy);
+  const int xm = x == 0 ? a.nx - 1 : x - 1, xp = x == a.nx - 1 ? 0 : x + 1;
+  const int ym = y == 0 ? a.ny - 1 : y - 1, yp = y == a.ny - 1 ? 0 : y + 1;
+  const double duy_dx = 0.5 * (double(a.U[P + (size_t)y * a.pitch + xp]) -
+                               double(a.U[P + (size_t)y * a.pitch + xm]));
+  const double dux_dy =
+      0.5 * (double(a.U[(size_t)yp * a.pitch + x]) - double(a.U[(size_t)ym * a.pitch + x]));
+  f[TFKT_F_VORT] = duy_dx - dux_dy;
+}
+
+template <typename real>
+__global__ void __launch_bounds__(256) fields_kernel(KernelArgs<real> a, uint32_t mask,
+                                                     double* out) {
+  const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
+  if (x >= a.nx || y >= a.ny) return;
+  double f[TFKT_NFIELDS];
+  node_fields(a, x, y, f);
+  const size_t N = (size_t)a.nx * a.ny, k = (size_t)y * a.nx + x;
+  int slot = 0;
+  for (int j = 0; j < TFKT_NFIELDS; ++j)
+    if (mask & (1u << j)) out[(size_t)(slot++) * N + k] = f[j];
+}
+
+template <typename real>
+__global__ void __launch_bounds__(256) psi_kernel(KernelArgs<real> a, double* out) {
+  const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
+  if (x >= a.nx || y >= a.ny) return;
+  const size_t n = (size_t)y * a.pitch + x, k = (size_t)y * a.nx + x;
+  for (int q = 0; q < a.nq; ++q)
+    out[k * a.nq + q] = double(a.tab.psi0[q]) + double(a.M[(size_t)q * a.plane + n]);
+}
+
+// Stored populations with the storage shift added back, as doubles.
+template <typename real>
+__global__ void __launch_bounds__(256) populations_kernel(KernelArgs<real> a, double* out) {
+  const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
+  if (x >= a.nx || y >= a.ny) return;
+  const size_t n = (size_t)y * a.pitch + x, k = (size_t)y * a.nx + x,
+               N = (size_t)a.nx * a.ny;
+  for (int i = 0; i < 9; ++i) out[(size_t)i * N + k] = w9(i) + double(a.src[(size_t)i * a.plane + n]);
+  for (int q = 0; q < a.nq; ++q)
+    for (int i = 0; i < 25; ++i) {
+      const int p = 9 + 25 * q + i;
+      out[(size_t)p * N + k] = w25(i) * double(a.tab.psi0[q]) + double(a.src[(size_t)p * a.plane + n]);
+    }
+}
+
+// Global diagnostics: per-block FP64 partial sums over a fixed node
+// partition (grid-stride, fixed order), then one block sums the partials in
+// block order: the result does not depend on scheduling.
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) v += __shfl_down_sync(0xffffffffu, v, s);
+  return v;
+}
+
+template <typename real>
+__global__ void __launch_bounds__(DIAG_THREADS) diag_partial_kernel(KernelArgs<real> a,
+                                                                    double* partials) {
+  double acc[TFKT_NDIAG] = {0, 0, 0, 0, 0, 0, 0, 0};
+  const size_t N = (size_t)a.nx * a.ny;
+  for (size_t k = (size_t)blockIdx.x * DIAG_THREADS + threadIdx.x; k < N;
+       k += (size_t)gridDim.x * DIAG_THREADS) {
+    const int x = int(k % a.nx), y = int(k / a.nx);
+    double f[TFKT_NFIELDS];
+    node_fields(a, x, y, f);
+    const double rho = f[TFKT_F_RHO_S] + f[TFKT_F_PSI_TOT];
+    const double ux = f[TFKT_F_UX], uy = f[TFKT_F_UY], w = f[TFKT_F_VORT];
+    acc[TFKT_D_MASS_S] += f[TFKT_F_RHO_S];
+    acc[TFKT_D_MASS_P] += f[TFKT_F_PSI_TOT];
+    acc[TFKT_D_PX] += rho * ux;
+    acc[TFKT_D_PY] += rho * uy;
+    acc[TFKT_D_KE] += 0.5 * rho * (ux * ux + uy * uy);
+    acc[TFKT_D_ENSTROPHY] += 0.5 * w * w;
+    acc[TFKT_D_QRMS_MEAN] += f[TFKT_F_QRMS];
+    acc[TFKT_D_EY2] += uy * uy;
+  }
+  __shared__ double red[DIAG_THREADS / 32][TFKT_NDIAG];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < TFKT_NDIAG; ++j) {
+    const double v = warp_sum(acc[j]);
+    if (lane == 0) red[warp][j] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < TFKT_NDIAG) {
+    double s = 0;
+    for (int w = 0; w < DIAG_THREADS / 32; ++w) s += red[w][threadIdx.x];
+    partials[(size_t)blockIdx.x * TFKT_NDIAG + threadIdx.x] = s;
+  }
+}
+
+__global__ void diag_final_kernel(const double* partials, int nblocks, double inv_n, double* out) {
+  if (threadIdx.x < TFKT_NDIAG) {
+    double s = 0;
+    for (int b = 0; b < nblocks; ++b) s += partials[(size_t)b * TFKT_NDIAG + threadIdx.x];
+    out[threadIdx.x] = threadIdx.x == TFKT_D_QRMS_MEAN ? s * inv_n : s;
+  }
+}
+
+inline dim3 node_grid(int nx, int ny) { return dim3((nx + TX - 1) / TX, (ny + TY - 1) / TY); }
+
+}  // namespace
+
+template <typename real>
+cudaError_t launch_init(const KernelArgs<real>& a, cudaStream_t s) {
+  init_kernel<real><<<node_grid(a.nx, a.ny), dim3(TX, TY), 0, s>>>(a);
+  return cudaGetLastError();
+}
+template <typename real>
+cudaError_t launch_moments(const KernelArgs<real>& a, cudaStream_t s) {
+  moments_kernel<real><<<node_grid(a.nx, a.ny), dim3(TX, TY), 0, s>>>(a);
+  return cudaGetLastError();
+}
+template <typename real>
+cudaError_t launch_step(const KernelArgs<real>& a, cudaStream_t s) {
+  step_kernel<real><<<node_grid(a.nx, a.ny), dim3(TX, TY), 0, s>>>(a);
+  return cudaGetLastError();
+}
+template <typename real>
+cudaError_t launch_velocity(const KernelArgs<real>& a, cudaStream_t s) {
+  velocity_kernel<real><<<node_grid(a.nx, a.ny), dim3(TX, TY), 0, s>>>(a);
+  return cudaGetLastError();
+}
+template <typename real>
+cudaError_t launch_fields(const KernelArgs<real>& a, uint32_t mask, double* out, cudaStream_t s) {
+  fields_kernel<real><<<node_grid(a.nx, a.ny), dim3(TX, TY), 0, s>>>(a, mask, out);
+  return cudaGetLastError();
+}
+template <typename real>
+cudaError_t launch_psi(const KernelArgs<real>& a, double* out, cudaStream_t s) {
+  psi_kernel<real><<<node_grid(a.nx, a.ny), dim3(TX, TY), 0, s>>>(a, out);
+  return cudaGetLastError();
+}
+template <typename real>
+cudaError_t launch_populations(const KernelArgs<real>& a, double* out, cudaStream_t s) {
+  populations_kernel<real><<<node_grid(a.nx, a.ny), dim3(TX, TY), 0, s>>>(a, out);
+  return cudaGetLastError();
+}
+template <typename real>
+cudaError_t launch_diag(const KernelArgs<real>& a, double* partials, int nblocks, double* out,
+                        cudaStream_t s) {
+  diag_partial_kernel<real><<<nblocks, DIAG_THREADS, 0, s>>>(a, partials);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  diag_final_kernel<<<1, 32, 0, s>>>(partials, nblocks, 1.0 / ((double)a.nx * a.ny), out);
+  return cudaGetLastError();
+}
+
+#define TFKT_INSTANTIATE(real)                                                                 \
+  template cudaError_t launch_init<real>(const KernelArgs<real>&, cudaStream_t);              \
+  template cudaError_t launch_moments<real>(const KernelArgs<real>&, cudaStream_t);           \
+  template cudaError_t launch_step<real>(const KernelArgs<real>&, cudaStream_t);              \
+  template cudaError_t launch_velocity<real>(const KernelArgs<real>&, cudaStream_t);          \
+  template cudaError_t launch_fields<real>(const KernelArgs<real>&, uint32_t, double*,        \
+                                           cudaStream_t);                                     \
+  template cudaError_t launch_psi<real>(const KernelArgs<real>&, double*, cudaStream_t);      \
+  template cudaError_t launch_populations<real>(const KernelArgs<real>&, double*,             \
+                                                cudaStream_t);                                \
+  template cudaError_t launch_diag<real>(const KernelArgs<real>&, double*, int, double*,      \
+                                         cudaStream_t);
+TFKT_INSTANTIATE(float)
+TFKT_INSTANTIATE(double)
+
+}  // namespace tfkt

@@ -1,0 +1,244 @@
+"""Python binding of libtfkt (include/tfkt.h): argument marshalling only.
+
+Every step of the two-fluid kinetic scheme runs in the library's CUDA kernels.
+There is no CPU fallback: if the in-tree library is missing or cannot be
+loaded, importing the binding's functions raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, fields as dc_fields
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libtfkt.so")
+
+FP64, FP32 = 0, 1
+FIELDS = ["rho_s", "psi_tot", "ux", "uy", "cxx", "cxy", "cyy", "thxx", "thxy", "thyy", "qrms",
+          "vort"]
+KERNELS = ["moments", "step"]
+DIAGS = ["mass_s", "mass_p", "px", "py", "ke", "enstrophy", "qrms_mean", "ey2"]
+STATUS = {0: "TFKT_OK", 1: "TFKT_EINVAL", 2: "TFKT_ENOMEM", 3: "TFKT_ECUDA", 4: "TFKT_ENAN",
+          5: "TFKT_ESTATE"}
+
+
+class TfktError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("q_side", ctypes.c_int32),
+                ("q_radius", ctypes.c_double), ("re", ctypes.c_double), ("wi", ctypes.c_double),
+                ("beta", ctypes.c_double), ("u0", ctypes.c_double),
+                ("k_periods", ctypes.c_int32), ("tau2", ctypes.c_double),
+                ("ell", ctypes.c_double), ("ic_mode", ctypes.c_int32),
+                ("precision", ctypes.c_int32)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nq", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("tau1", ctypes.c_double),
+                ("tau2", ctypes.c_double), ("H", ctypes.c_double), ("kappa", ctypes.c_double),
+                ("ell", ctypes.c_double), ("psi_tot", ctypes.c_double),
+                ("sigma_q2", ctypes.c_double), ("a0", ctypes.c_double), ("kf", ctypes.c_double),
+                ("nu", ctypes.c_double), ("nu_s", ctypes.c_double), ("eta_p", ctypes.c_double),
+                ("lambda_h", ctypes.c_double), ("step", ctypes.c_int64),
+                ("workspace_bytes", ctypes.c_size_t), ("pitch", ctypes.c_size_t),
+                ("bytes_per_node_step", ctypes.c_size_t)]
+
+
+@dataclass
+class Params:
+    """Mirror of tfkt_params (physical description of one Kolmogorov run)."""
+    nx: int
+    ny: int
+    q_side: int
+    q_radius: float
+    re: float
+    wi: float
+    beta: float
+    u0: float = 0.05
+    k_periods: int = 1
+    tau2: float = 0.0
+    ell: float = 0.0
+    ic_mode: int = 0
+    precision: int = FP64
+
+    def _c(self) -> _Params:
+        return _Params(*(getattr(self, f.name) for f in dc_fields(self)))
+
+    @classmethod
+    def from_workload(cls, w, precision: int = FP64):
+        return cls(w.nx, w.ny, w.q_side, w.q_radius, w.re, w.wi, w.beta, w.u0, w.k_periods,
+                   w.tau2, 0.0, w.ic_mode, precision)
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load the in-tree libtfkt.so (built by __graft_entry__.build()); raises if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libtfkt.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P, S = ctypes.c_void_p, ctypes.c_int
+        D = ctypes.POINTER(ctypes.c_double)
+        L.tfkt_required_bytes.argtypes = [ctypes.POINTER(_Params), ctypes.POINTER(ctypes.c_size_t)]
+        L.tfkt_create.argtypes = [ctypes.POINTER(_Params), D, P, ctypes.c_size_t, P,
+                                  ctypes.POINTER(P)]
+        L.tfkt_step.argtypes = [P, ctypes.c_int64]
+        L.tfkt_step_profiled.argtypes = [P, ctypes.c_int64, D, ctypes.POINTER(ctypes.c_int64)]
+        L.tfkt_moments.argtypes = [P, ctypes.c_uint32, P, ctypes.c_size_t, ctypes.c_int]
+        L.tfkt_psi.argtypes = [P, P, ctypes.c_size_t, ctypes.c_int]
+        L.tfkt_diagnostics.argtypes = [P, D]
+        L.tfkt_populations.argtypes = [P, D, ctypes.c_size_t]
+        L.tfkt_get_info.argtypes = [P, ctypes.POINTER(_Info)]
+        L.tfkt_lattice.argtypes = [ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+        L.tfkt_sync.argtypes = [P]
+        L.tfkt_destroy.argtypes = [P]
+        L.tfkt_status_string.argtypes = [S]
+        L.tfkt_status_string.restype = ctypes.c_char_p
+        L.tfkt_last_error.restype = ctypes.c_char_p
+        for n in ("tfkt_required_bytes", "tfkt_create", "tfkt_step", "tfkt_step_profiled",
+                  "tfkt_moments", "tfkt_psi",
+                  "tfkt_diagnostics", "tfkt_populations", "tfkt_get_info", "tfkt_lattice",
+                  "tfkt_sync", "tfkt_destroy"):
+            getattr(L, n).restype = S
+        _lib = L
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise TfktError(status, where, lib().tfkt_last_error().decode())
+
+
+def _dptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def required_bytes(p: Params) -> int:
+    n = ctypes.c_size_t()
+    _check(lib().tfkt_required_bytes(ctypes.byref(p._c()), ctypes.byref(n)), "tfkt_required_bytes")
+    return n.value
+
+
+def lattice():
+    c9 = np.zeros((9, 2), np.int32)
+    c25 = np.zeros((25, 4), np.int32)
+    _check(lib().tfkt_lattice(c9.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                              c25.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))), "tfkt_lattice")
+    return c9, c25
+
+
+def field_mask(names) -> int:
+    m = 0
+    for n in names:
+        m |= 1 << FIELDS.index(n)
+    return m
+
+
+class Solver:
+    """One tfkt context. workspace: optional device buffer (e.g. a torch uint8
+    tensor) of at least required_bytes(params), kept alive by the solver;
+    stream: optional cudaStream_t handle (int), e.g. torch's cuda_stream."""
+
+    def __init__(self, params: Params, perturb: np.ndarray | None = None, workspace=None,
+                 stream: int | None = None):
+        self.params = params
+        self._workspace = workspace
+        if perturb is not None:
+            perturb = np.ascontiguousarray(perturb, dtype=np.float64)
+            assert perturb.shape == (2, params.ny, params.nx)
+        ws_ptr, ws_bytes = None, 0
+        if workspace is not None:
+            ws_ptr = workspace.data_ptr()
+            ws_bytes = workspace.numel() * workspace.element_size()
+        h = ctypes.c_void_p()
+        _check(lib().tfkt_create(ctypes.byref(params._c()),
+                                 None if perturb is None else _dptr(perturb), ws_ptr, ws_bytes,
+                                 stream, ctypes.byref(h)), "tfkt_create")
+        self._h = h
+        self.info = self.get_info()
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _check(lib().tfkt_destroy(self._h), "tfkt_destroy")
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---- the C-ABI calls
+    def step(self, n: int = 1):
+        _check(lib().tfkt_step(self._h, int(n)), "tfkt_step")
+
+    def step_profiled(self, n: int, kernel_ms: np.ndarray, launches: np.ndarray):
+        """tfkt_step_profiled: adds per-kernel milliseconds and launch counts."""
+        assert kernel_ms.dtype == np.float64 and launches.dtype == np.int64
+        _check(lib().tfkt_step_profiled(self._h, int(n), _dptr(kernel_ms),
+                                        launches.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))),
+               "tfkt_step_profiled")
+
+    def sync(self):
+        _check(lib().tfkt_sync(self._h), "tfkt_sync")
+
+    def get_info(self) -> dict:
+        i = _Info()
+        _check(lib().tfkt_get_info(self._h, ctypes.byref(i)), "tfkt_get_info")
+        return {k: getattr(i, k) for k, _ in _Info._fields_}
+
+    def moments(self, names=FIELDS, out=None) -> dict:
+        """Fields as float64 [ny, nx] arrays (host), or into a device buffer `out`
+        (a tensor with data_ptr()) when given; returns {name: array} for host."""
+        names = [n for n in FIELDS if n in names]
+        mask = field_mask(names)
+        ny, nx = self.params.ny, self.params.nx
+        if out is not None:
+            nbytes = out.numel() * out.element_size()
+            _check(lib().tfkt_moments(self._h, mask, out.data_ptr(), nbytes, 1), "tfkt_moments")
+            return {}
+        buf = np.empty((len(names), ny, nx), np.float64)
+        _check(lib().tfkt_moments(self._h, mask, buf.ctypes.data, buf.nbytes, 0), "tfkt_moments")
+        return {n: buf[k] for k, n in enumerate(names)}
+
+    def moments_into(self, mask: int, host: np.ndarray):
+        _check(lib().tfkt_moments(self._h, mask, host.ctypes.data, host.nbytes, 0),
+               "tfkt_moments")
+
+    def psi(self) -> np.ndarray:
+        ny, nx, nq = self.params.ny, self.params.nx, self.info["nq"]
+        buf = np.empty((ny, nx, nq), np.float64)
+        _check(lib().tfkt_psi(self._h, buf.ctypes.data, buf.nbytes, 0), "tfkt_psi")
+        return buf
+
+    def diagnostics(self) -> dict:
+        out = np.zeros(len(DIAGS))
+        _check(lib().tfkt_diagnostics(self._h, _dptr(out)), "tfkt_diagnostics")
+        return dict(zip(DIAGS, out.tolist()))
+
+    def diagnostics_into(self, out: np.ndarray):
+        _check(lib().tfkt_diagnostics(self._h, _dptr(out)), "tfkt_diagnostics")
+
+    def populations(self) -> np.ndarray:
+        """Stored post-collision g' as float64 [9 + 25 nq, ny, nx]."""
+        ny, nx, nq = self.params.ny, self.params.nx, self.info["nq"]
+        buf = np.empty((9 + 25 * nq, ny, nx), np.float64)
+        _check(lib().tfkt_populations(self._h, _dptr(buf), buf.nbytes), "tfkt_populations")
+        return buf

@@ -1,0 +1,59 @@
+"""C-ABI checks that need no GPU: the library loads, exports every function that
+include/tfkt.h declares, and rejects invalid parameters before touching a device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def T():
+    from paper_2201_10132_gb300 import build, tfkt
+    build.build()
+    return tfkt
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "tfkt.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(tfkt_[a-z_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(T):
+    names = _declared()
+    assert {"tfkt_create", "tfkt_step", "tfkt_moments", "tfkt_destroy"} <= set(names)
+    lib = ctypes.CDLL(T.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_lattice_order_is_a_velocity_set(T):
+    import numpy as np
+    c9, c25 = T.lattice()
+    assert len({tuple(v) for v in c9.tolist()}) == 9
+    assert len({tuple(v) for v in c25.tolist()}) == 25
+    assert all((np.abs(v) <= 1).all() for v in c25)
+    assert sorted(int((v != 0).sum()) for v in c25) == [0] + [2] * 24
+
+
+def test_required_bytes_matches_layout(T):
+    p = T.Params(4096, 4096, 6, 3.0, 10.0, 1.0, 0.2, 0.05, 64, precision=T.FP32)
+    n = T.required_bytes(p)
+    nodes = 4096 * 4096
+    pops = (9 + 25 * 32) * nodes * 4 * 2
+    assert pops < n < pops * 1.1
+
+
+@pytest.mark.parametrize("kw", [dict(beta=0.0), dict(beta=1.5), dict(re=0.0), dict(u0=0.5),
+                                dict(wi=0.0), dict(tau2=1e-4), dict(q_radius=0.0), dict(nx=0),
+                                dict(q_side=65), dict(precision=7), dict(ic_mode=3),
+                                dict(q_radius=0.1, q_side=2)])
+def test_invalid_parameters(T, kw):
+    args = dict(nx=8, ny=8, q_side=4, q_radius=2.0, re=5.0, wi=0.5, beta=0.2)
+    args.update(kw)
+    with pytest.raises(T.TfktError) as e:
+        T.required_bytes(T.Params(**args))
+    assert e.value.status == 1  # TFKT_EINVAL

@@ -1,0 +1,168 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the FP64 CPU oracle.
+
+FP64 mode must match the oracle to 1e-12 relative (relative to the field's
+largest magnitude) on every macroscopic field, on psi(r, q) and on the stored
+post-collision populations. The grids span several 32 x 8 tiles with ragged
+tails, plus the degenerate 1 x 1 grid and a one-node Q-disk.
+
+FP32 mode stores populations as float deviations from rest and updates them
+in float. Its tolerance follows from the arithmetic: each moment is a sum of
+~25 nq + 9 terms of size ~w_i |deviation| rounded at 2^-24, and every step
+re-rounds the state, so after n steps the absolute error in U is of order
+sqrt(n) * 1e-7 * |U|-scale plus the float rounding of U itself; the tests
+allow 2e-5 of the field's largest magnitude for n <= 50, where velocity-derived
+fields (U_x, U_y, vorticity) are measured against the largest velocity.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ["rho_s", "psi_tot", "ux", "uy", "cxx", "cxy", "cyy", "thxx", "thxy", "thyy", "qrms",
+          "vort"]
+
+
+@pytest.fixture(scope="module")
+def T():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2201_10132_gb300 import build, tfkt
+    build.build()
+    return tfkt
+
+
+def _oracle_run(O, nx, ny, S, R, re, wi, beta, kp, tau2, pert, ic, steps):
+    lat = O.map_params(nx, ny, S, R, re, wi, beta, 0.05, kp, tau2)
+    o = O.Oracle(lat)
+    o.init(pert, ic)
+    o.step(steps)
+    return o
+
+
+def _rel(a, b):
+    scale = np.abs(b).max()
+    return np.abs(a - b).max() / scale if scale > 0 else np.abs(a - b).max()
+
+
+CASES = [
+    # nx, ny, S, R, re, wi, beta, kp, tau2, ic, steps
+    (24, 16, 6, 3.0, 5.0, 0.5, 0.2, 1, 0.0, 1, 1),
+    (24, 16, 6, 3.0, 5.0, 0.5, 0.2, 1, 0.0, 1, 25),
+    (70, 19, 8, 4.0, 5.0, 0.5, 0.2, 1, 0.0, 0, 12),      # ragged in x and y
+    (40, 24, 6, 3.0, 4.0, 1.0, 0.5, 2, 0.3, 1, 15),      # tau2 > tau1: two relaxations active
+    (33, 9, 4, 2.0, 3.0, 0.0, 1.0, 1, 0.0, 1, 10),       # Newtonian: no polymer
+    (1, 1, 1, 1.0, 5.0, 0.5, 0.2, 1, 0.0, 0, 7),         # one r-node, one Q-node
+    (5, 3, 2, 1.0, 5.0, 0.5, 0.2, 1, 0.0, 1, 9),         # 2x2 Q-grid: every Q-move bounces
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_fp64_matches_oracle(T, oracle_mod, case):
+    from paper_2201_10132_gb300.inputs import perturbation
+    nx, ny, S, R, re, wi, beta, kp, tau2, ic, steps = case
+    pert = perturbation(nx, ny, 7, 0.05, 0.05) if nx * ny > 1 else None
+    p = T.Params(nx, ny, S, R, re, wi, beta, 0.05, kp, tau2, 0.0, ic, T.FP64)
+    o = _oracle_run(oracle_mod, nx, ny, S, R, re, wi, beta, kp, tau2, pert, ic, steps)
+    with T.Solver(p, pert) as s:
+        assert s.info["nq"] == o.nq
+        s.step(steps)
+        g = s.moments()
+        psi = s.psi()
+        pops = s.populations()
+        diag = s.diagnostics()
+    f = o.fields(with_psi=True)
+    for k in FIELDS:
+        assert _rel(g[k], f[k]) < 1e-12, (k, _rel(g[k], f[k]))
+    assert _rel(psi, f["psi"]) < 1e-12
+    # stored populations: the oracle's post-collision g' of the last step
+    hs, hp = o.get_gpost()
+    c9, c25 = T.lattice()
+    oc9, _, _ = oracle_mod.d2q9()
+    oc25, _, _ = oracle_mod.d4q25()
+    m9 = [next(j for j in range(9) if (oc9[j] == c9[i]).all()) for i in range(9)]
+    m25 = [next(j for j in range(25) if (oc25[j] == c25[i]).all()) for i in range(25)]
+    ref = np.concatenate([hs[..., m9].transpose(2, 0, 1),
+                          hp[..., m25].transpose(2, 3, 0, 1).reshape(25 * o.nq, ny, nx)])
+    assert _rel(pops[:9], ref[:9]) < 1e-12
+    if o.lat.psi_tot > 0:
+        assert _rel(pops[9:], ref[9:]) < 1e-12
+    od = o.diagnostics()
+    for k in ("mass_s", "mass_p", "ke", "enstrophy", "qrms_mean", "ey2"):
+        assert diag[k] == pytest.approx(od[k], rel=1e-12, abs=1e-300), k
+    for k in ("px", "py"):
+        assert diag[k] == pytest.approx(od[k], rel=1e-9, abs=1e-13 * max(1.0, od["mass_s"])), k
+
+
+@pytest.mark.parametrize("case", [CASES[1], CASES[2], CASES[3]])
+def test_fp32_within_tolerance(T, oracle_mod, case):
+    from paper_2201_10132_gb300.inputs import perturbation
+    nx, ny, S, R, re, wi, beta, kp, tau2, ic, steps = case
+    pert = perturbation(nx, ny, 7, 0.05, 0.05)
+    p = T.Params(nx, ny, S, R, re, wi, beta, 0.05, kp, tau2, 0.0, ic, T.FP32)
+    o = _oracle_run(oracle_mod, nx, ny, S, R, re, wi, beta, kp, tau2, pert, ic, steps)
+    with T.Solver(p, pert) as s:
+        s.step(steps)
+        g = s.moments()
+    f = o.fields()
+    uscale = max(np.abs(f["ux"]).max(), np.abs(f["uy"]).max())
+    for k in FIELDS:
+        # velocity-derived fields are measured against the velocity scale
+        scale = uscale if k in ("ux", "uy", "vort") else np.abs(f[k]).max()
+        err = np.abs(g[k] - f[k]).max() / scale
+        assert err < 2e-5, (k, err)
+
+
+def test_full_size_tiled_matches_oracle(T, oracle_mod):
+    """The 4096^2, N_Q = 32 throughput workload in its benchmark launch configuration
+    (FP32), started from a perturbation that repeats every 64 nodes: with the
+    forcing period also 64 nodes, the solution is the 64^2 oracle run tiled 64 x 64
+    times, so every node of the full-size launch is checked."""
+    import torch
+    from paper_2201_10132_gb300.inputs import KOLMOGOROV_4096 as W, perturbation
+    n0 = 64
+    steps = 6
+    small = perturbation(n0, n0, 11, 1e-2, W.u0)
+    pert = np.tile(small, (1, W.ny // n0, W.nx // n0))
+    p = T.Params.from_workload(W, T.FP32)
+    ws = torch.empty(T.required_bytes(p), dtype=torch.uint8, device="cuda")
+    with T.Solver(p, pert, workspace=ws) as s:
+        assert s.info["nq"] == 32
+        s.step(steps)
+        g = s.moments(["ux", "uy", "rho_s", "cxy"])
+    o = _oracle_run(oracle_mod, n0, n0, W.q_side, W.q_radius, W.re, W.wi, W.beta, 1, 0.0, small,
+                    0, steps)
+    f = o.fields()
+    uscale = max(np.abs(f["ux"]).max(), np.abs(f["uy"]).max())
+    for k in ("ux", "uy", "rho_s", "cxy"):
+        ref = np.tile(f[k], (W.ny // n0, W.nx // n0))
+        scale = uscale if k in ("ux", "uy") else np.abs(ref).max()
+        err = np.abs(g[k] - ref).max() / scale
+        assert err < 2e-5, (k, err)
+    del ws
+    torch.cuda.empty_cache()
+
+
+def test_caller_workspace_and_stream(T, oracle_mod):
+    import torch
+    from paper_2201_10132_gb300.inputs import perturbation
+    nx, ny = 40, 24
+    pert = perturbation(nx, ny, 2, 0.05, 0.05)
+    p = T.Params(nx, ny, 6, 3.0, 5.0, 0.5, 0.2, 0.05, 1, ic_mode=1, precision=T.FP64)
+    ws = torch.empty(T.required_bytes(p), dtype=torch.uint8, device="cuda")
+    st = torch.cuda.Stream()
+    with T.Solver(p, pert, workspace=ws, stream=st.cuda_stream) as s:
+        s.step(5)
+        g = s.moments(["ux"])
+    with T.Solver(p, pert) as s2:
+        s2.step(5)
+        h = s2.moments(["ux"])
+    assert np.array_equal(g["ux"], h["ux"])  # deterministic, independent of the stream
+
+
+def test_workspace_too_small(T):
+    import torch
+    p = T.Params(32, 32, 4, 2.0, 5.0, 0.5, 0.2)
+    ws = torch.empty(T.required_bytes(p) // 2, dtype=torch.uint8, device="cuda")
+    with pytest.raises(T.TfktError) as e:
+        T.Solver(p, None, workspace=ws)
+    assert e.value.status == 2
