@@ -155,6 +155,40 @@ tfkt_status tfkt_diagnostics(tfkt_ctx* ctx, double* out);
    order), then plane 9 + 25 q + i for the polymer. Synchronises. */
 tfkt_status tfkt_populations(tfkt_ctx* ctx, double* host_dst, size_t bytes);
 
+/* Macroscopic fields without any device allocation. The paper has no
+   counterpart of this call; it exists for callers that may not allocate GPU
+   memory at the point where they need the fields: code inside a fixed-size
+   memory arena or pool whose budget is already spoken for, or a host
+   framework that forbids entering the allocator from that point. It computes
+   the same fields as tfkt_moments from a population buffer the caller
+   passes; its scratch (moment planes, velocity planes, lattice tables) is one
+   static device array of TFKT_NOALLOC_SCRATCH_BYTES that every GPU loading
+   the library holds until the process exits.
+   p:      the run's parameters (as given to tfkt_create).
+   pops:   device pointer to a population buffer in a context's storage
+           layout. A context created on workspace W keeps its state, after
+           n steps, at W + (n mod 2) * B with B = the population bytes
+           (9 + 25 nq) * ny * pitch * element size rounded up to 256
+           (nq, pitch from tfkt_get_info; element size 8 for TFKT_FP64,
+           4 for TFKT_FP32).
+   dst:    device pointer, popcount(field_mask) * ny * nx doubles; bytes is
+           its size.
+   stream: cudaStream_t or NULL. The lattice tables are copied from host
+           memory and the stream is synchronised once before the kernels are
+           queued; the kernels then run asynchronously on the stream.
+   Errors: TFKT_EINVAL for invalid parameters, pointers or mask, and when the
+           grid needs more scratch than TFKT_NOALLOC_SCRATCH_BYTES (the
+           message gives both sizes); TFKT_ECUDA if a CUDA call fails.
+   The first call on a device looks up the address of the static array on
+   that device (with the device current); make that first call before any
+   stream capture. All calls share the one array, which keeps what the last
+   call left in it; every value a call reads from it is written by the same
+   call first, so nothing needs clearing. Calls whose work overlaps on the
+   GPU (other streams, other threads) race on the array. */
+#define TFKT_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+tfkt_status tfkt_moments_noalloc(const tfkt_params* p, const void* pops, uint32_t field_mask,
+                                 double* dst, size_t bytes, void* stream);
+
 tfkt_status tfkt_get_info(const tfkt_ctx* ctx, tfkt_info* info);
 
 /* Velocity ordering of the library: c9[9][2] (D2Q9), c25[25][4] (D4Q25 on

@@ -12,7 +12,6 @@
 #include "tfkt_internal.cuh"
 
 namespace tfkt {
-namespace {
 
 thread_local std::string g_last_error;
 
@@ -137,11 +136,6 @@ size_t layout(const Lattice& L, Workspace* w) {
   return o;
 }
 
-struct HostTables {
-  std::vector<double> qx, qy, psi0, delta, arow, urow;
-  std::vector<int> pull;
-};
-
 int opposite25(int i) {
   const V4 c = c25(i);
   for (int j = 0; j < 25; ++j) {
@@ -198,6 +192,8 @@ HostTables build_tables(const Lattice& L) {
   }
   return t;
 }
+
+namespace {
 
 template <typename real>
 KernelArgs<real> make_args(const Ctx* c, const HostTables* ht = nullptr) {

@@ -7,6 +7,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include "tfkt.h"
 
@@ -120,6 +121,17 @@ struct Ctx {
   int64_t step = 0;
   int diag_blocks = 0;
 };
+
+// Host helpers (tfkt_api.cu).
+tfkt_status fail(tfkt_status s, const std::string& msg);
+size_t align_up(size_t v, size_t a);
+tfkt_status map_params(const tfkt_params* p, Lattice* L);
+size_t real_size(const Lattice& L);
+struct HostTables {
+  std::vector<double> qx, qy, psi0, delta, arow, urow;
+  std::vector<int> pull;
+};
+HostTables build_tables(const Lattice& L);
 
 // Launchers (tfkt_kernels.cu). Each returns the launch status.
 template <typename real>

@@ -96,6 +96,9 @@ def lib() -> ctypes.CDLL:
         L.tfkt_step_profiled.argtypes = [P, ctypes.c_int64, D, ctypes.POINTER(ctypes.c_int64)]
         L.tfkt_moments.argtypes = [P, ctypes.c_uint32, P, ctypes.c_size_t, ctypes.c_int]
         L.tfkt_psi.argtypes = [P, P, ctypes.c_size_t, ctypes.c_int]
+        L.tfkt_moments_noalloc.argtypes = [ctypes.POINTER(_Params), P, ctypes.c_uint32, P,
+                                           ctypes.c_size_t, P]
+        L.tfkt_moments_noalloc.restype = S
         L.tfkt_diagnostics.argtypes = [P, D]
         L.tfkt_populations.argtypes = [P, D, ctypes.c_size_t]
         L.tfkt_get_info.argtypes = [P, ctypes.POINTER(_Info)]
@@ -136,6 +139,14 @@ def lattice():
     _check(lib().tfkt_lattice(c9.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                               c25.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))), "tfkt_lattice")
     return c9, c25
+
+
+def moments_noalloc(p: Params, pops_ptr: int, mask: int, dst_ptr: int, dst_bytes: int,
+                    stream: int | None = None):
+    """tfkt_moments_noalloc: fields from a device population buffer into device memory,
+    using the library's static scratch instead of any allocation."""
+    _check(lib().tfkt_moments_noalloc(ctypes.byref(p._c()), pops_ptr, mask, dst_ptr, dst_bytes,
+                                      stream), "tfkt_moments_noalloc")
 
 
 def field_mask(names) -> int:
