@@ -87,7 +87,9 @@ typedef struct tfkt_ctx tfkt_ctx;
 /* Kernels timed by tfkt_step_profiled. */
 enum {
   TFKT_K_MOMENTS = 0,  /* pull-read of all populations -> moment planes */
-  TFKT_K_STEP,         /* pull, collide and write of all populations */
+  TFKT_K_STEP,         /* two-pass path: pull, collide and write of all populations */
+  TFKT_K_FUSED,        /* fused path: pull, collide, write and next-step moments */
+  TFKT_K_FIXUP,        /* fused path: completion of the tiles' border moments */
   TFKT_NKERNELS
 };
 

@@ -133,6 +133,14 @@ size_t layout(const Lattice& L, Workspace* w) {
   o = align_up(o + (size_t)diag_blocks_for(L) * TFKT_NDIAG * sizeof(double), A);
   w->off_diag = o;
   o = align_up(o + TFKT_NDIAG * sizeof(double), A);
+  if (fused_supported(L.nx, L.ny, L.nq, sz)) {
+    w->off_M2 = o;
+    o = align_up(o + (size_t)L.nm * L.plane * sz, A);
+    w->off_exp = o;
+    o = align_up(o + fused_export_elems(L.nx, L.ny, L.nq) * sz, A);
+    w->off_ftab = o;
+    o = align_up(o + (size_t)L.nq * (9 * sizeof(int) + sz) + A, A);
+  }
   return o;
 }
 
@@ -202,7 +210,7 @@ KernelArgs<real> make_args(const Ctx* c, const HostTables* ht = nullptr) {
   KernelArgs<real> a{};
   a.src = (const real*)(base + c->ws.off_pop[c->cur]);
   a.dst = (real*)(base + c->ws.off_pop[c->cur ^ 1]);
-  a.M = (real*)(base + c->ws.off_M);
+  a.M = (real*)(base + (c->mcur ? c->ws.off_M2 : c->ws.off_M));
   a.U = (real*)(base + c->ws.off_U);
   a.perturb = nullptr;
   a.nx = L.nx;
@@ -246,6 +254,35 @@ KernelArgs<real> make_args(const Ctx* c, const HostTables* ht = nullptr) {
 }
 
 template <typename real>
+FusedArgs<real> make_fused(const Ctx* c) {
+  const Lattice& L = c->L;
+  char* base = (char*)c->ws.base;
+  FusedArgs<real> f{};
+  f.Min = (const real*)(base + (c->mcur ? c->ws.off_M2 : c->ws.off_M));
+  f.Mout = (real*)(base + (c->mcur ? c->ws.off_M : c->ws.off_M2));
+  f.exports = (real*)(base + c->ws.off_exp);
+  f.tgt = (const int*)(base + c->ws.off_ftab);
+  f.dpsi = (const real*)(base + c->ws.off_ftab + align_up((size_t)L.nq * 9 * sizeof(int), 256));
+  f.dvx = (real)c->dvx;
+  f.dvy = (real)c->dvy;
+  return f;
+}
+
+template <typename real>
+tfkt_status upload_fused_tables(Ctx* c, const HostTables& t) {
+  std::vector<int> tgt;
+  std::vector<double> dpsi;
+  fused_tables(c->L, t, tgt, dpsi, c->dvx, c->dvy);
+  FusedArgs<real> f = make_fused<real>(c);
+  std::vector<real> d(dpsi.begin(), dpsi.end());
+  TFKT_CUDA(c, cudaMemcpy((void*)f.tgt, tgt.data(), tgt.size() * sizeof(int),
+                          cudaMemcpyHostToDevice));
+  TFKT_CUDA(c, cudaMemcpy((void*)f.dpsi, d.data(), d.size() * sizeof(real),
+                          cudaMemcpyHostToDevice));
+  return TFKT_OK;
+}
+
+template <typename real>
 tfkt_status upload_tables(Ctx* c, const HostTables& t) {
   KernelArgs<real> a = make_args<real>(c);
   auto put = [&](const void* dptr, const std::vector<double>& v) -> cudaError_t {
@@ -260,6 +297,7 @@ tfkt_status upload_tables(Ctx* c, const HostTables& t) {
   TFKT_CUDA(c, put(a.tab.delta, t.delta));
   TFKT_CUDA(c, put(a.tab.arow, t.arow));
   TFKT_CUDA(c, put(a.tab.urow, t.urow));
+  if (c->fused) return upload_fused_tables<real>(c, t);
   return TFKT_OK;
 }
 
@@ -294,15 +332,25 @@ tfkt_status ensure_moments(Ctx* c) {
   return TFKT_OK;
 }
 
+// One step. Fused path: the step kernel also produces the next state's
+// moment planes (completed at tile borders by the fix-up kernel), so the
+// moments stay valid. Two-pass path: moments kernel, then the step kernel.
 template <typename real>
 tfkt_status do_step(Ctx* c, int64_t n) {
   for (int64_t k = 0; k < n; ++k) {
     tfkt_status s = ensure_moments<real>(c);
     if (s != TFKT_OK) return s;
     KernelArgs<real> a = make_args<real>(c);
-    TFKT_CUDA(c, launch_step<real>(a, c->stream));
+    if (c->fused) {
+      FusedArgs<real> f = make_fused<real>(c);
+      TFKT_CUDA(c, launch_step_fused<real>(a, f, c->stream));
+      TFKT_CUDA(c, launch_fixup<real>(a, f, c->stream));
+      c->mcur ^= 1;
+    } else {
+      TFKT_CUDA(c, launch_step<real>(a, c->stream));
+      c->m_valid = false;
+    }
     c->cur ^= 1;
-    c->m_valid = false;
     ++c->step;
   }
   return TFKT_OK;
@@ -311,16 +359,16 @@ tfkt_status do_step(Ctx* c, int64_t n) {
 // tfkt_step with an event pair around each launch (profiling only).
 template <typename real>
 tfkt_status do_step_profiled(Ctx* c, int64_t n, double* ms, int64_t* launches) {
-  cudaEvent_t ev[2 * 2];
+  cudaEvent_t ev[2 * TFKT_NKERNELS];
   for (auto& e : ev) TFKT_CUDA(c, cudaEventCreate(&e));
   struct Guard {
     cudaEvent_t* e;
     ~Guard() {
-      for (int k = 0; k < 4; ++k) cudaEventDestroy(e[k]);
+      for (int k = 0; k < 2 * TFKT_NKERNELS; ++k) cudaEventDestroy(e[k]);
     }
   } guard{ev};
-  double acc[TFKT_NKERNELS] = {0, 0};
-  int64_t cnt[TFKT_NKERNELS] = {0, 0};
+  double acc[TFKT_NKERNELS] = {};
+  int64_t cnt[TFKT_NKERNELS] = {};
   auto timed = [&](int kind, auto&& launch) -> tfkt_status {
     TFKT_CUDA(c, cudaEventRecord(ev[2 * kind], c->stream));
     TFKT_CUDA(c, launch());
@@ -340,10 +388,20 @@ tfkt_status do_step_profiled(Ctx* c, int64_t n, double* ms, int64_t* launches) {
       c->m_valid = true;
     }
     KernelArgs<real> a = make_args<real>(c);
-    tfkt_status s = timed(TFKT_K_STEP, [&] { return launch_step<real>(a, c->stream); });
-    if (s != TFKT_OK) return s;
+    if (c->fused) {
+      FusedArgs<real> f = make_fused<real>(c);
+      tfkt_status s =
+          timed(TFKT_K_FUSED, [&] { return launch_step_fused<real>(a, f, c->stream); });
+      if (s != TFKT_OK) return s;
+      s = timed(TFKT_K_FIXUP, [&] { return launch_fixup<real>(a, f, c->stream); });
+      if (s != TFKT_OK) return s;
+      c->mcur ^= 1;
+    } else {
+      tfkt_status s = timed(TFKT_K_STEP, [&] { return launch_step<real>(a, c->stream); });
+      if (s != TFKT_OK) return s;
+      c->m_valid = false;
+    }
     c->cur ^= 1;
-    c->m_valid = false;
     ++c->step;
   }
   for (int j = 0; j < TFKT_NKERNELS; ++j) {
@@ -462,6 +520,7 @@ tfkt_status tfkt_create(const tfkt_params* p, const double* perturb, void* dev_w
   if (!c) return fail(TFKT_ENOMEM, "host allocation failed");
   c->L = L;
   c->stream = (cudaStream_t)stream;
+  c->fused = fused_supported(L.nx, L.ny, L.nq, real_size(L));
   const size_t need = layout(L, &c->ws);
   c->diag_blocks = diag_blocks_for(L);
   if (dev_workspace) {

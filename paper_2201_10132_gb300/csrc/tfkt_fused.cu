@@ -1,0 +1,574 @@
+// Fused single-pass step: pull-stream, moments, collision and write-back of
+// every population of a 32 x 8 tile, plus the moment planes of the NEXT step,
+// in one read and one write of the populations (Sec. VI-C update; moments of
+// Sec. VI-A / VI-B; elastic stress of Sec. III).
+//
+// The next step's moments of node y are sums of post-collision populations
+// arriving at y: g'_i(y - c_r, q) lands on (y, q + Qdot_i), or bounces back to
+// (y, q) as the opposite velocity when q + Qdot_i leaves the Q-disk. A tile
+// writes its post-collision values into shared memory and every thread sums,
+// in a fixed order, the arrivals at its own node from sources inside the tile;
+// 84 threads do the same for the ring of nodes around the tile. Arrivals from
+// neighbouring tiles reach a border node through those tiles' ring exports,
+// which the fix-up kernel adds in a fixed order. No atomics: results do not
+// depend on scheduling.
+//
+// M planes written for step n+1: interior nodes get final values (delta psi,
+// delta rho, J, delta Theta); border nodes get the tile's raw partial sums in
+// the delta psi, delta rho and J planes, completed by the fix-up kernel.
+#include <type_traits>
+#include <utility>
+
+#include "tfkt_internal.cuh"
+
+namespace tfkt {
+namespace {
+
+// Calls f(std::integral_constant<int, B + k>) for k = 0 .. N-1: a loop whose
+// index is a compile-time constant in the body.
+template <int B, typename F, int... Is>
+__device__ __forceinline__ void static_for_impl(F&& f, std::integer_sequence<int, Is...>) {
+  (f(std::integral_constant<int, B + Is>{}), ...);
+}
+template <int B, int N, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+  static_for_impl<B>(f, std::make_integer_sequence<int, N>{});
+}
+
+constexpr int NT = TX * TY;                  // threads / nodes per tile
+constexpr int RING = 2 * (TX + 2) + 2 * TY;  // ring nodes around a tile
+
+// Ring position of frame coordinates (ex, ey) in [-1, TX] x [-1, TY] \ tile.
+__host__ __device__ constexpr int ring_pos(int ex, int ey) {
+  return ey == -1 ? ex + 1
+       : ey == TY ? TX + 3 + ex
+       : ex == -1 ? 2 * TX + 4 + ey
+                  : 2 * TX + 4 + TY + ey;
+}
+__device__ __forceinline__ void ring_coords(int k, int& ex, int& ey) {
+  if (k < TX + 2) { ex = k - 1; ey = -1; }
+  else if (k < 2 * TX + 4) { ex = k - (TX + 3); ey = TY; }
+  else if (k < 2 * TX + 4 + TY) { ex = -1; ey = k - (2 * TX + 4); }
+  else { ex = TX; ey = k - (2 * TX + 4 + TY); }
+}
+
+// Q-displacement group of a velocity: (qy + 1) * 3 + (qx + 1); 4 = no Q motion.
+__host__ __device__ constexpr int qgroup(const V4 c) { return (c.qy + 1) * 3 + (c.qx + 1); }
+__host__ __device__ constexpr int qgroup9(int cx, int cy) { return (cy + 1) * 3 + (cx + 1); }
+
+__device__ __forceinline__ bool in_tile(int x, int y) {
+  return x >= 0 && x < TX && y >= 0 && y < TY;
+}
+
+// Adds s * v for a compile-time s in {-1, 0, 1} (no multiply by a zero
+// coefficient, which IEEE arithmetic would not let the compiler drop).
+template <int S, typename real>
+__device__ __forceinline__ void acc(real& sum, real v) {
+  if constexpr (S == 1) sum += v;
+  else if constexpr (S == -1) sum -= v;
+}
+
+// Velocities 1..20 move in r (they reach other r-nodes); 0 and 21..24 do not.
+__host__ __device__ constexpr bool moves_r(int i) { return i >= 1 && i <= 20; }
+__host__ __device__ constexpr int rbit(int cx, int cy) { return (cy + 1) * 3 + (cx + 1); }
+
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
+}
+template <typename real>
+__device__ __forceinline__ void cp_async(real* smem, const real* gmem) {
+  if constexpr (sizeof(real) == 4) cp_async4(smem, gmem);
+  else cp_async8(smem, gmem);
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+constexpr int NSTAGE = 25 + 4;  // the 25 pulled populations and 4 neighbour psi of one Q-node
+
+template <typename real>
+struct Smem {
+  real* st;      // [NSTAGE][NT] prefetched inputs of the next Q-node (each thread its own column)
+  real* hb;      // [20][NT] post-collision values of the r-moving velocities
+  real* A;       // [nq][NT] own-node arrival sums per Q-node
+  real* Ar;      // [nq][RING] ring-node arrival sums per Q-node
+  real* Ux;      // [TY+2][TX+2]
+  real* Uy;
+  real* delta;   // [nq*25] pull shift differences
+  int* tgt;      // [nq][9] target Q-node of each Q-displacement group, -1: bounce-back
+  int* pull;     // [nq*25] pull source plane (>= 0) or ~plane for bounce-back
+};
+
+template <typename real>
+__device__ __forceinline__ Smem<real> carve(void* base, int nq) {
+  Smem<real> s;
+  real* p = (real*)base;
+  s.st = p; p += NSTAGE * NT;
+  s.hb = p; p += 20 * NT;
+  s.A = p; p += (size_t)nq * NT;
+  s.Ar = p; p += (size_t)nq * RING;
+  s.Ux = p; p += (TY + 2) * (TX + 2);
+  s.Uy = p; p += (TY + 2) * (TX + 2);
+  s.delta = p; p += (size_t)nq * 25;
+  s.tgt = (int*)p;
+  s.pull = s.tgt + (size_t)nq * 9;
+  return s;
+}
+
+template <typename real>
+__device__ __forceinline__ void velocity_at(const KernelArgs<real>& a, const real* M, int x, int y,
+                                            real& ux, real& uy) {
+  const int nq = a.nq;
+  const size_t P = a.plane;
+  const int xm = x == 0 ? a.nx - 1 : x - 1, xp = x == a.nx - 1 ? 0 : x + 1;
+  const int ym = y == 0 ? a.ny - 1 : y - 1, yp = y == a.ny - 1 ? 0 : y + 1;
+  const size_t n = (size_t)y * a.pitch + x;
+  const size_t nxm = (size_t)y * a.pitch + xm, nxp = (size_t)y * a.pitch + xp;
+  const size_t nym = (size_t)ym * a.pitch + x, nyp = (size_t)yp * a.pitch + x;
+  const real* Txx = M + (size_t)(nq + M_THXX) * P;
+  const real* Txy = M + (size_t)(nq + M_THXY) * P;
+  const real* Tyy = M + (size_t)(nq + M_THYY) * P;
+  const real rho = a.rho0 + M[(size_t)(nq + M_DRHO) * P + n];
+  const real jx = M[(size_t)(nq + M_JX) * P + n];
+  const real jy = M[(size_t)(nq + M_JY) * P + n];
+  const real ex = real(0.5) * (Txx[nxp] - Txx[nxm]) + real(0.5) * (Txy[nyp] - Txy[nym]);
+  const real ey = real(0.5) * (Txy[nxp] - Txy[nxm]) + real(0.5) * (Tyy[nyp] - Tyy[nym]);
+  const real f = a.tab.arow[y];
+  ux = (jx + real(0.5) * (ex + rho * f)) / rho;
+  uy = (jy + real(0.5) * ey) / rho;
+}
+
+// Queues the copies of Q-node q's inputs into this thread's stage column.
+template <typename real>
+__device__ __forceinline__ void prefetch_q(const Smem<real>& sm, const real* src, const real* Min,
+                                           size_t P, const uint32_t* off, int q, int tid) {
+#pragma unroll
+  for (int i = 0; i < 25; ++i) {
+    const V4 cv = c25(i);
+    const int e = sm.pull[q * 25 + i];
+    const uint32_t o = e >= 0 ? off[shift_index(-cv.rx, -cv.ry)] : off[4];
+    const int pl = e >= 0 ? e : ~e;
+    cp_async(sm.st + i * NT + tid, src + (size_t)pl * P + o);
+  }
+  const real* Mq = Min + (size_t)q * P;
+  cp_async(sm.st + 25 * NT + tid, Mq + off[5]);
+  cp_async(sm.st + 26 * NT + tid, Mq + off[3]);
+  cp_async(sm.st + 27 * NT + tid, Mq + off[7]);
+  cp_async(sm.st + 28 * NT + tid, Mq + off[1]);
+  cp_async_commit();
+}
+
+template <typename real>
+__global__ void __launch_bounds__(NT, 2)
+step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nq = a.nq;
+  Smem<real> sm = carve<real>(smem_raw, nq);
+  const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * TX + lx;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int x = x0 + lx, y = y0 + ly;
+  const size_t P = a.plane;
+  const real* __restrict__ Min = fa.Min;
+  real* __restrict__ Mout = fa.Mout;
+  const real* __restrict__ src = a.src;
+  real* __restrict__ dst = a.dst;
+
+  // pull offsets within a plane (32-bit: a plane holds < 2^31 elements)
+  const int xm = x == 0 ? a.nx - 1 : x - 1, xp = x == a.nx - 1 ? 0 : x + 1;
+  const int ym = y == 0 ? a.ny - 1 : y - 1, yp = y == a.ny - 1 ? 0 : y + 1;
+  const int pitch = (int)a.pitch;
+  uint32_t off[9];
+  off[0] = ym * pitch + xm; off[1] = ym * pitch + x; off[2] = ym * pitch + xp;
+  off[3] = y * pitch + xm;  off[4] = y * pitch + x;  off[5] = y * pitch + xp;
+  off[6] = yp * pitch + xm; off[7] = yp * pitch + x; off[8] = yp * pitch + xp;
+  const uint32_t n = off[4];
+
+  // ---- stage: tables, zeroed accumulators, U on the tile and its 1-node ring
+  for (int k = tid; k < nq * 9; k += NT) sm.tgt[k] = fa.tgt[k];
+  for (int k = tid; k < nq * 25; k += NT) {
+    sm.pull[k] = a.tab.pull[k];
+    sm.delta[k] = a.tab.delta[k];
+  }
+  for (int p = 0; p < nq; ++p) sm.A[p * NT + tid] = real(0);
+  for (int k = tid; k < nq * RING; k += NT) sm.Ar[k] = real(0);
+  for (int k = tid; k < (TX + 2) * (TY + 2); k += NT) {
+    const int hx = k % (TX + 2), hy = k / (TX + 2);
+    int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
+    gx = gx < 0 ? gx + a.nx : (gx >= a.nx ? gx - a.nx : gx);
+    gy = gy < 0 ? gy + a.ny : (gy >= a.ny ? gy - a.ny : gy);
+    real ux, uy;
+    velocity_at(a, Min, gx, gy, ux, uy);
+    sm.Ux[k] = ux;
+    sm.Uy[k] = uy;
+  }
+  __syncthreads();
+  prefetch_q(sm, src, Min, P, off, 0, tid);   // overlaps the solvent work
+
+  const int c = (ly + 1) * (TX + 2) + (lx + 1);
+  const real Ux = sm.Ux[c], Uy = sm.Uy[c];
+  const real G00 = real(0.5) * (sm.Ux[c + 1] - sm.Ux[c - 1]);                    // d_x U_x
+  const real G01 = real(0.5) * (sm.Uy[c + 1] - sm.Uy[c - 1]);                    // d_x U_y
+  const real G10 = real(0.5) * (sm.Ux[c + TX + 2] - sm.Ux[c - TX - 2]);          // d_y U_x
+  const real G11 = real(0.5) * (sm.Uy[c + TX + 2] - sm.Uy[c - TX - 2]);          // d_y U_y
+
+  // sources inside the tile, per r-displacement: own node and (threads < RING) ring node
+  uint32_t vmask = 0, rmask = 0;
+  const bool ring_thread = tid < RING;
+  int rex = 0, rey = 0;
+  if (ring_thread) ring_coords(tid, rex, rey);
+#pragma unroll
+  for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+    for (int dx = -1; dx <= 1; ++dx) {
+      if (in_tile(lx - dx, ly - dy)) vmask |= 1u << rbit(dx, dy);
+      if (ring_thread && in_tile(rex - dx, rey - dy)) rmask |= 1u << rbit(dx, dy);
+    }
+  const int rbase = rey * TX + rex;
+
+  const real rho = a.rho0 + Min[(size_t)(nq + M_DRHO) * P + n];
+  const real force = rho * a.tab.arow[y];
+  real jx_arr = 0, jy_arr = 0, ms_arr = 0;    // own-node arrivals (momentum, solvent mass)
+  real jx_r = 0, jy_r = 0, ms_r = 0;          // ring-node arrivals
+
+  // ---- solvent
+  {
+    real h[9];
+    real drs = 0, jsx = 0, jsy = 0;
+    static_for<0, 9>([&](auto I) {
+      constexpr int i = I;
+      h[i] = src[(size_t)i * P + off[shift_index(-c9x(i), -c9y(i))]];
+      drs += h[i];
+      acc<c9x(i)>(jsx, h[i]);
+      acc<c9y(i)>(jsy, h[i]);
+    });
+    const real rs = real(1) + drs;
+    const real jfx = (a.c2 * jsx + rs * Ux + a.tau2 * force) * a.inv_c2p1;
+    const real jfy = (a.c2 * jsy + rs * Uy) * a.inv_c2p1;
+    const real usx = jfx / rs, usy = jfy / rs;
+    const real vx = a.omr * usx + a.r * Ux, vy = a.omr * usy + a.r * Uy;
+    const real sq = a.omr * (usx * usx + usy * usy) + a.r * (Ux * Ux + Uy * Uy);
+    static_for<0, 9>([&](auto I) {
+      constexpr int i = I;
+      real cus = 0, cu = 0, cv = 0;
+      acc<c9x(i)>(cus, usx); acc<c9y(i)>(cus, usy);
+      acc<c9x(i)>(cu, Ux);   acc<c9y(i)>(cu, Uy);
+      acc<c9x(i)>(cv, vx);   acc<c9y(i)>(cv, vy);
+      // Guo source (3 (c - U) + 9 (c . U) c) . (force, 0)
+      real gx = -real(3) * Ux;
+      acc<c9x(i)>(gx, real(3) + real(9) * cu);
+      const real feq_dev = real(w9(i)) * (drs + rs * (real(3) * cv +
+                                                      real(4.5) * (a.omr * cus * cus + a.r * cu * cu) -
+                                                      real(1.5) * sq));
+      const real hp = a.om2b * h[i] + a.tb * feq_dev + a.omb * real(w9(i)) * gx * force;
+      dst[(size_t)i * P + n] = hp;
+      if constexpr (i == 0) ms_arr += hp;
+      else sm.hb[(i - 1) * NT + tid] = hp;
+    });
+  }
+  __syncthreads();
+  static_for<1, 8>([&](auto I) {
+    constexpr int i = I;
+    constexpr int k = rbit(c9x(i), c9y(i));
+    if ((vmask >> k) & 1u) {
+      const real v = sm.hb[(i - 1) * NT + tid - (c9y(i) * TX + c9x(i))];
+      ms_arr += v;
+      acc<c9x(i)>(jx_arr, v);
+      acc<c9y(i)>(jy_arr, v);
+    }
+  });
+  if (ring_thread) {
+    static_for<1, 8>([&](auto I) {
+      constexpr int i = I;
+      constexpr int k = rbit(c9x(i), c9y(i));
+      if ((rmask >> k) & 1u) {
+        const real v = sm.hb[(i - 1) * NT + rbase - (c9y(i) * TX + c9x(i))];
+        ms_r += v;
+        acc<c9x(i)>(jx_r, v);
+        acc<c9y(i)>(jy_r, v);
+      }
+    });
+  }
+  __syncthreads();
+
+  // ---- polymer, one Q-node at a time; the next Q-node's inputs are in flight meanwhile
+  for (int q = 0; q < nq; ++q) {
+    cp_async_wait_all();
+    real h[25];
+#pragma unroll
+    for (int i = 0; i < 25; ++i) h[i] = sm.st[i * NT + tid] + sm.delta[q * 25 + i];
+    const real dpx = real(0.5) * (sm.st[25 * NT + tid] - sm.st[26 * NT + tid]);
+    const real dpy = real(0.5) * (sm.st[27 * NT + tid] - sm.st[28 * NT + tid]);
+    if (q + 1 < nq) prefetch_q(sm, src, Min, P, off, q + 1, tid);
+
+    int tg[9];
+    uint32_t bm = 0;
+#pragma unroll
+    for (int g = 0; g < 9; ++g) {
+      tg[g] = sm.tgt[q * 9 + g];
+      if (tg[g] < 0) bm |= 1u << g;
+    }
+    real dpsi = 0, rx = 0, ry = 0, qx = 0, qy = 0;
+    static_for<0, 25>([&](auto I) {
+      constexpr int i = I;
+      dpsi += h[i];
+      acc<c25(i).rx>(rx, h[i]);
+      acc<c25(i).ry>(ry, h[i]);
+      acc<c25(i).qx>(qx, h[i]);
+      acc<c25(i).qy>(qy, h[i]);
+    });
+    const real Qx = a.tab.qx[q], Qy = a.tab.qy[q];
+    const real psi = a.tab.psi0[q] + dpsi;
+    const real qg = Qx * dpx + Qy * dpy;
+    const real jrex = psi * Ux + a.tau2 * a.hl2h * Qx * qg;
+    const real jrey = psi * Uy + a.tau2 * a.hl2h * Qy * qg;
+    const real jqex = psi * (Qx * G00 + Qy * G10 - a.kappa * Qx);
+    const real jqey = psi * (Qx * G01 + Qy * G11 - a.kappa * Qy);
+    // 3 x the momenta of the mixed equilibrium (1 - r) f* + r f^eq
+    const real mrx = real(3) * (a.omr * (a.c2 * rx + jrex) * a.inv_c2p1 + a.r * jrex);
+    const real mry = real(3) * (a.omr * (a.c2 * ry + jrey) * a.inv_c2p1 + a.r * jrey);
+    const real mqx = real(3) * (a.omr * (a.c2 * qx + jqex) * a.inv_c2p1 + a.r * jqex);
+    const real mqy = real(3) * (a.omr * (a.c2 * qy + jqey) * a.inv_c2p1 + a.r * jqey);
+    real* dq = dst + (size_t)(9 + 25 * q) * P + n;
+    real grp[9];
+#pragma unroll
+    for (int g = 0; g < 9; ++g) grp[g] = real(0);
+    static_for<0, 25>([&](auto I) {
+      constexpr int i = I;
+      real d = dpsi;
+      acc<c25(i).rx>(d, mrx);
+      acc<c25(i).ry>(d, mry);
+      acc<c25(i).qx>(d, mqx);
+      acc<c25(i).qy>(d, mqy);
+      const real hp = a.om2b * h[i] + a.tb * real(w25(i)) * d;
+      dq[(size_t)i * P] = hp;
+      constexpr int g = qgroup(c25(i));
+      if constexpr (!moves_r(i)) {
+        // stays at this r-node: lands on Q-node q + Qdot, or bounces back to q
+        if ((bm >> g) & 1u) grp[4] += hp;
+        else grp[g] += hp;
+      } else {
+        if ((bm >> g) & 1u) {
+          // bounces back to (r, q) moving with -c
+          grp[4] += hp;
+          acc<-c25(i).rx>(jx_arr, hp);
+          acc<-c25(i).ry>(jy_arr, hp);
+        } else {
+          sm.hb[(i - 1) * NT + tid] = hp;
+        }
+      }
+    });
+    __syncthreads();
+    // arrivals from the other r-nodes of the tile
+    static_for<1, 20>([&](auto I) {
+      constexpr int i = I;
+      constexpr V4 cv = c25(i);
+      constexpr int g = qgroup(cv);
+      if (!((bm >> g) & 1u) && ((vmask >> rbit(cv.rx, cv.ry)) & 1u)) {
+        const real v = sm.hb[(i - 1) * NT + tid - (cv.ry * TX + cv.rx)];
+        grp[g] += v;
+        acc<cv.rx>(jx_arr, v);
+        acc<cv.ry>(jy_arr, v);
+      }
+    });
+#pragma unroll
+    for (int g = 0; g < 9; ++g) {
+      const int t = g == 4 ? q : tg[g];
+      if (t >= 0) sm.A[t * NT + tid] += grp[g];
+    }
+    if (ring_thread) {
+      real gr[9];
+#pragma unroll
+      for (int g = 0; g < 9; ++g) gr[g] = real(0);
+      static_for<1, 20>([&](auto I) {
+        constexpr int i = I;
+        constexpr V4 cv = c25(i);
+        constexpr int g = qgroup(cv);
+        if (!((bm >> g) & 1u) && ((rmask >> rbit(cv.rx, cv.ry)) & 1u)) {
+          const real v = sm.hb[(i - 1) * NT + rbase - (cv.ry * TX + cv.rx)];
+          gr[g] += v;
+          acc<cv.rx>(jx_r, v);
+          acc<cv.ry>(jy_r, v);
+        }
+      });
+#pragma unroll
+      for (int g = 0; g < 9; ++g) {
+        const int t = g == 4 ? q : tg[g];
+        if (t >= 0) sm.Ar[t * RING + tid] += gr[g];
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- flush the next step's moments
+  const bool border = lx == 0 || lx == TX - 1 || ly == 0 || ly == TY - 1;
+  if (!border) {
+    real drho = ms_arr, txx = 0, txy = 0, tyy = 0;
+    for (int p = 0; p < nq; ++p) {
+      const real d = sm.A[p * NT + tid] + fa.dpsi[p];
+      Mout[(size_t)p * P + n] = d;
+      drho += d;
+      const real Qx = a.tab.qx[p], Qy = a.tab.qy[p];
+      txx += d * Qx * Qx;
+      txy += d * Qx * Qy;
+      tyy += d * Qy * Qy;
+    }
+    Mout[(size_t)(nq + M_DRHO) * P + n] = drho;
+    Mout[(size_t)(nq + M_JX) * P + n] = jx_arr + fa.dvx;
+    Mout[(size_t)(nq + M_JY) * P + n] = jy_arr + fa.dvy;
+    Mout[(size_t)(nq + M_THXX) * P + n] = a.hl2h * txx;
+    Mout[(size_t)(nq + M_THXY) * P + n] = a.hl2h * txy;
+    Mout[(size_t)(nq + M_THYY) * P + n] = a.hl2h * tyy;
+  } else {
+    for (int p = 0; p < nq; ++p) Mout[(size_t)p * P + n] = sm.A[p * NT + tid];
+    Mout[(size_t)(nq + M_DRHO) * P + n] = ms_arr;
+    Mout[(size_t)(nq + M_JX) * P + n] = jx_arr;
+    Mout[(size_t)(nq + M_JY) * P + n] = jy_arr;
+  }
+  if (ring_thread) {
+    const size_t ntiles = (size_t)gridDim.x * gridDim.y;
+    const size_t tile = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+    real* ex = fa.exports;
+    for (int p = 0; p < nq; ++p) ex[((size_t)p * ntiles + tile) * RING + tid] = sm.Ar[p * RING + tid];
+    ex[((size_t)(nq + 0) * ntiles + tile) * RING + tid] = ms_r;
+    ex[((size_t)(nq + 1) * ntiles + tile) * RING + tid] = jx_r;
+    ex[((size_t)(nq + 2) * ntiles + tile) * RING + tid] = jy_r;
+  }
+}
+
+// Completes the border nodes of every tile: own partial sums plus the ring
+// exports of the neighbouring tiles (left, right, down, up, then the four
+// diagonal neighbours at corners), plus the constant shift terms; then
+// delta rho and delta Theta.
+template <typename real>
+__global__ void __launch_bounds__(128) fixup_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
+  constexpr int NB = 2 * TX + 2 * (TY - 2);
+  const int k = threadIdx.x;
+  if (k >= NB) return;
+  int lx, ly;
+  if (k < TX) { lx = k; ly = 0; }
+  else if (k < 2 * TX) { lx = k - TX; ly = TY - 1; }
+  else if (k < 2 * TX + TY - 2) { lx = 0; ly = 1 + (k - 2 * TX); }
+  else { lx = TX - 1; ly = 1 + (k - 2 * TX - (TY - 2)); }
+  const int ntx = gridDim.x, nty = gridDim.y;
+  const int tx = blockIdx.x, ty = blockIdx.y;
+  const size_t ntiles = (size_t)ntx * nty;
+  const int nq = a.nq;
+  const size_t P = a.plane;
+  const size_t n = (size_t)(ty * TY + ly) * a.pitch + (tx * TX + lx);
+  // contributing neighbour tiles and the ring position of this node in each
+  int ctile[8], cpos[8], nc = 0;
+  auto tile_of = [&](int dx, int dy) {
+    const int ax = (tx + dx + ntx) % ntx, ay = (ty + dy + nty) % nty;
+    return ay * ntx + ax;
+  };
+  if (lx == 0) { ctile[nc] = tile_of(-1, 0); cpos[nc++] = ring_pos(TX, ly); }
+  if (lx == TX - 1) { ctile[nc] = tile_of(1, 0); cpos[nc++] = ring_pos(-1, ly); }
+  if (ly == 0) { ctile[nc] = tile_of(0, -1); cpos[nc++] = ring_pos(lx, TY); }
+  if (ly == TY - 1) { ctile[nc] = tile_of(0, 1); cpos[nc++] = ring_pos(lx, -1); }
+  if (lx == 0 && ly == 0) { ctile[nc] = tile_of(-1, -1); cpos[nc++] = ring_pos(TX, TY); }
+  if (lx == TX - 1 && ly == 0) { ctile[nc] = tile_of(1, -1); cpos[nc++] = ring_pos(-1, TY); }
+  if (lx == 0 && ly == TY - 1) { ctile[nc] = tile_of(-1, 1); cpos[nc++] = ring_pos(TX, -1); }
+  if (lx == TX - 1 && ly == TY - 1) { ctile[nc] = tile_of(1, 1); cpos[nc++] = ring_pos(-1, -1); }
+  const real* ex = fa.exports;
+  auto gather = [&](int j, real v) {
+    for (int c = 0; c < nc; ++c) v += ex[((size_t)j * ntiles + ctile[c]) * RING + cpos[c]];
+    return v;
+  };
+  real* M = fa.Mout;
+  real drho = gather(nq + 0, M[(size_t)(nq + M_DRHO) * P + n]);
+  const real jx = gather(nq + 1, M[(size_t)(nq + M_JX) * P + n]) + fa.dvx;
+  const real jy = gather(nq + 2, M[(size_t)(nq + M_JY) * P + n]) + fa.dvy;
+  real txx = 0, txy = 0, tyy = 0;
+  for (int p = 0; p < nq; ++p) {
+    const real d = gather(p, M[(size_t)p * P + n]) + fa.dpsi[p];
+    M[(size_t)p * P + n] = d;
+    drho += d;
+    const real Qx = a.tab.qx[p], Qy = a.tab.qy[p];
+    txx += d * Qx * Qx;
+    txy += d * Qx * Qy;
+    tyy += d * Qy * Qy;
+  }
+  M[(size_t)(nq + M_DRHO) * P + n] = drho;
+  M[(size_t)(nq + M_JX) * P + n] = jx;
+  M[(size_t)(nq + M_JY) * P + n] = jy;
+  M[(size_t)(nq + M_THXX) * P + n] = a.hl2h * txx;
+  M[(size_t)(nq + M_THXY) * P + n] = a.hl2h * txy;
+  M[(size_t)(nq + M_THYY) * P + n] = a.hl2h * tyy;
+}
+
+}  // namespace
+
+size_t fused_smem_bytes(int nq, size_t real_bytes) {
+  return real_bytes * ((NSTAGE + 20) * NT + (size_t)nq * NT + (size_t)nq * RING +
+                       2 * (TY + 2) * (TX + 2) + (size_t)nq * 25) +
+         sizeof(int) * (size_t)nq * (9 + 25);
+}
+
+size_t fused_export_elems(int nx, int ny, int nq) {
+  return (size_t)(nx / TX) * (ny / TY) * RING * (size_t)(nq + 3);
+}
+
+bool fused_supported(int nx, int ny, int nq, size_t real_bytes) {
+  return nx % TX == 0 && ny % TY == 0 && fused_smem_bytes(nq, real_bytes) <= 227 * 1024;
+}
+
+template <typename real>
+cudaError_t launch_step_fused(const KernelArgs<real>& a, const FusedArgs<real>& f, cudaStream_t s) {
+  const size_t smem = fused_smem_bytes(a.nq, sizeof(real));
+  cudaError_t e = cudaFuncSetAttribute(step_fused_kernel<real>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  step_fused_kernel<real><<<dim3(a.nx / TX, a.ny / TY), dim3(TX, TY), smem, s>>>(a, f);
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_fixup(const KernelArgs<real>& a, const FusedArgs<real>& f, cudaStream_t s) {
+  fixup_kernel<real><<<dim3(a.nx / TX, a.ny / TY), 128, 0, s>>>(a, f);
+  return cudaGetLastError();
+}
+
+// Host-side tables of the fused kernel: target Q-node of every
+// (Q-node, Q-displacement group), -1 where the displacement leaves the disk;
+// the per-Q-node sum of the pull shift differences; their r-momentum sum.
+void fused_tables(const Lattice& L, const HostTables& t, std::vector<int>& tgt,
+                  std::vector<double>& dpsi, double& dvx, double& dvy) {
+  tgt.assign((size_t)L.nq * 9, -1);
+  std::vector<int> qmap((size_t)L.S * L.S, -1);
+  std::vector<int> gi(L.nq), gj(L.nq);
+  for (int q = 0; q < L.nq; ++q) {
+    gi[q] = (int)lround(t.qx[q] + 0.5 * (L.S - 1));
+    gj[q] = (int)lround(t.qy[q] + 0.5 * (L.S - 1));
+    qmap[(size_t)gj[q] * L.S + gi[q]] = q;
+  }
+  for (int q = 0; q < L.nq; ++q)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int i = gi[q] + dx, j = gj[q] + dy;
+        const int tq = (i >= 0 && i < L.S && j >= 0 && j < L.S) ? qmap[(size_t)j * L.S + i] : -1;
+        tgt[(size_t)q * 9 + qgroup9(dx, dy)] = tq;
+      }
+  dpsi.assign(L.nq, 0.0);
+  dvx = dvy = 0;
+  for (int q = 0; q < L.nq; ++q)
+    for (int i = 0; i < 25; ++i) {
+      const double d = t.delta[(size_t)q * 25 + i];
+      dpsi[q] += d;
+      dvx += c25(i).rx * d;
+      dvy += c25(i).ry * d;
+    }
+}
+
+#define TFKT_INSTANTIATE_FUSED(real)                                                           \
+  template cudaError_t launch_step_fused<real>(const KernelArgs<real>&, const FusedArgs<real>&, \
+                                               cudaStream_t);                                  \
+  template cudaError_t launch_fixup<real>(const KernelArgs<real>&, const FusedArgs<real>&,     \
+                                          cudaStream_t);
+TFKT_INSTANTIATE_FUSED(float)
+TFKT_INSTANTIATE_FUSED(double)
+
+}  // namespace tfkt

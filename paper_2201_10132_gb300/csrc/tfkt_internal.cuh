@@ -103,12 +103,24 @@ struct KernelArgs {
   Tables<real> tab;
 };
 
+// Extra arguments of the fused step and its border fix-up.
+template <typename real>
+struct FusedArgs {
+  const real* Min;      // complete moment planes of the state being stepped
+  real* Mout;           // moment planes of the next state (written)
+  real* exports;        // [nq + 3][tiles][ring] arrivals at ring nodes from each tile
+  const int* tgt;       // [nq][9] target Q-node per Q-displacement group, -1: bounce-back
+  const real* dpsi;     // [nq] sum over i of the pull shift differences of Q-node q
+  real dvx, dvy;        // r-momentum of all pull shift differences
+};
+
 struct Workspace {
   void* base = nullptr;
   size_t bytes = 0;
   bool owned = false;
   size_t off_pop[2] = {0, 0};
   size_t off_M = 0, off_U = 0, off_tab = 0, off_part = 0, off_diag = 0;
+  size_t off_M2 = 0, off_exp = 0, off_ftab = 0;  // fused path: second M, ring exports, tables
 };
 
 struct Ctx {
@@ -120,6 +132,9 @@ struct Ctx {
   bool poisoned = false;
   int64_t step = 0;
   int diag_blocks = 0;
+  bool fused = false;     // grid fits the fused single-pass kernel
+  int mcur = 0;           // moment buffer (0: off_M, 1: off_M2) of the current state
+  double dvx = 0, dvy = 0;  // r-momentum of all pull shift differences (fused path)
 };
 
 // Host helpers (tfkt_api.cu).
@@ -151,6 +166,17 @@ cudaError_t launch_populations(const KernelArgs<real>& a, double* out, cudaStrea
 template <typename real>
 cudaError_t launch_diag(const KernelArgs<real>& a, double* partials, int nblocks, double* out,
                         cudaStream_t s);
+
+// Fused single-pass step (tfkt_fused.cu).
+size_t fused_smem_bytes(int nq, size_t real_bytes);
+size_t fused_export_elems(int nx, int ny, int nq);
+bool fused_supported(int nx, int ny, int nq, size_t real_bytes);
+void fused_tables(const Lattice& L, const HostTables& t, std::vector<int>& tgt,
+                  std::vector<double>& dpsi, double& dvx, double& dvy);
+template <typename real>
+cudaError_t launch_step_fused(const KernelArgs<real>& a, const FusedArgs<real>& f, cudaStream_t s);
+template <typename real>
+cudaError_t launch_fixup(const KernelArgs<real>& a, const FusedArgs<real>& f, cudaStream_t s);
 
 constexpr int TX = 32;   // tile width (one warp along x)
 constexpr int TY = 8;    // tile height

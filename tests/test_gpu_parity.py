@@ -53,7 +53,32 @@ CASES = [
     (33, 9, 4, 2.0, 3.0, 0.0, 1.0, 1, 0.0, 1, 10),       # Newtonian: no polymer
     (1, 1, 1, 1.0, 5.0, 0.5, 0.2, 1, 0.0, 0, 7),         # one r-node, one Q-node
     (5, 3, 2, 1.0, 5.0, 0.5, 0.2, 1, 0.0, 1, 9),         # 2x2 Q-grid: every Q-move bounces
+    # grids that are multiples of the 32 x 8 tile take the fused single-pass kernel
+    (64, 32, 6, 3.0, 5.0, 0.5, 0.2, 1, 0.0, 1, 12),      # 2 x 4 tiles
+    (32, 8, 8, 4.0, 5.0, 0.5, 0.2, 1, 0.0, 0, 9),        # one tile: its ring wraps onto itself
+    (96, 16, 6, 3.0, 4.0, 1.0, 0.5, 2, 0.3, 1, 15),      # tau2 > tau1
+    (64, 16, 4, 2.0, 3.0, 0.0, 1.0, 1, 0.0, 1, 10),      # Newtonian
+    (32, 16, 2, 1.0, 5.0, 0.5, 0.2, 1, 0.0, 1, 9),       # every Q-move bounces
 ]
+FUSED = [c for c in CASES if c[0] % 32 == 0 and c[1] % 8 == 0]
+
+
+@pytest.mark.parametrize("case", [CASES[2], CASES[7]])
+def test_path_dispatch(T, case):
+    """Tile-multiple grids run the fused kernel plus its border fix-up; others the
+    moments + step pair."""
+    nx, ny, S, R, re, wi, beta, kp, tau2, ic, steps = case
+    p = T.Params(nx, ny, S, R, re, wi, beta, 0.05, kp, tau2, 0.0, ic, T.FP64)
+    ms = np.zeros(len(T.KERNELS))
+    n = np.zeros(len(T.KERNELS), np.int64)
+    with T.Solver(p) as s:
+        s.step_profiled(4, ms, n)
+    k = dict(zip(T.KERNELS, n.tolist()))
+    if case in FUSED:
+        assert k == {"moments": 0, "step": 0, "fused": 4, "fixup": 4}
+    else:
+        # the moments of the initial state come from tfkt_create
+        assert k == {"moments": 3, "step": 4, "fused": 0, "fixup": 0}
 
 
 @pytest.mark.parametrize("case", CASES)
@@ -93,7 +118,7 @@ def test_fp64_matches_oracle(T, oracle_mod, case):
         assert diag[k] == pytest.approx(od[k], rel=1e-9, abs=1e-13 * max(1.0, od["mass_s"])), k
 
 
-@pytest.mark.parametrize("case", [CASES[1], CASES[2], CASES[3]])
+@pytest.mark.parametrize("case", [CASES[1], CASES[2], CASES[3], CASES[7], CASES[9]])
 def test_fp32_within_tolerance(T, oracle_mod, case):
     from paper_2201_10132_gb300.inputs import perturbation
     nx, ny, S, R, re, wi, beta, kp, tau2, ic, steps = case
