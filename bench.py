@@ -146,6 +146,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="kolmogorov-4096x4096-nq32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     args = ap.parse_args()
     from paper_2201_10132_gb300.inputs import WORKLOADS
     W = WORKLOADS[args.workload]
@@ -210,24 +211,28 @@ def main():
     # end to end through the C-ABI with pinned host buffers: create from the host
     # perturbation, per step a step and a diagnostics read-back, then the velocity
     # and density fields back to the host
-    out_diag = torch.zeros(len(tfkt.DIAGS), dtype=torch.float64).pin_memory()
-    names = ["rho_s", "ux", "uy"]
-    host_f = torch.empty((len(names), W.ny, W.nx), dtype=torch.float64).pin_memory()
-    barrier()
-    t0 = time.perf_counter()
-    s2 = tfkt.Solver(p, pert.numpy(), workspace=ws, stream=stream.cuda_stream)
-    for _ in range(args.steps):
-        s2.step(1)
-        s2.diagnostics_into(out_diag.numpy())
-    s2.moments_into(tfkt.field_mask(names), host_f.numpy())
-    s2.close()
-    t_e2e = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    h2d = pert.numel() * 8 / args.steps
-    d2h = (args.steps * out_diag.numel() * 8 + host_f.numel() * 8) / args.steps
+    e2e = None
+    if not args.no_e2e:
+        out_diag = torch.zeros(len(tfkt.DIAGS), dtype=torch.float64).pin_memory()
+        names = ["rho_s", "ux", "uy"]
+        host_f = torch.empty((len(names), W.ny, W.nx), dtype=torch.float64).pin_memory()
+        barrier()
+        t0 = time.perf_counter()
+        s2 = tfkt.Solver(p, pert.numpy(), workspace=ws, stream=stream.cuda_stream)
+        for _ in range(args.steps):
+            s2.step(1)
+            s2.diagnostics_into(out_diag.numpy())
+        s2.moments_into(tfkt.field_mask(names), host_f.numpy())
+        s2.close()
+        t_e2e = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        e2e = {"value": world * nodes * args.steps / t_e2e / 1e9, "unit": "GLUPS",
+               "h2d_bytes_per_step": pert.numel() * 8 / args.steps,
+               "d2h_bytes_per_step": (args.steps * out_diag.numel() * 8 + host_f.numel() * 8)
+               / args.steps}
 
     if rank == 0:
         hbm_peak, peak_kind = _peaks()
@@ -264,8 +269,7 @@ def main():
                          "bytes_per_launch": per[top]["bytes_per_launch"],
                          "step_model_gbs": nodes * (2 * npl + 2 * nm) * s / (ms / args.steps / 1e3) / 1e9,
                          "kernels": per},
-            "e2e": {"value": world * nodes * args.steps / t_e2e / 1e9, "unit": "GLUPS",
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "e2e": e2e,
             "gpu_launches": int(launches.sum()),
             "clocks": clocks,
             "cpu_baseline": cpu_base,

@@ -60,6 +60,12 @@ __device__ __forceinline__ bool in_tile(int x, int y) {
   return x >= 0 && x < TX && y >= 0 && y < TY;
 }
 
+template <typename T>
+__device__ __forceinline__ T __int_as_T(int v) {
+  if constexpr (std::is_same<T, float>::value) return __int_as_float(v);
+  else return (T)v;
+}
+
 // Adds s * v for a compile-time s in {-1, 0, 1} (no multiply by a zero
 // coefficient, which IEEE arithmetic would not let the compiler drop).
 template <int S, typename real>
@@ -72,34 +78,44 @@ __device__ __forceinline__ void acc(real& sum, real v) {
 __host__ __device__ constexpr bool moves_r(int i) { return i >= 1 && i <= 20; }
 __host__ __device__ constexpr int rbit(int cx, int cy) { return (cy + 1) * 3 + (cx + 1); }
 
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
+// Loads N values (N a multiple of the vector width) from 16-byte aligned shared memory.
+template <int N, typename T>
+__device__ __forceinline__ void load_vec(T* out, const T* src) {
+  if constexpr (sizeof(T) == 4) {
+    static_assert(N % 4 == 0, "");
+#pragma unroll
+    for (int k = 0; k < N / 4; ++k) {
+      const int4 v = reinterpret_cast<const int4*>(src)[k];
+      out[4 * k] = __int_as_T<T>(v.x);
+      out[4 * k + 1] = __int_as_T<T>(v.y);
+      out[4 * k + 2] = __int_as_T<T>(v.z);
+      out[4 * k + 3] = __int_as_T<T>(v.w);
+    }
+  } else {
+    static_assert(N % 2 == 0, "");
+#pragma unroll
+    for (int k = 0; k < N / 2; ++k) {
+      const double2 v = reinterpret_cast<const double2*>(src)[k];
+      out[2 * k] = v.x;
+      out[2 * k + 1] = v.y;
+    }
+  }
 }
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
-}
-template <typename real>
-__device__ __forceinline__ void cp_async(real* smem, const real* gmem) {
-  if constexpr (sizeof(real) == 4) cp_async4(smem, gmem);
-  else cp_async8(smem, gmem);
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-constexpr int NSTAGE = 25 + 4;  // the 25 pulled populations and 4 neighbour psi of one Q-node
+constexpr int HBW = TX + 1;      // padded row of the post-collision exchange buffer
+constexpr int HBS = TY * HBW;    // one velocity's plane in that buffer
+constexpr int DQ = 28;           // per-Q-node stride of the shift table (vector loads)
+constexpr int GQ = 12;           // per-Q-node stride of the target table (vector loads)
 
 template <typename real>
 struct Smem {
-  real* st;      // [NSTAGE][NT] prefetched inputs of the next Q-node (each thread its own column)
-  real* hb;      // [20][NT] post-collision values of the r-moving velocities
+  real* hb;      // [20][TY][HBW] post-collision values of the r-moving velocities
   real* A;       // [nq][NT] own-node arrival sums per Q-node
   real* Ar;      // [nq][RING] ring-node arrival sums per Q-node
   real* Ux;      // [TY+2][TX+2]
   real* Uy;
-  real* delta;   // [nq*25] pull shift differences
-  int* tgt;      // [nq][9] target Q-node of each Q-displacement group, -1: bounce-back
+  real* delta;   // [nq][DQ] pull shift differences
+  int* tgt;      // [nq][GQ] target Q-node of each Q-displacement group, -1: bounce-back
   int* pull;     // [nq*25] pull source plane (>= 0) or ~plane for bounce-back
 };
 
@@ -107,15 +123,15 @@ template <typename real>
 __device__ __forceinline__ Smem<real> carve(void* base, int nq) {
   Smem<real> s;
   real* p = (real*)base;
-  s.st = p; p += NSTAGE * NT;
-  s.hb = p; p += 20 * NT;
+  s.hb = p; p += 20 * HBS;
   s.A = p; p += (size_t)nq * NT;
   s.Ar = p; p += (size_t)nq * RING;
   s.Ux = p; p += (TY + 2) * (TX + 2);
   s.Uy = p; p += (TY + 2) * (TX + 2);
-  s.delta = p; p += (size_t)nq * 25;
-  s.tgt = (int*)p;
-  s.pull = s.tgt + (size_t)nq * 9;
+  p = (real*)(((uintptr_t)p + 15) & ~(uintptr_t)15);
+  s.delta = p; p += (size_t)nq * DQ;
+  s.tgt = (int*)(((uintptr_t)p + 15) & ~(uintptr_t)15);
+  s.pull = s.tgt + (size_t)nq * GQ;
   return s;
 }
 
@@ -140,26 +156,6 @@ __device__ __forceinline__ void velocity_at(const KernelArgs<real>& a, const rea
   const real f = a.tab.arow[y];
   ux = (jx + real(0.5) * (ex + rho * f)) / rho;
   uy = (jy + real(0.5) * ey) / rho;
-}
-
-// Queues the copies of Q-node q's inputs into this thread's stage column.
-template <typename real>
-__device__ __forceinline__ void prefetch_q(const Smem<real>& sm, const real* src, const real* Min,
-                                           size_t P, const uint32_t* off, int q, int tid) {
-#pragma unroll
-  for (int i = 0; i < 25; ++i) {
-    const V4 cv = c25(i);
-    const int e = sm.pull[q * 25 + i];
-    const uint32_t o = e >= 0 ? off[shift_index(-cv.rx, -cv.ry)] : off[4];
-    const int pl = e >= 0 ? e : ~e;
-    cp_async(sm.st + i * NT + tid, src + (size_t)pl * P + o);
-  }
-  const real* Mq = Min + (size_t)q * P;
-  cp_async(sm.st + 25 * NT + tid, Mq + off[5]);
-  cp_async(sm.st + 26 * NT + tid, Mq + off[3]);
-  cp_async(sm.st + 27 * NT + tid, Mq + off[7]);
-  cp_async(sm.st + 28 * NT + tid, Mq + off[1]);
-  cp_async_commit();
 }
 
 template <typename real>
@@ -188,10 +184,14 @@ step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
   const uint32_t n = off[4];
 
   // ---- stage: tables, zeroed accumulators, U on the tile and its 1-node ring
-  for (int k = tid; k < nq * 9; k += NT) sm.tgt[k] = fa.tgt[k];
-  for (int k = tid; k < nq * 25; k += NT) {
-    sm.pull[k] = a.tab.pull[k];
-    sm.delta[k] = a.tab.delta[k];
+  for (int k = tid; k < nq * GQ; k += NT) {
+    const int q = k / GQ, g = k % GQ;
+    sm.tgt[k] = g < 9 ? fa.tgt[q * 9 + g] : -1;
+  }
+  for (int k = tid; k < nq * 25; k += NT) sm.pull[k] = a.tab.pull[k];
+  for (int k = tid; k < nq * DQ; k += NT) {
+    const int q = k / DQ, i = k % DQ;
+    sm.delta[k] = i < 25 ? a.tab.delta[q * 25 + i] : real(0);
   }
   for (int p = 0; p < nq; ++p) sm.A[p * NT + tid] = real(0);
   for (int k = tid; k < nq * RING; k += NT) sm.Ar[k] = real(0);
@@ -206,7 +206,6 @@ step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
     sm.Uy[k] = uy;
   }
   __syncthreads();
-  prefetch_q(sm, src, Min, P, off, 0, tid);   // overlaps the solvent work
 
   const int c = (ly + 1) * (TX + 2) + (lx + 1);
   const real Ux = sm.Ux[c], Uy = sm.Uy[c];
@@ -227,7 +226,8 @@ step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
       if (in_tile(lx - dx, ly - dy)) vmask |= 1u << rbit(dx, dy);
       if (ring_thread && in_tile(rex - dx, rey - dy)) rmask |= 1u << rbit(dx, dy);
     }
-  const int rbase = rey * TX + rex;
+  const int rbase = rey * HBW + rex;
+  const int hbo = ly * HBW + lx;
 
   const real rho = a.rho0 + Min[(size_t)(nq + M_DRHO) * P + n];
   const real force = rho * a.tab.arow[y];
@@ -266,7 +266,7 @@ step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
       const real hp = a.om2b * h[i] + a.tb * feq_dev + a.omb * real(w9(i)) * gx * force;
       dst[(size_t)i * P + n] = hp;
       if constexpr (i == 0) ms_arr += hp;
-      else sm.hb[(i - 1) * NT + tid] = hp;
+      else sm.hb[(i - 1) * HBS + hbo] = hp;
     });
   }
   __syncthreads();
@@ -274,7 +274,7 @@ step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
     constexpr int i = I;
     constexpr int k = rbit(c9x(i), c9y(i));
     if ((vmask >> k) & 1u) {
-      const real v = sm.hb[(i - 1) * NT + tid - (c9y(i) * TX + c9x(i))];
+      const real v = sm.hb[(i - 1) * HBS + hbo - (c9y(i) * HBW + c9x(i))];
       ms_arr += v;
       acc<c9x(i)>(jx_arr, v);
       acc<c9y(i)>(jy_arr, v);
@@ -285,7 +285,7 @@ step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
       constexpr int i = I;
       constexpr int k = rbit(c9x(i), c9y(i));
       if ((rmask >> k) & 1u) {
-        const real v = sm.hb[(i - 1) * NT + rbase - (c9y(i) * TX + c9x(i))];
+        const real v = sm.hb[(i - 1) * HBS + rbase - (c9y(i) * HBW + c9x(i))];
         ms_r += v;
         acc<c9x(i)>(jx_r, v);
         acc<c9y(i)>(jy_r, v);
@@ -294,23 +294,31 @@ step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
   }
   __syncthreads();
 
-  // ---- polymer, one Q-node at a time; the next Q-node's inputs are in flight meanwhile
+  // ---- polymer, one Q-node at a time
   for (int q = 0; q < nq; ++q) {
-    cp_async_wait_all();
     real h[25];
+    {
+      real dl[DQ];
+      load_vec<DQ>(dl, sm.delta + q * DQ);
 #pragma unroll
-    for (int i = 0; i < 25; ++i) h[i] = sm.st[i * NT + tid] + sm.delta[q * 25 + i];
-    const real dpx = real(0.5) * (sm.st[25 * NT + tid] - sm.st[26 * NT + tid]);
-    const real dpy = real(0.5) * (sm.st[27 * NT + tid] - sm.st[28 * NT + tid]);
-    if (q + 1 < nq) prefetch_q(sm, src, Min, P, off, q + 1, tid);
+      for (int i = 0; i < 25; ++i) {
+        const V4 cv = c25(i);
+        const int e = sm.pull[q * 25 + i];
+        const uint32_t o = e >= 0 ? off[shift_index(-cv.rx, -cv.ry)] : off[4];
+        const int pl = e >= 0 ? e : ~e;
+        h[i] = src[(size_t)pl * P + o] + dl[i];
+      }
+    }
+    const real* Mq = Min + (size_t)q * P;
+    const real dpx = real(0.5) * (Mq[off[5]] - Mq[off[3]]);
+    const real dpy = real(0.5) * (Mq[off[7]] - Mq[off[1]]);
 
-    int tg[9];
+    int tg[GQ];
+    load_vec<GQ>(tg, sm.tgt + q * GQ);
     uint32_t bm = 0;
 #pragma unroll
-    for (int g = 0; g < 9; ++g) {
-      tg[g] = sm.tgt[q * 9 + g];
+    for (int g = 0; g < 9; ++g)
       if (tg[g] < 0) bm |= 1u << g;
-    }
     real dpsi = 0, rx = 0, ry = 0, qx = 0, qy = 0;
     static_for<0, 25>([&](auto I) {
       constexpr int i = I;
@@ -357,7 +365,7 @@ step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
           acc<-c25(i).rx>(jx_arr, hp);
           acc<-c25(i).ry>(jy_arr, hp);
         } else {
-          sm.hb[(i - 1) * NT + tid] = hp;
+          sm.hb[(i - 1) * HBS + hbo] = hp;
         }
       }
     });
@@ -368,7 +376,7 @@ step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
       constexpr V4 cv = c25(i);
       constexpr int g = qgroup(cv);
       if (!((bm >> g) & 1u) && ((vmask >> rbit(cv.rx, cv.ry)) & 1u)) {
-        const real v = sm.hb[(i - 1) * NT + tid - (cv.ry * TX + cv.rx)];
+        const real v = sm.hb[(i - 1) * HBS + hbo - (cv.ry * HBW + cv.rx)];
         grp[g] += v;
         acc<cv.rx>(jx_arr, v);
         acc<cv.ry>(jy_arr, v);
@@ -388,7 +396,7 @@ step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
         constexpr V4 cv = c25(i);
         constexpr int g = qgroup(cv);
         if (!((bm >> g) & 1u) && ((rmask >> rbit(cv.rx, cv.ry)) & 1u)) {
-          const real v = sm.hb[(i - 1) * NT + rbase - (cv.ry * TX + cv.rx)];
+          const real v = sm.hb[(i - 1) * HBS + rbase - (cv.ry * HBW + cv.rx)];
           gr[g] += v;
           acc<cv.rx>(jx_r, v);
           acc<cv.ry>(jy_r, v);
@@ -503,9 +511,9 @@ __global__ void __launch_bounds__(128) fixup_kernel(KernelArgs<real> a, FusedArg
 }  // namespace
 
 size_t fused_smem_bytes(int nq, size_t real_bytes) {
-  return real_bytes * ((NSTAGE + 20) * NT + (size_t)nq * NT + (size_t)nq * RING +
-                       2 * (TY + 2) * (TX + 2) + (size_t)nq * 25) +
-         sizeof(int) * (size_t)nq * (9 + 25);
+  return real_bytes * (20 * HBS + (size_t)nq * NT + (size_t)nq * RING +
+                       2 * (TY + 2) * (TX + 2) + (size_t)nq * DQ) +
+         sizeof(int) * (size_t)nq * (GQ + 25) + 64;
 }
 
 size_t fused_export_elems(int nx, int ny, int nq) {

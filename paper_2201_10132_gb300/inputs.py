@@ -101,4 +101,7 @@ KOLMOGOROV_4096 = Workload("kolmogorov-4096x4096-nq32", 4096, 4096, 6, 3.0, 10.0
 # Profiling case: same lattice parameters at 1024^2 (forcing wavelength 64 nodes).
 KOLMOGOROV_1024 = Workload("kolmogorov-1024x1024-nq32", 1024, 1024, 6, 3.0, 10.0, 1.0, 0.2, 0.05,
                            16, 0, 1e-3)
-WORKLOADS = {w.name: w for w in (KOLMOGOROV_64, KOLMOGOROV_1024, KOLMOGOROV_4096)}
+# Profiling case small enough for a full ncu capture (inputs still larger than L2).
+KOLMOGOROV_512 = Workload("kolmogorov-512x512-nq32", 512, 512, 6, 3.0, 10.0, 1.0, 0.2, 0.05,
+                          8, 0, 1e-3)
+WORKLOADS = {w.name: w for w in (KOLMOGOROV_64, KOLMOGOROV_512, KOLMOGOROV_1024, KOLMOGOROV_4096)}
