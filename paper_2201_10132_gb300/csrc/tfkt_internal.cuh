@@ -2,6 +2,7 @@
 // arguments and launchers. Not part of the C-ABI (include/tfkt.h is).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -121,6 +122,7 @@ struct Workspace {
   size_t off_pop[2] = {0, 0};
   size_t off_M = 0, off_U = 0, off_tab = 0, off_part = 0, off_diag = 0;
   size_t off_M2 = 0, off_exp = 0, off_ftab = 0;  // fused path: second M, ring exports, tables
+  size_t off_err = 0;                             // device error flag (bounded waits that gave up)
 };
 
 struct Ctx {
@@ -135,6 +137,10 @@ struct Ctx {
   bool fused = false;     // grid fits the fused single-pass kernel
   int mcur = 0;           // moment buffer (0: off_M, 1: off_M2) of the current state
   double dvx = 0, dvy = 0;  // r-momentum of all pull shift differences (fused path)
+  bool tma = false;         // FP32 fused path with bulk tensor copies
+  CUtensorMap tm_load[2];   // per population buffer: pull boxes (TX + 8) x TY
+  CUtensorMap tm_store9[2];   // per population buffer: the 9 solvent planes of a tile
+  CUtensorMap tm_store25[2];  // per population buffer: the 25 planes of one Q-node of a tile
 };
 
 // Host helpers (tfkt_api.cu).
@@ -177,6 +183,12 @@ template <typename real>
 cudaError_t launch_step_fused(const KernelArgs<real>& a, const FusedArgs<real>& f, cudaStream_t s);
 template <typename real>
 cudaError_t launch_fixup(const KernelArgs<real>& a, const FusedArgs<real>& f, cudaStream_t s);
+// TMA variant of the fused step (FP32 storage).
+size_t tma_smem_bytes(int nq);
+bool tma_supported(int nx, int ny, int nq, int precision);
+cudaError_t launch_step_tma(const KernelArgs<float>& a, const FusedArgs<float>& f,
+                            const CUtensorMap& load_map, const CUtensorMap& store9,
+                            const CUtensorMap& store25, int* err, cudaStream_t s);
 
 constexpr int TX = 32;   // tile width (one warp along x)
 constexpr int TY = 8;    // tile height
