@@ -43,8 +43,7 @@ typedef enum {
   TFKT_ENOMEM = 2,  /* device allocation failed, or the workspace is too small */
   TFKT_ECUDA = 3,   /* a CUDA call failed; the context is now poisoned */
   TFKT_ENAN = 4,    /* diagnostics found a non-finite value; state kept */
-  TFKT_ESTATE = 5,  /* the context was poisoned by an earlier CUDA error */
-  TFKT_ETIMEOUT = 6 /* a kernel's bounded wait for its own bulk copies gave up; state invalid */
+  TFKT_ESTATE = 5   /* the context was poisoned by an earlier CUDA error */
 } tfkt_status;
 
 typedef enum {

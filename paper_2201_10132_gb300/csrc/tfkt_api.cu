@@ -1,7 +1,5 @@
 // Host side of libtfkt: parameter mapping, lattice tables, workspace layout
 // and the extern "C" entry points declared in include/tfkt.h.
-#include <cuda.h>
-#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -136,15 +134,13 @@ size_t layout(const Lattice& L, Workspace* w) {
   o = align_up(o + (size_t)diag_blocks_for(L) * TFKT_NDIAG * sizeof(double), A);
   w->off_diag = o;
   o = align_up(o + TFKT_NDIAG * sizeof(double), A);
-  w->off_err = o;
-  o = align_up(o + sizeof(int), A);
   if (fused_supported(L.nx, L.ny, L.nq, sz)) {
     w->off_M2 = o;
     o = align_up(o + (size_t)L.nm * L.plane * sz, A);
     w->off_exp = o;
     o = align_up(o + fused_export_elems(L.nx, L.ny, L.nq) * sz, A);
     w->off_ftab = o;
-    o = align_up(o + (size_t)L.nq * (9 * sizeof(int) + sz) + A, A);
+    o = align_up(o + (size_t)L.nq * (9 * sizeof(int) + sz + 25 * sizeof(long long)) + 2 * A, A);
   }
   return o;
 }
@@ -208,61 +204,6 @@ HostTables build_tables(const Lattice& L) {
 
 namespace {
 
-// Bulk-tensor descriptors of one population buffer: a 3-D tensor (x, y, plane)
-// of FP32 values; loads take (TX + 8) x TY boxes (16-byte aligned start x0 - 4
-// covering the +-1 pull shifts), stores TX x TY tiles.
-tfkt_status encode_maps(Ctx* c) {
-  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  if (!encode) {
-    cudaDriverEntryPointQueryResult q;
-    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void**)&encode,
-                                                     12000, cudaEnableDefault, &q);
-    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !encode) {
-      encode = nullptr;
-      return fail(TFKT_ECUDA, "cuTensorMapEncodeTiled is not available");
-    }
-  }
-  const Lattice& L = c->L;
-  const cuuint64_t dims[3] = {(cuuint64_t)L.pitch, (cuuint64_t)L.ny, (cuuint64_t)L.npl};
-  const cuuint64_t strides[2] = {(cuuint64_t)L.pitch * sizeof(float),
-                                 (cuuint64_t)L.plane * sizeof(float)};
-  const cuuint32_t box_load[3] = {(cuuint32_t)(TX + 8), (cuuint32_t)TY, 1};
-  const cuuint32_t box_store9[3] = {(cuuint32_t)TX, (cuuint32_t)TY, 9};
-  const cuuint32_t box_store25[3] = {(cuuint32_t)TX, (cuuint32_t)TY, 25};
-  const cuuint32_t estr[3] = {1, 1, 1};
-  for (int b = 0; b < 2; ++b) {
-    void* base = (char*)c->ws.base + c->ws.off_pop[b];
-    CUresult r = encode(&c->tm_load[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides,
-                        box_load, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return fail(TFKT_ECUDA, "cuTensorMapEncodeTiled (load) failed");
-    r = encode(&c->tm_store9[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides,
-               box_store9, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return fail(TFKT_ECUDA, "cuTensorMapEncodeTiled (store) failed");
-    r = encode(&c->tm_store25[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides,
-               box_store25, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return fail(TFKT_ECUDA, "cuTensorMapEncodeTiled (store) failed");
-  }
-  return TFKT_OK;
-}
-
-int* err_flag(const Ctx* c) { return (int*)((char*)c->ws.base + c->ws.off_err); }
-
-// Reads the kernels' error flag (synchronises the stream).
-tfkt_status check_err(Ctx* c) {
-  int h = 0;
-  cudaError_t e = cudaMemcpyAsync(&h, err_flag(c), sizeof(int), cudaMemcpyDeviceToHost, c->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-  if (e != cudaSuccess) return cuda_fail(c, e, "error flag");
-  if (h) {
-    c->poisoned = true;
-    return fail(TFKT_ETIMEOUT, "a bounded wait for bulk copies gave up; the state is invalid");
-  }
-  return TFKT_OK;
-}
-
 template <typename real>
 KernelArgs<real> make_args(const Ctx* c, const HostTables* ht = nullptr) {
   const Lattice& L = c->L;
@@ -323,6 +264,7 @@ FusedArgs<real> make_fused(const Ctx* c) {
   f.exports = (real*)(base + c->ws.off_exp);
   f.tgt = (const int*)(base + c->ws.off_ftab);
   f.dpsi = (const real*)(base + c->ws.off_ftab + align_up((size_t)L.nq * 9 * sizeof(int), 256));
+  f.poff = (const long long*)((const char*)f.dpsi + align_up((size_t)L.nq * sizeof(real), 256));
   f.dvx = (real)c->dvx;
   f.dvy = (real)c->dvy;
   return f;
@@ -332,9 +274,12 @@ template <typename real>
 tfkt_status upload_fused_tables(Ctx* c, const HostTables& t) {
   std::vector<int> tgt;
   std::vector<double> dpsi;
-  fused_tables(c->L, t, tgt, dpsi, c->dvx, c->dvy);
+  std::vector<long long> poff;
+  fused_tables(c->L, t, tgt, dpsi, c->dvx, c->dvy, poff);
   FusedArgs<real> f = make_fused<real>(c);
   std::vector<real> d(dpsi.begin(), dpsi.end());
+  TFKT_CUDA(c, cudaMemcpy((void*)f.poff, poff.data(), poff.size() * sizeof(long long),
+                          cudaMemcpyHostToDevice));
   TFKT_CUDA(c, cudaMemcpy((void*)f.tgt, tgt.data(), tgt.size() * sizeof(int),
                           cudaMemcpyHostToDevice));
   TFKT_CUDA(c, cudaMemcpy((void*)f.dpsi, d.data(), d.size() * sizeof(real),
@@ -403,15 +348,7 @@ tfkt_status do_step(Ctx* c, int64_t n) {
     KernelArgs<real> a = make_args<real>(c);
     if (c->fused) {
       FusedArgs<real> f = make_fused<real>(c);
-      if constexpr (std::is_same<real, float>::value) {
-        if (c->tma)
-          TFKT_CUDA(c, launch_step_tma(a, f, c->tm_load[c->cur], c->tm_store9[c->cur ^ 1],
-                                       c->tm_store25[c->cur ^ 1], err_flag(c), c->stream));
-        else
-          TFKT_CUDA(c, launch_step_fused<real>(a, f, c->stream));
-      } else {
-        TFKT_CUDA(c, launch_step_fused<real>(a, f, c->stream));
-      }
+      TFKT_CUDA(c, launch_step_fused<real>(a, f, c->stream));
       TFKT_CUDA(c, launch_fixup<real>(a, f, c->stream));
       c->mcur ^= 1;
     } else {
@@ -458,14 +395,8 @@ tfkt_status do_step_profiled(Ctx* c, int64_t n, double* ms, int64_t* launches) {
     KernelArgs<real> a = make_args<real>(c);
     if (c->fused) {
       FusedArgs<real> f = make_fused<real>(c);
-      tfkt_status s = timed(TFKT_K_FUSED, [&] {
-        if constexpr (std::is_same<real, float>::value) {
-          if (c->tma)
-            return launch_step_tma(a, f, c->tm_load[c->cur], c->tm_store9[c->cur ^ 1],
-                                   c->tm_store25[c->cur ^ 1], err_flag(c), c->stream);
-        }
-        return launch_step_fused<real>(a, f, c->stream);
-      });
+      tfkt_status s =
+          timed(TFKT_K_FUSED, [&] { return launch_step_fused<real>(a, f, c->stream); });
       if (s != TFKT_OK) return s;
       s = timed(TFKT_K_FIXUP, [&] { return launch_fixup<real>(a, f, c->stream); });
       if (s != TFKT_OK) return s;
@@ -482,15 +413,13 @@ tfkt_status do_step_profiled(Ctx* c, int64_t n, double* ms, int64_t* launches) {
     ms[j] += acc[j];
     if (launches) launches[j] += cnt[j];
   }
-  return check_err(c);
+  return TFKT_OK;
 }
 
 template <typename real>
 tfkt_status do_fields(Ctx* c, uint32_t mask, double* dst, int dst_is_device) {
   const Lattice& L = c->L;
-  tfkt_status s = check_err(c);
-  if (s != TFKT_OK) return s;
-  s = ensure_moments<real>(c);
+  tfkt_status s = ensure_moments<real>(c);
   if (s != TFKT_OK) return s;
   KernelArgs<real> a = make_args<real>(c);
   TFKT_CUDA(c, launch_velocity<real>(a, c->stream));
@@ -509,9 +438,7 @@ tfkt_status do_fields(Ctx* c, uint32_t mask, double* dst, int dst_is_device) {
 template <typename real>
 tfkt_status do_psi(Ctx* c, double* dst, int dst_is_device) {
   const Lattice& L = c->L;
-  tfkt_status s = check_err(c);
-  if (s != TFKT_OK) return s;
-  s = ensure_moments<real>(c);
+  tfkt_status s = ensure_moments<real>(c);
   if (s != TFKT_OK) return s;
   KernelArgs<real> a = make_args<real>(c);
   const size_t bytes = (size_t)L.nq * L.nx * L.ny * sizeof(double);
@@ -544,9 +471,7 @@ tfkt_status do_populations(Ctx* c, double* host) {
 
 template <typename real>
 tfkt_status do_diag(Ctx* c, double* out) {
-  tfkt_status s = check_err(c);
-  if (s != TFKT_OK) return s;
-  s = ensure_moments<real>(c);
+  tfkt_status s = ensure_moments<real>(c);
   if (s != TFKT_OK) return s;
   KernelArgs<real> a = make_args<real>(c);
   TFKT_CUDA(c, launch_velocity<real>(a, c->stream));
@@ -601,7 +526,6 @@ tfkt_status tfkt_create(const tfkt_params* p, const double* perturb, void* dev_w
   c->L = L;
   c->stream = (cudaStream_t)stream;
   c->fused = fused_supported(L.nx, L.ny, L.nq, real_size(L));
-  c->tma = c->fused && tma_supported(L.nx, L.ny, L.nq, L.precision);
   const size_t need = layout(L, &c->ws);
   c->diag_blocks = diag_blocks_for(L);
   if (dev_workspace) {
@@ -625,22 +549,6 @@ tfkt_status tfkt_create(const tfkt_params* p, const double* perturb, void* dev_w
     c->ws.owned = true;
   }
   c->ws.bytes = need;
-  if (c->tma) {
-    s = encode_maps(c);
-    if (s != TFKT_OK) {
-      if (c->ws.owned) cudaFree(c->ws.base);
-      delete c;
-      return s;
-    }
-  }
-  {
-    cudaError_t e = cudaMemsetAsync(err_flag(c), 0, sizeof(int), c->stream);
-    if (e != cudaSuccess) {
-      if (c->ws.owned) cudaFree(c->ws.base);
-      delete c;
-      return fail(TFKT_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
-    }
-  }
   HostTables t = build_tables(L);
   s = L.precision == TFKT_FP64 ? upload_tables<double>(c, t) : upload_tables<float>(c, t);
   if (s == TFKT_OK) s = DISPATCH(c, init_state, c, perturb);
@@ -753,7 +661,7 @@ tfkt_status tfkt_sync(tfkt_ctx* c) {
   tfkt_status s = check_ctx(c);
   if (s != TFKT_OK) return s;
   TFKT_CUDA(c, cudaStreamSynchronize(c->stream));
-  return check_err(c);
+  return TFKT_OK;
 }
 
 tfkt_status tfkt_destroy(tfkt_ctx* c) {
@@ -776,7 +684,6 @@ const char* tfkt_status_string(tfkt_status s) {
     case TFKT_ECUDA: return "CUDA error";
     case TFKT_ENAN: return "non-finite value";
     case TFKT_ESTATE: return "context poisoned";
-    case TFKT_ETIMEOUT: return "bounded wait gave up";
   }
   return "unknown status";
 }

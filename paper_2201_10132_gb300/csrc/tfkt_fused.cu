@@ -16,8 +16,6 @@
 // M planes written for step n+1: interior nodes get final values (delta psi,
 // delta rho, J, delta Theta); border nodes get the tile's raw partial sums in
 // the delta psi, delta rho and J planes, completed by the fix-up kernel.
-#include <cuda.h>
-
 #include <type_traits>
 #include <utility>
 
@@ -58,9 +56,6 @@ __device__ __forceinline__ void ring_coords(int k, int& ex, int& ey) {
 __host__ __device__ constexpr int qgroup(const V4 c) { return (c.qy + 1) * 3 + (c.qx + 1); }
 __host__ __device__ constexpr int qgroup9(int cx, int cy) { return (cy + 1) * 3 + (cx + 1); }
 
-__device__ __forceinline__ bool in_tile(int x, int y) {
-  return x >= 0 && x < TX && y >= 0 && y < TY;
-}
 
 template <typename T>
 __device__ __forceinline__ T __int_as_T(int v) {
@@ -78,7 +73,6 @@ __device__ __forceinline__ void acc(real& sum, real v) {
 
 // Velocities 1..20 move in r (they reach other r-nodes); 0 and 21..24 do not.
 __host__ __device__ constexpr bool moves_r(int i) { return i >= 1 && i <= 20; }
-__host__ __device__ constexpr int rbit(int cx, int cy) { return (cy + 1) * 3 + (cx + 1); }
 
 // Loads N values (N a multiple of the vector width) from 16-byte aligned shared memory.
 template <int N, typename T>
@@ -104,36 +98,59 @@ __device__ __forceinline__ void load_vec(T* out, const T* src) {
   }
 }
 
-constexpr int HBW = TX + 1;      // padded row of the post-collision exchange buffer
-constexpr int HBS = TY * HBW;    // one velocity's plane in that buffer
+constexpr int HX = TX + 4;       // exchange-buffer row: the tile plus a 2-node zero halo
+constexpr int HY = TY + 4;
+constexpr int HSZ = HX * HY;     // one velocity's plane in the exchange buffer
 constexpr int DQ = 28;           // per-Q-node stride of the shift table (vector loads)
 constexpr int GQ = 12;           // per-Q-node stride of the target table (vector loads)
 
 template <typename real>
 struct Smem {
-  real* hb;      // [20][TY][HBW] post-collision values of the r-moving velocities
-  real* A;       // [nq][NT] own-node arrival sums per Q-node
-  real* Ar;      // [nq][RING] ring-node arrival sums per Q-node
-  real* Ux;      // [TY+2][TX+2]
+  real* hb;          // [20][HY][HX] collided values of the r-moving velocities, zero halo
+  real* A;           // [nq][NT] own-node arrival sums per Q-node
+  real* Ar;          // [nq][RING] ring-node arrival sums per Q-node
+  real* Ux;          // [TY+2][TX+2]
   real* Uy;
-  real* delta;   // [nq][DQ] pull shift differences
-  int* tgt;      // [nq][GQ] target Q-node of each Q-displacement group, -1: bounce-back
-  int* pull;     // [nq*25] pull source plane (>= 0) or ~plane for bounce-back
+  long long* poff;   // [nq*25] element offset of each pull's source plane
+  real* delta;       // [nq][DQ] pull shift differences
+  int* tgt;          // [nq][GQ] target Q-node of each Q-displacement group, -1: bounce-back
 };
 
 template <typename real>
-__device__ __forceinline__ Smem<real> carve(void* base, int nq) {
+__host__ __device__ constexpr size_t smem_layout(int nq, size_t* o_A, size_t* o_Ar, size_t* o_U,
+                                                 size_t* o_poff, size_t* o_delta, size_t* o_tgt) {
+  size_t o = sizeof(real) * 20 * HSZ;
+  *o_A = o;
+  o += sizeof(real) * (size_t)nq * NT;
+  *o_Ar = o;
+  o += sizeof(real) * (size_t)nq * RING;
+  *o_U = o;
+  o += sizeof(real) * 2 * (TY + 2) * (TX + 2);
+  o = (o + 15) & ~(size_t)15;
+  *o_poff = o;
+  o += sizeof(long long) * (size_t)nq * 25;
+  o = (o + 15) & ~(size_t)15;
+  *o_delta = o;
+  o += sizeof(real) * (size_t)nq * DQ;
+  o = (o + 15) & ~(size_t)15;
+  *o_tgt = o;
+  o += sizeof(int) * (size_t)nq * GQ;
+  return o;
+}
+
+template <typename real>
+__device__ __forceinline__ Smem<real> carve(unsigned char* base, int nq) {
+  size_t oA, oAr, oU, op, od, ot;
+  smem_layout<real>(nq, &oA, &oAr, &oU, &op, &od, &ot);
   Smem<real> s;
-  real* p = (real*)base;
-  s.hb = p; p += 20 * HBS;
-  s.A = p; p += (size_t)nq * NT;
-  s.Ar = p; p += (size_t)nq * RING;
-  s.Ux = p; p += (TY + 2) * (TX + 2);
-  s.Uy = p; p += (TY + 2) * (TX + 2);
-  p = (real*)(((uintptr_t)p + 15) & ~(uintptr_t)15);
-  s.delta = p; p += (size_t)nq * DQ;
-  s.tgt = (int*)(((uintptr_t)p + 15) & ~(uintptr_t)15);
-  s.pull = s.tgt + (size_t)nq * GQ;
+  s.hb = (real*)base;
+  s.A = (real*)(base + oA);
+  s.Ar = (real*)(base + oAr);
+  s.Ux = (real*)(base + oU);
+  s.Uy = s.Ux + (TY + 2) * (TX + 2);
+  s.poff = (long long*)(base + op);
+  s.delta = (real*)(base + od);
+  s.tgt = (int*)(base + ot);
   return s;
 }
 
@@ -185,16 +202,17 @@ step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
   off[6] = yp * pitch + xm; off[7] = yp * pitch + x; off[8] = yp * pitch + xp;
   const uint32_t n = off[4];
 
-  // ---- stage: tables, zeroed accumulators, U on the tile and its 1-node ring
+  // ---- stage: tables, zeroed accumulators and exchange halo, U on the tile and its ring
   for (int k = tid; k < nq * GQ; k += NT) {
     const int q = k / GQ, g = k % GQ;
     sm.tgt[k] = g < 9 ? fa.tgt[q * 9 + g] : -1;
   }
-  for (int k = tid; k < nq * 25; k += NT) sm.pull[k] = a.tab.pull[k];
+  for (int k = tid; k < nq * 25; k += NT) sm.poff[k] = fa.poff[k];
   for (int k = tid; k < nq * DQ; k += NT) {
     const int q = k / DQ, i = k % DQ;
     sm.delta[k] = i < 25 ? a.tab.delta[q * 25 + i] : real(0);
   }
+  for (int k = tid; k < 20 * HSZ; k += NT) sm.hb[k] = real(0);
   for (int p = 0; p < nq; ++p) sm.A[p * NT + tid] = real(0);
   for (int k = tid; k < nq * RING; k += NT) sm.Ar[k] = real(0);
   for (int k = tid; k < (TX + 2) * (TY + 2); k += NT) {
@@ -216,20 +234,13 @@ step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
   const real G10 = real(0.5) * (sm.Ux[c + TX + 2] - sm.Ux[c - TX - 2]);          // d_y U_x
   const real G11 = real(0.5) * (sm.Uy[c + TX + 2] - sm.Uy[c - TX - 2]);          // d_y U_y
 
-  // sources inside the tile, per r-displacement: own node and (threads < RING) ring node
-  uint32_t vmask = 0, rmask = 0;
+  // exchange-buffer cells: own node, and (threads < RING) one ring node; a
+  // source outside the tile falls on the zero halo, so the sums need no masks
+  const int hcell = (ly + 2) * HX + (lx + 2);
   const bool ring_thread = tid < RING;
   int rex = 0, rey = 0;
   if (ring_thread) ring_coords(tid, rex, rey);
-#pragma unroll
-  for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-    for (int dx = -1; dx <= 1; ++dx) {
-      if (in_tile(lx - dx, ly - dy)) vmask |= 1u << rbit(dx, dy);
-      if (ring_thread && in_tile(rex - dx, rey - dy)) rmask |= 1u << rbit(dx, dy);
-    }
-  const int rbase = rey * HBW + rex;
-  const int hbo = ly * HBW + lx;
+  const int rcell = (rey + 2) * HX + (rex + 2);
 
   const real rho = a.rho0 + Min[(size_t)(nq + M_DRHO) * P + n];
   const real force = rho * a.tab.arow[y];
@@ -268,59 +279,56 @@ step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
       const real hp = a.om2b * h[i] + a.tb * feq_dev + a.omb * real(w9(i)) * gx * force;
       dst[(size_t)i * P + n] = hp;
       if constexpr (i == 0) ms_arr += hp;
-      else sm.hb[(i - 1) * HBS + hbo] = hp;
+      else sm.hb[(i - 1) * HSZ + hcell] = hp;
     });
   }
   __syncthreads();
   static_for<1, 8>([&](auto I) {
     constexpr int i = I;
-    constexpr int k = rbit(c9x(i), c9y(i));
-    if ((vmask >> k) & 1u) {
-      const real v = sm.hb[(i - 1) * HBS + hbo - (c9y(i) * HBW + c9x(i))];
-      ms_arr += v;
-      acc<c9x(i)>(jx_arr, v);
-      acc<c9y(i)>(jy_arr, v);
-    }
+    const real v = sm.hb[(i - 1) * HSZ + hcell - (c9y(i) * HX + c9x(i))];
+    ms_arr += v;
+    acc<c9x(i)>(jx_arr, v);
+    acc<c9y(i)>(jy_arr, v);
   });
   if (ring_thread) {
     static_for<1, 8>([&](auto I) {
       constexpr int i = I;
-      constexpr int k = rbit(c9x(i), c9y(i));
-      if ((rmask >> k) & 1u) {
-        const real v = sm.hb[(i - 1) * HBS + rbase - (c9y(i) * HBW + c9x(i))];
-        ms_r += v;
-        acc<c9x(i)>(jx_r, v);
-        acc<c9y(i)>(jy_r, v);
-      }
+      const real v = sm.hb[(i - 1) * HSZ + rcell - (c9y(i) * HX + c9x(i))];
+      ms_r += v;
+      acc<c9x(i)>(jx_r, v);
+      acc<c9y(i)>(jy_r, v);
     });
   }
   __syncthreads();
 
   // ---- polymer, one Q-node at a time
   for (int q = 0; q < nq; ++q) {
-    real h[25];
-    {
-      real dl[DQ];
-      load_vec<DQ>(dl, sm.delta + q * DQ);
-#pragma unroll
-      for (int i = 0; i < 25; ++i) {
-        const V4 cv = c25(i);
-        const int e = sm.pull[q * 25 + i];
-        const uint32_t o = e >= 0 ? off[shift_index(-cv.rx, -cv.ry)] : off[4];
-        const int pl = e >= 0 ? e : ~e;
-        h[i] = src[(size_t)pl * P + o] + dl[i];
-      }
-    }
-    const real* Mq = Min + (size_t)q * P;
-    const real dpx = real(0.5) * (Mq[off[5]] - Mq[off[3]]);
-    const real dpy = real(0.5) * (Mq[off[7]] - Mq[off[1]]);
-
     int tg[GQ];
     load_vec<GQ>(tg, sm.tgt + q * GQ);
     uint32_t bm = 0;
 #pragma unroll
     for (int g = 0; g < 9; ++g)
       if (tg[g] < 0) bm |= 1u << g;
+    real h[25];
+    {
+      real dl[DQ];
+      load_vec<DQ>(dl, sm.delta + q * DQ);
+      const long long* po = sm.poff + q * 25;
+      static_for<0, 25>([&](auto I) {
+        constexpr int i = I;
+        constexpr V4 cv = c25(i);
+        constexpr int g = qgroup(cv);
+        uint32_t o = off[shift_index(-cv.rx, -cv.ry)];
+        if constexpr (moves_r(i)) {
+          // the pull bounces when q - Qdot leaves the disk: the opposite group 8 - g
+          if ((bm >> (8 - g)) & 1u) o = off[4];
+        }
+        h[i] = src[po[i] + o] + dl[i];
+      });
+    }
+    const real* Mq = Min + (size_t)q * P;
+    const real dpx = real(0.5) * (Mq[off[5]] - Mq[off[3]]);
+    const real dpy = real(0.5) * (Mq[off[7]] - Mq[off[1]]);
     real dpsi = 0, rx = 0, ry = 0, qx = 0, qy = 0;
     static_for<0, 25>([&](auto I) {
       constexpr int i = I;
@@ -356,19 +364,21 @@ step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
       const real hp = a.om2b * h[i] + a.tb * real(w25(i)) * d;
       dq[(size_t)i * P] = hp;
       constexpr int g = qgroup(c25(i));
+      const bool b = (bm >> g) & 1u;
       if constexpr (!moves_r(i)) {
         // stays at this r-node: lands on Q-node q + Qdot, or bounces back to q
-        if ((bm >> g) & 1u) grp[4] += hp;
-        else grp[g] += hp;
-      } else {
-        if ((bm >> g) & 1u) {
-          // bounces back to (r, q) moving with -c
-          grp[4] += hp;
-          acc<-c25(i).rx>(jx_arr, hp);
-          acc<-c25(i).ry>(jy_arr, hp);
-        } else {
-          sm.hb[(i - 1) * HBS + hbo] = hp;
+        if constexpr (g == 4) grp[4] += hp;
+        else {
+          grp[4] += b ? hp : real(0);
+          grp[g] += b ? real(0) : hp;
         }
+      } else {
+        // a bounced value returns to (r, q) moving with -c; it is not exchanged
+        const real back = b ? hp : real(0);
+        sm.hb[(i - 1) * HSZ + hcell] = b ? real(0) : hp;
+        grp[4] += back;
+        acc<-c25(i).rx>(jx_arr, back);
+        acc<-c25(i).ry>(jy_arr, back);
       }
     });
     __syncthreads();
@@ -376,13 +386,10 @@ step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
     static_for<1, 20>([&](auto I) {
       constexpr int i = I;
       constexpr V4 cv = c25(i);
-      constexpr int g = qgroup(cv);
-      if (!((bm >> g) & 1u) && ((vmask >> rbit(cv.rx, cv.ry)) & 1u)) {
-        const real v = sm.hb[(i - 1) * HBS + hbo - (cv.ry * HBW + cv.rx)];
-        grp[g] += v;
-        acc<cv.rx>(jx_arr, v);
-        acc<cv.ry>(jy_arr, v);
-      }
+      const real v = sm.hb[(i - 1) * HSZ + hcell - (cv.ry * HX + cv.rx)];
+      grp[qgroup(cv)] += v;
+      acc<cv.rx>(jx_arr, v);
+      acc<cv.ry>(jy_arr, v);
     });
 #pragma unroll
     for (int g = 0; g < 9; ++g) {
@@ -396,13 +403,10 @@ step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
       static_for<1, 20>([&](auto I) {
         constexpr int i = I;
         constexpr V4 cv = c25(i);
-        constexpr int g = qgroup(cv);
-        if (!((bm >> g) & 1u) && ((rmask >> rbit(cv.rx, cv.ry)) & 1u)) {
-          const real v = sm.hb[(i - 1) * HBS + rbase - (cv.ry * HBW + cv.rx)];
-          gr[g] += v;
-          acc<cv.rx>(jx_r, v);
-          acc<cv.ry>(jy_r, v);
-        }
+        const real v = sm.hb[(i - 1) * HSZ + rcell - (cv.ry * HX + cv.rx)];
+        gr[qgroup(cv)] += v;
+        acc<cv.rx>(jx_r, v);
+        acc<cv.ry>(jy_r, v);
       });
 #pragma unroll
       for (int g = 0; g < 9; ++g) {
@@ -414,500 +418,6 @@ step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
   }
 
   // ---- flush the next step's moments
-  const bool border = lx == 0 || lx == TX - 1 || ly == 0 || ly == TY - 1;
-  if (!border) {
-    real drho = ms_arr, txx = 0, txy = 0, tyy = 0;
-    for (int p = 0; p < nq; ++p) {
-      const real d = sm.A[p * NT + tid] + fa.dpsi[p];
-      Mout[(size_t)p * P + n] = d;
-      drho += d;
-      const real Qx = a.tab.qx[p], Qy = a.tab.qy[p];
-      txx += d * Qx * Qx;
-      txy += d * Qx * Qy;
-      tyy += d * Qy * Qy;
-    }
-    Mout[(size_t)(nq + M_DRHO) * P + n] = drho;
-    Mout[(size_t)(nq + M_JX) * P + n] = jx_arr + fa.dvx;
-    Mout[(size_t)(nq + M_JY) * P + n] = jy_arr + fa.dvy;
-    Mout[(size_t)(nq + M_THXX) * P + n] = a.hl2h * txx;
-    Mout[(size_t)(nq + M_THXY) * P + n] = a.hl2h * txy;
-    Mout[(size_t)(nq + M_THYY) * P + n] = a.hl2h * tyy;
-  } else {
-    for (int p = 0; p < nq; ++p) Mout[(size_t)p * P + n] = sm.A[p * NT + tid];
-    Mout[(size_t)(nq + M_DRHO) * P + n] = ms_arr;
-    Mout[(size_t)(nq + M_JX) * P + n] = jx_arr;
-    Mout[(size_t)(nq + M_JY) * P + n] = jy_arr;
-  }
-  if (ring_thread) {
-    const size_t ntiles = (size_t)gridDim.x * gridDim.y;
-    const size_t tile = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
-    real* ex = fa.exports;
-    for (int p = 0; p < nq; ++p) ex[((size_t)p * ntiles + tile) * RING + tid] = sm.Ar[p * RING + tid];
-    ex[((size_t)(nq + 0) * ntiles + tile) * RING + tid] = ms_r;
-    ex[((size_t)(nq + 1) * ntiles + tile) * RING + tid] = jx_r;
-    ex[((size_t)(nq + 2) * ntiles + tile) * RING + tid] = jy_r;
-  }
-}
-
-// ------------------------------------------------------------------------
-// TMA variant of the fused step (FP32 storage). One elected thread moves the
-// populations between HBM and shared memory with cp.async.bulk.tensor: per
-// velocity a 16-byte aligned box of (TX + 2 PADX) x TY source elements that
-// covers the +-1 pull shifts, double-buffered over Q-nodes and tracked by
-// mbarriers; the collided values of a Q-node are written to a shared tile that
-// feeds both the bulk tensor stores and the moment gather. Sources that wrap
-// around the periodic grid edge fall outside the box (the copy fills zeros
-// there) and are read directly by the few edge threads that need them.
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ void tma_load3(void* dst, const CUtensorMap* map, int x, int y, int z,
-                                          uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
-      "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ void tma_store3(const CUtensorMap* map, int x, int y, int z,
-                                           const void* src) {
-  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
-                   (uint64_t)map),
-               "r"(x), "r"(y), "r"(z), "r"(smem_u32(src))
-               : "memory");
-}
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void bulk_wait_read() {
-  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
-}
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// Bounded wait on a stage barrier: gives up after a fixed number of polls and
-// records the failure (the kernel then runs to its end without further waits,
-// so every thread reaches every block barrier; the host reports the error).
-constexpr int kWaitPolls = 1 << 18;
-__device__ __forceinline__ bool stage_wait(uint64_t* bar, uint32_t parity, bool& failed, int* err) {
-  if (failed) return false;
-  for (int it = 0; it < kWaitPolls; ++it)
-    if (mbar_try_wait(bar, parity)) return true;
-  failed = true;
-  atomicOr(err, 1);
-  return false;
-}
-
-// r_y component of D4Q25 velocity i for a runtime i.
-__device__ __forceinline__ int c25_ry(int i) {
-  int r = 0;
-  static_for<0, 25>([&](auto I) {
-    if (i == I) r = c25(I).ry;
-  });
-  return r;
-}
-
-template <typename real>
-struct TmaGeom {
-  static constexpr int PADX = 16 / (int)sizeof(real);  // aligned start x0 - PADX
-  static constexpr int BX = TX + 2 * PADX;             // load box width
-  static constexpr int BOX = BX * TY;                  // elements per load box
-  static constexpr int SBOX = TX * TY;                 // elements per store box
-};
-
-template <typename real>
-struct TmaSmem {
-  uint64_t* bar;   // [2] stage barriers
-  real* stage;     // [2][25][BOX]
-  real* out;       // [2][25][SBOX] collided values (bulk store source, gather source)
-  real* A;         // [nq][NT]
-  real* Ar;        // [nq][RING]
-  real* Ux;
-  real* Uy;
-  real* delta;     // [nq][DQ]
-  int* tgt;        // [nq][GQ]
-  int* pull;       // [nq*25]
-};
-
-template <typename real>
-__host__ __device__ constexpr size_t tma_smem_layout(int nq, size_t* o_stage, size_t* o_out,
-                                                     size_t* o_A, size_t* o_Ar, size_t* o_U,
-                                                     size_t* o_delta, size_t* o_tgt,
-                                                     size_t* o_pull) {
-  using G = TmaGeom<real>;
-  size_t o = 128;  // barriers
-  *o_stage = o;
-  o += sizeof(real) * 2 * 25 * G::BOX;
-  o = (o + 127) & ~(size_t)127;
-  *o_out = o;
-  o += sizeof(real) * 2 * 25 * G::SBOX;
-  *o_A = o;
-  o += sizeof(real) * (size_t)nq * NT;
-  *o_Ar = o;
-  o += sizeof(real) * (size_t)nq * RING;
-  *o_U = o;
-  o += sizeof(real) * 2 * (TY + 2) * (TX + 2);
-  o = (o + 15) & ~(size_t)15;
-  *o_delta = o;
-  o += sizeof(real) * (size_t)nq * DQ;
-  o = (o + 15) & ~(size_t)15;
-  *o_tgt = o;
-  o += sizeof(int) * (size_t)nq * GQ;
-  *o_pull = o;
-  o += sizeof(int) * (size_t)nq * 25;
-  return o;
-}
-
-template <typename real>
-__device__ __forceinline__ TmaSmem<real> tma_carve(unsigned char* base, int nq) {
-  size_t os, oo, oa, oar, ou, od, ot, op;
-  tma_smem_layout<real>(nq, &os, &oo, &oa, &oar, &ou, &od, &ot, &op);
-  TmaSmem<real> s;
-  s.bar = (uint64_t*)base;
-  s.stage = (real*)(base + os);
-  s.out = (real*)(base + oo);
-  s.A = (real*)(base + oa);
-  s.Ar = (real*)(base + oar);
-  s.Ux = (real*)(base + ou);
-  s.Uy = s.Ux + (TY + 2) * (TX + 2);
-  s.delta = (real*)(base + od);
-  s.tgt = (int*)(base + ot);
-  s.pull = (int*)(base + op);
-  return s;
-}
-
-// Called by all 32 lanes of warp 0: lane 0 arms the stage barrier, then lanes
-// 0..24 each start the copy of one velocity's source box.
-template <typename real>
-__device__ __forceinline__ void issue_polymer(const TmaSmem<real>& sm, const CUtensorMap* tm, int q,
-                                              int x0, int y0, int stage, int lane) {
-  using G = TmaGeom<real>;
-  uint64_t* bar = sm.bar + stage;
-  real* dst = sm.stage + (size_t)stage * 25 * G::BOX;
-  if (lane == 0) mbar_expect_tx(bar, 25u * G::BOX * (uint32_t)sizeof(real));
-  __syncwarp();
-  if (lane < 25) {
-    const int e = sm.pull[q * 25 + lane];
-    const int plane = e >= 0 ? e : ~e;
-    const int ys = e >= 0 ? y0 - c25_ry(lane) : y0;
-    tma_load3(dst + lane * G::BOX, tm, x0 - G::PADX, ys, plane, bar);
-  }
-}
-
-template <typename real>
-__global__ void __launch_bounds__(NT, 1)
-step_tma_kernel(KernelArgs<real> a, FusedArgs<real> fa, const __grid_constant__ CUtensorMap tmL,
-                const __grid_constant__ CUtensorMap tmS9, const __grid_constant__ CUtensorMap tmS25,
-                int* err) {
-  using G = TmaGeom<real>;
-  extern __shared__ __align__(1024) unsigned char smem_tma[];
-  const int nq = a.nq;
-  TmaSmem<real> sm = tma_carve<real>(smem_tma, nq);
-  const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * TX + lx;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  const int x = x0 + lx, y = y0 + ly;
-  const bool leader = tid == 0;
-  const bool warp0 = tid < 32;
-  const size_t P = a.plane;
-  const real* __restrict__ Min = fa.Min;
-  real* __restrict__ Mout = fa.Mout;
-  const real* __restrict__ src = a.src;
-
-  const int xm = x == 0 ? a.nx - 1 : x - 1, xp = x == a.nx - 1 ? 0 : x + 1;
-  const int ym = y == 0 ? a.ny - 1 : y - 1, yp = y == a.ny - 1 ? 0 : y + 1;
-  const int pitch = (int)a.pitch;
-  uint32_t off[9];
-  off[0] = ym * pitch + xm; off[1] = ym * pitch + x; off[2] = ym * pitch + xp;
-  off[3] = y * pitch + xm;  off[4] = y * pitch + x;  off[5] = y * pitch + xp;
-  off[6] = yp * pitch + xm; off[7] = yp * pitch + x; off[8] = yp * pitch + xp;
-  const uint32_t n = off[4];
-  // edge threads whose shifted source wraps around the periodic grid
-  const bool wxm = x0 == 0 && lx == 0, wxp = x0 + TX == a.nx && lx == TX - 1;
-  const bool wym = y0 == 0 && ly == 0, wyp = y0 + TY == a.ny && ly == TY - 1;
-
-  if (leader) {
-    mbar_init(sm.bar + 0, 1);
-    mbar_init(sm.bar + 1, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  for (int k = tid; k < nq * GQ; k += NT) {
-    const int q = k / GQ, g = k % GQ;
-    sm.tgt[k] = g < 9 ? fa.tgt[q * 9 + g] : -1;
-  }
-  for (int k = tid; k < nq * 25; k += NT) sm.pull[k] = a.tab.pull[k];
-  for (int k = tid; k < nq * DQ; k += NT) {
-    const int q = k / DQ, i = k % DQ;
-    sm.delta[k] = i < 25 ? a.tab.delta[q * 25 + i] : real(0);
-  }
-  for (int p = 0; p < nq; ++p) sm.A[p * NT + tid] = real(0);
-  for (int k = tid; k < nq * RING; k += NT) sm.Ar[k] = real(0);
-  __syncthreads();
-  // loads #0 (solvent) into stage 0 and #1 (Q-node 0) into stage 1
-  if (warp0) {
-    if (leader) mbar_expect_tx(sm.bar + 0, 9u * G::BOX * (uint32_t)sizeof(real));
-    __syncwarp();
-    if (tid < 9) tma_load3(sm.stage + tid * G::BOX, &tmL, x0 - G::PADX, y0 - c9y(tid), tid, sm.bar + 0);
-    issue_polymer(sm, &tmL, 0, x0, y0, 1, tid);
-  }
-  for (int k = tid; k < (TX + 2) * (TY + 2); k += NT) {
-    const int hx = k % (TX + 2), hy = k / (TX + 2);
-    int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
-    gx = gx < 0 ? gx + a.nx : (gx >= a.nx ? gx - a.nx : gx);
-    gy = gy < 0 ? gy + a.ny : (gy >= a.ny ? gy - a.ny : gy);
-    real ux, uy;
-    velocity_at(a, Min, gx, gy, ux, uy);
-    sm.Ux[k] = ux;
-    sm.Uy[k] = uy;
-  }
-  __syncthreads();
-
-  const int c = (ly + 1) * (TX + 2) + (lx + 1);
-  const real Ux = sm.Ux[c], Uy = sm.Uy[c];
-  const real G00 = real(0.5) * (sm.Ux[c + 1] - sm.Ux[c - 1]);
-  const real G01 = real(0.5) * (sm.Uy[c + 1] - sm.Uy[c - 1]);
-  const real G10 = real(0.5) * (sm.Ux[c + TX + 2] - sm.Ux[c - TX - 2]);
-  const real G11 = real(0.5) * (sm.Uy[c + TX + 2] - sm.Uy[c - TX - 2]);
-
-  uint32_t vmask = 0, rmask = 0;
-  const bool ring_thread = tid < RING;
-  int rex = 0, rey = 0;
-  if (ring_thread) ring_coords(tid, rex, rey);
-#pragma unroll
-  for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-    for (int dx = -1; dx <= 1; ++dx) {
-      if (in_tile(lx - dx, ly - dy)) vmask |= 1u << rbit(dx, dy);
-      if (ring_thread && in_tile(rex - dx, rey - dy)) rmask |= 1u << rbit(dx, dy);
-    }
-  const int rbase = rey * TX + rex;   // dense rows in the output tile
-
-  const real rho = a.rho0 + Min[(size_t)(nq + M_DRHO) * P + n];
-  const real force = rho * a.tab.arow[y];
-  real jx_arr = 0, jy_arr = 0, ms_arr = 0;
-  real jx_r = 0, jy_r = 0, ms_r = 0;
-  bool failed = false;
-
-  // ---- solvent (load #0, stage 0; collided values in output buffer 1)
-  {
-    stage_wait(sm.bar + 0, 0, failed, err);
-    const real* stg = sm.stage;
-    real* outb = sm.out + (size_t)1 * 25 * G::SBOX;
-    real h[9];
-    real drs = 0, jsx = 0, jsy = 0;
-    static_for<0, 9>([&](auto I) {
-      constexpr int i = I;
-      constexpr int cx = c9x(i), cy = c9y(i);
-      const bool direct = (cx == 1 && wxm) || (cx == -1 && wxp) || (cy == 1 && wym) ||
-                          (cy == -1 && wyp);
-      h[i] = direct ? src[(size_t)i * P + off[shift_index(-cx, -cy)]]
-                    : stg[i * G::BOX + ly * G::BX + lx + G::PADX - cx];
-      drs += h[i];
-      acc<cx>(jsx, h[i]);
-      acc<cy>(jsy, h[i]);
-    });
-    const real rs = real(1) + drs;
-    const real jfx = (a.c2 * jsx + rs * Ux + a.tau2 * force) * a.inv_c2p1;
-    const real jfy = (a.c2 * jsy + rs * Uy) * a.inv_c2p1;
-    const real usx = jfx / rs, usy = jfy / rs;
-    const real vx = a.omr * usx + a.r * Ux, vy = a.omr * usy + a.r * Uy;
-    const real sq = a.omr * (usx * usx + usy * usy) + a.r * (Ux * Ux + Uy * Uy);
-    static_for<0, 9>([&](auto I) {
-      constexpr int i = I;
-      real cus = 0, cu = 0, cv = 0;
-      acc<c9x(i)>(cus, usx); acc<c9y(i)>(cus, usy);
-      acc<c9x(i)>(cu, Ux);   acc<c9y(i)>(cu, Uy);
-      acc<c9x(i)>(cv, vx);   acc<c9y(i)>(cv, vy);
-      real gx = -real(3) * Ux;
-      acc<c9x(i)>(gx, real(3) + real(9) * cu);
-      const real feq_dev = real(w9(i)) * (drs + rs * (real(3) * cv +
-                                                      real(4.5) * (a.omr * cus * cus + a.r * cu * cu) -
-                                                      real(1.5) * sq));
-      const real hp = a.om2b * h[i] + a.tb * feq_dev + a.omb * real(w9(i)) * gx * force;
-      outb[i * G::SBOX + tid] = hp;
-      if constexpr (i == 0) ms_arr += hp;
-    });
-    fence_async_smem();
-    __syncthreads();
-    if (warp0) {
-      if (leader) {
-        tma_store3(&tmS9, x0, y0, 0, outb);   // the 9 solvent planes as one box
-        bulk_commit();
-      }
-      if (nq > 1) issue_polymer(sm, &tmL, 1, x0, y0, 0, tid);
-    }
-    static_for<1, 8>([&](auto I) {
-      constexpr int i = I;
-      if ((vmask >> rbit(c9x(i), c9y(i))) & 1u) {
-        const real v = outb[i * G::SBOX + tid - (c9y(i) * TX + c9x(i))];
-        ms_arr += v;
-        acc<c9x(i)>(jx_arr, v);
-        acc<c9y(i)>(jy_arr, v);
-      }
-    });
-    if (ring_thread) {
-      static_for<1, 8>([&](auto I) {
-        constexpr int i = I;
-        if ((rmask >> rbit(c9x(i), c9y(i))) & 1u) {
-          const real v = outb[i * G::SBOX + rbase - (c9y(i) * TX + c9x(i))];
-          ms_r += v;
-          acc<c9x(i)>(jx_r, v);
-          acc<c9y(i)>(jy_r, v);
-        }
-      });
-    }
-  }
-
-  // ---- polymer: Q-node q is load #(q + 1) in stage (q + 1) & 1; output buffer q & 1
-  for (int q = 0; q < nq; ++q) {
-    const int stage = (q + 1) & 1;
-    stage_wait(sm.bar + stage, ((q + 1) >> 1) & 1, failed, err);
-    const real* stg = sm.stage + (size_t)stage * 25 * G::BOX;
-    real* outb = sm.out + (size_t)(q & 1) * 25 * G::SBOX;
-    real h[25];
-    {
-      real dl[DQ];
-      load_vec<DQ>(dl, sm.delta + q * DQ);
-      static_for<0, 25>([&](auto I) {
-        constexpr int i = I;
-        constexpr V4 cv = c25(i);
-        const int e = sm.pull[q * 25 + i];
-        real v;
-        if (e >= 0) {
-          const bool direct = (cv.rx == 1 && wxm) || (cv.rx == -1 && wxp) ||
-                              (cv.ry == 1 && wym) || (cv.ry == -1 && wyp);
-          v = direct ? src[(size_t)e * P + off[shift_index(-cv.rx, -cv.ry)]]
-                     : stg[i * G::BOX + ly * G::BX + lx + G::PADX - cv.rx];
-        } else {
-          v = stg[i * G::BOX + ly * G::BX + lx + G::PADX];
-        }
-        h[i] = v + dl[i];
-      });
-    }
-    const real* Mq = Min + (size_t)q * P;
-    const real dpx = real(0.5) * (Mq[off[5]] - Mq[off[3]]);
-    const real dpy = real(0.5) * (Mq[off[7]] - Mq[off[1]]);
-    int tg[GQ];
-    load_vec<GQ>(tg, sm.tgt + q * GQ);
-    uint32_t bm = 0;
-#pragma unroll
-    for (int g = 0; g < 9; ++g)
-      if (tg[g] < 0) bm |= 1u << g;
-    real dpsi = 0, rx = 0, ry = 0, qx = 0, qy = 0;
-    static_for<0, 25>([&](auto I) {
-      constexpr int i = I;
-      dpsi += h[i];
-      acc<c25(i).rx>(rx, h[i]);
-      acc<c25(i).ry>(ry, h[i]);
-      acc<c25(i).qx>(qx, h[i]);
-      acc<c25(i).qy>(qy, h[i]);
-    });
-    const real Qx = a.tab.qx[q], Qy = a.tab.qy[q];
-    const real psi = a.tab.psi0[q] + dpsi;
-    const real qg = Qx * dpx + Qy * dpy;
-    const real jrex = psi * Ux + a.tau2 * a.hl2h * Qx * qg;
-    const real jrey = psi * Uy + a.tau2 * a.hl2h * Qy * qg;
-    const real jqex = psi * (Qx * G00 + Qy * G10 - a.kappa * Qx);
-    const real jqey = psi * (Qx * G01 + Qy * G11 - a.kappa * Qy);
-    const real mrx = real(3) * (a.omr * (a.c2 * rx + jrex) * a.inv_c2p1 + a.r * jrex);
-    const real mry = real(3) * (a.omr * (a.c2 * ry + jrey) * a.inv_c2p1 + a.r * jrey);
-    const real mqx = real(3) * (a.omr * (a.c2 * qx + jqex) * a.inv_c2p1 + a.r * jqex);
-    const real mqy = real(3) * (a.omr * (a.c2 * qy + jqey) * a.inv_c2p1 + a.r * jqey);
-    real grp[9];
-#pragma unroll
-    for (int g = 0; g < 9; ++g) grp[g] = real(0);
-    static_for<0, 25>([&](auto I) {
-      constexpr int i = I;
-      real d = dpsi;
-      acc<c25(i).rx>(d, mrx);
-      acc<c25(i).ry>(d, mry);
-      acc<c25(i).qx>(d, mqx);
-      acc<c25(i).qy>(d, mqy);
-      const real hp = a.om2b * h[i] + a.tb * real(w25(i)) * d;
-      outb[i * G::SBOX + tid] = hp;
-      constexpr int g = qgroup(c25(i));
-      if constexpr (!moves_r(i)) {
-        if ((bm >> g) & 1u) grp[4] += hp;
-        else grp[g] += hp;
-      } else {
-        if ((bm >> g) & 1u) {
-          grp[4] += hp;
-          acc<-c25(i).rx>(jx_arr, hp);
-          acc<-c25(i).ry>(jy_arr, hp);
-        }
-      }
-    });
-    fence_async_smem();
-    __syncthreads();   // collided tile complete; this stage consumed by every thread
-    if (warp0) {
-      if (leader) {
-        tma_store3(&tmS25, x0, y0, 9 + 25 * q, outb);   // the 25 planes of Q-node q as one box
-        bulk_commit();
-      }
-      if (q + 2 < nq) issue_polymer(sm, &tmL, q + 2, x0, y0, stage, tid);
-    }
-    static_for<1, 20>([&](auto I) {
-      constexpr int i = I;
-      constexpr V4 cv = c25(i);
-      constexpr int g = qgroup(cv);
-      if (!((bm >> g) & 1u) && ((vmask >> rbit(cv.rx, cv.ry)) & 1u)) {
-        const real v = outb[i * G::SBOX + tid - (cv.ry * TX + cv.rx)];
-        grp[g] += v;
-        acc<cv.rx>(jx_arr, v);
-        acc<cv.ry>(jy_arr, v);
-      }
-    });
-#pragma unroll
-    for (int g = 0; g < 9; ++g) {
-      const int t = g == 4 ? q : tg[g];
-      if (t >= 0) sm.A[t * NT + tid] += grp[g];
-    }
-    if (ring_thread) {
-      real gr[9];
-#pragma unroll
-      for (int g = 0; g < 9; ++g) gr[g] = real(0);
-      static_for<1, 20>([&](auto I) {
-        constexpr int i = I;
-        constexpr V4 cv = c25(i);
-        constexpr int g = qgroup(cv);
-        if (!((bm >> g) & 1u) && ((rmask >> rbit(cv.rx, cv.ry)) & 1u)) {
-          const real v = outb[i * G::SBOX + rbase - (cv.ry * TX + cv.rx)];
-          gr[g] += v;
-          acc<cv.rx>(jx_r, v);
-          acc<cv.ry>(jy_r, v);
-        }
-      });
-#pragma unroll
-      for (int g = 0; g < 9; ++g) {
-        const int t = g == 4 ? q : tg[g];
-        if (t >= 0) sm.Ar[t * RING + tid] += gr[g];
-      }
-    }
-    if (leader) bulk_wait_read<1>();   // the other output buffer may be rewritten
-    __syncthreads();
-  }
-  if (leader) bulk_wait_all();
-
-  // ---- flush the next step's moments (as in the register-load variant)
   const bool border = lx == 0 || lx == TX - 1 || ly == 0 || ly == TY - 1;
   if (!border) {
     real drho = ms_arr, txx = 0, txy = 0, tyy = 0;
@@ -1007,9 +517,9 @@ __global__ void __launch_bounds__(128) fixup_kernel(KernelArgs<real> a, FusedArg
 }  // namespace
 
 size_t fused_smem_bytes(int nq, size_t real_bytes) {
-  return real_bytes * (20 * HBS + (size_t)nq * NT + (size_t)nq * RING +
-                       2 * (TY + 2) * (TX + 2) + (size_t)nq * DQ) +
-         sizeof(int) * (size_t)nq * (GQ + 25) + 64;
+  size_t a, b, c, d, e, f;
+  return real_bytes == 8 ? smem_layout<double>(nq, &a, &b, &c, &d, &e, &f)
+                         : smem_layout<float>(nq, &a, &b, &c, &d, &e, &f);
 }
 
 size_t fused_export_elems(int nx, int ny, int nq) {
@@ -1040,7 +550,13 @@ cudaError_t launch_fixup(const KernelArgs<real>& a, const FusedArgs<real>& f, cu
 // (Q-node, Q-displacement group), -1 where the displacement leaves the disk;
 // the per-Q-node sum of the pull shift differences; their r-momentum sum.
 void fused_tables(const Lattice& L, const HostTables& t, std::vector<int>& tgt,
-                  std::vector<double>& dpsi, double& dvx, double& dvy) {
+                  std::vector<double>& dpsi, double& dvx, double& dvy,
+                  std::vector<long long>& poff) {
+  poff.resize((size_t)L.nq * 25);
+  for (size_t k = 0; k < poff.size(); ++k) {
+    const int e = t.pull[k];
+    poff[k] = (long long)(e >= 0 ? e : ~e) * (long long)L.plane;
+  }
   tgt.assign((size_t)L.nq * 9, -1);
   std::vector<int> qmap((size_t)L.S * L.S, -1);
   std::vector<int> gi(L.nq), gj(L.nq);
@@ -1065,28 +581,6 @@ void fused_tables(const Lattice& L, const HostTables& t, std::vector<int>& tgt,
       dvx += c25(i).rx * d;
       dvy += c25(i).ry * d;
     }
-}
-
-size_t tma_smem_bytes(int nq) {
-  size_t a, b, c, d, e, f, g, h;
-  return tma_smem_layout<float>(nq, &a, &b, &c, &d, &e, &f, &g, &h);
-}
-
-bool tma_supported(int nx, int ny, int nq, int precision) {
-  return precision == TFKT_FP32 && nx % TX == 0 && ny % TY == 0 &&
-         tma_smem_bytes(nq) <= 227 * 1024;
-}
-
-cudaError_t launch_step_tma(const KernelArgs<float>& a, const FusedArgs<float>& f,
-                            const CUtensorMap& load_map, const CUtensorMap& store9,
-                            const CUtensorMap& store25, int* err, cudaStream_t s) {
-  const size_t smem = tma_smem_bytes(a.nq);
-  cudaError_t e = cudaFuncSetAttribute(step_tma_kernel<float>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  step_tma_kernel<float><<<dim3(a.nx / TX, a.ny / TY), dim3(TX, TY), smem, s>>>(
-      a, f, load_map, store9, store25, err);
-  return cudaGetLastError();
 }
 
 #define TFKT_INSTANTIATE_FUSED(real)                                                           \

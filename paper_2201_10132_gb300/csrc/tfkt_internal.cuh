@@ -2,7 +2,6 @@
 // arguments and launchers. Not part of the C-ABI (include/tfkt.h is).
 #pragma once
 
-#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -112,6 +111,7 @@ struct FusedArgs {
   real* exports;        // [nq + 3][tiles][ring] arrivals at ring nodes from each tile
   const int* tgt;       // [nq][9] target Q-node per Q-displacement group, -1: bounce-back
   const real* dpsi;     // [nq] sum over i of the pull shift differences of Q-node q
+  const long long* poff;  // [nq*25] element offset of each pull's source plane
   real dvx, dvy;        // r-momentum of all pull shift differences
 };
 
@@ -122,7 +122,6 @@ struct Workspace {
   size_t off_pop[2] = {0, 0};
   size_t off_M = 0, off_U = 0, off_tab = 0, off_part = 0, off_diag = 0;
   size_t off_M2 = 0, off_exp = 0, off_ftab = 0;  // fused path: second M, ring exports, tables
-  size_t off_err = 0;                             // device error flag (bounded waits that gave up)
 };
 
 struct Ctx {
@@ -137,10 +136,6 @@ struct Ctx {
   bool fused = false;     // grid fits the fused single-pass kernel
   int mcur = 0;           // moment buffer (0: off_M, 1: off_M2) of the current state
   double dvx = 0, dvy = 0;  // r-momentum of all pull shift differences (fused path)
-  bool tma = false;         // FP32 fused path with bulk tensor copies
-  CUtensorMap tm_load[2];   // per population buffer: pull boxes (TX + 8) x TY
-  CUtensorMap tm_store9[2];   // per population buffer: the 9 solvent planes of a tile
-  CUtensorMap tm_store25[2];  // per population buffer: the 25 planes of one Q-node of a tile
 };
 
 // Host helpers (tfkt_api.cu).
@@ -178,17 +173,12 @@ size_t fused_smem_bytes(int nq, size_t real_bytes);
 size_t fused_export_elems(int nx, int ny, int nq);
 bool fused_supported(int nx, int ny, int nq, size_t real_bytes);
 void fused_tables(const Lattice& L, const HostTables& t, std::vector<int>& tgt,
-                  std::vector<double>& dpsi, double& dvx, double& dvy);
+                  std::vector<double>& dpsi, double& dvx, double& dvy,
+                  std::vector<long long>& poff);
 template <typename real>
 cudaError_t launch_step_fused(const KernelArgs<real>& a, const FusedArgs<real>& f, cudaStream_t s);
 template <typename real>
 cudaError_t launch_fixup(const KernelArgs<real>& a, const FusedArgs<real>& f, cudaStream_t s);
-// TMA variant of the fused step (FP32 storage).
-size_t tma_smem_bytes(int nq);
-bool tma_supported(int nx, int ny, int nq, int precision);
-cudaError_t launch_step_tma(const KernelArgs<float>& a, const FusedArgs<float>& f,
-                            const CUtensorMap& load_map, const CUtensorMap& store9,
-                            const CUtensorMap& store25, int* err, cudaStream_t s);
 
 constexpr int TX = 32;   // tile width (one warp along x)
 constexpr int TY = 8;    // tile height

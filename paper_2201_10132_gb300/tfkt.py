@@ -21,7 +21,7 @@ FIELDS = ["rho_s", "psi_tot", "ux", "uy", "cxx", "cxy", "cyy", "thxx", "thxy", "
 KERNELS = ["moments", "step", "fused", "fixup"]
 DIAGS = ["mass_s", "mass_p", "px", "py", "ke", "enstrophy", "qrms_mean", "ey2"]
 STATUS = {0: "TFKT_OK", 1: "TFKT_EINVAL", 2: "TFKT_ENOMEM", 3: "TFKT_ECUDA", 4: "TFKT_ENAN",
-          5: "TFKT_ESTATE", 6: "TFKT_ETIMEOUT"}
+          5: "TFKT_ESTATE"}
 
 
 class TfktError(RuntimeError):
