@@ -247,16 +247,50 @@ step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
   real jx_arr = 0, jy_arr = 0, ms_arr = 0;    // own-node arrivals (momentum, solvent mass)
   real jx_r = 0, jy_r = 0, ms_r = 0;          // ring-node arrivals
 
+  // Bounce-back mask of Q-node q: bit g set when q + displacement g leaves the disk.
+  auto bounce_mask = [&](int q) {
+    int tv[GQ];
+    load_vec<GQ>(tv, sm.tgt + q * GQ);
+    uint32_t m = 0;
+#pragma unroll
+    for (int g = 0; g < 9; ++g)
+      if (tv[g] < 0) m |= 1u << g;
+    return m;
+  };
+  // Source offset of the pull of velocity i at Q-node q (bm: that Q-node's mask);
+  // the pull bounces when q - Qdot_i leaves the disk, the opposite group 8 - g.
+  auto pull_offset = [&](auto I, int q, uint32_t bm) {
+    constexpr int i = decltype(I)::value;
+    constexpr V4 cv = c25(i);
+    uint32_t o = off[shift_index(-cv.rx, -cv.ry)];
+    if constexpr (moves_r(i)) {
+      if ((bm >> (8 - qgroup(cv))) & 1u) o = off[4];
+    }
+    return sm.poff[q * 25 + i] + o;
+  };
+  // The populations of a Q-node are loaded one Q-node ahead: register h[i] is
+  // refilled for Q-node q + 1 as soon as the collision of Q-node q has used it,
+  // so the loads are in flight during the exchange and the barriers.
+  real h[25], mn[4];
+  if (nq > 0) {
+    const uint32_t bm0 = bounce_mask(0);
+    static_for<0, 25>([&](auto I) { h[decltype(I)::value] = src[pull_offset(I, 0, bm0)]; });
+    mn[0] = Min[off[5]];
+    mn[1] = Min[off[3]];
+    mn[2] = Min[off[7]];
+    mn[3] = Min[off[1]];
+  }
+
   // ---- solvent
   {
-    real h[9];
+    real hs[9];
     real drs = 0, jsx = 0, jsy = 0;
     static_for<0, 9>([&](auto I) {
       constexpr int i = I;
-      h[i] = src[(size_t)i * P + off[shift_index(-c9x(i), -c9y(i))]];
-      drs += h[i];
-      acc<c9x(i)>(jsx, h[i]);
-      acc<c9y(i)>(jsy, h[i]);
+      hs[i] = src[(size_t)i * P + off[shift_index(-c9x(i), -c9y(i))]];
+      drs += hs[i];
+      acc<c9x(i)>(jsx, hs[i]);
+      acc<c9y(i)>(jsy, hs[i]);
     });
     const real rs = real(1) + drs;
     const real jfx = (a.c2 * jsx + rs * Ux + a.tau2 * force) * a.inv_c2p1;
@@ -276,7 +310,7 @@ step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
       const real feq_dev = real(w9(i)) * (drs + rs * (real(3) * cv +
                                                       real(4.5) * (a.omr * cus * cus + a.r * cu * cu) -
                                                       real(1.5) * sq));
-      const real hp = a.om2b * h[i] + a.tb * feq_dev + a.omb * real(w9(i)) * gx * force;
+      const real hp = a.om2b * hs[i] + a.tb * feq_dev + a.omb * real(w9(i)) * gx * force;
       dst[(size_t)i * P + n] = hp;
       if constexpr (i == 0) ms_arr += hp;
       else sm.hb[(i - 1) * HSZ + hcell] = hp;
@@ -303,32 +337,24 @@ step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
 
   // ---- polymer, one Q-node at a time
   for (int q = 0; q < nq; ++q) {
-    int tg[GQ];
-    load_vec<GQ>(tg, sm.tgt + q * GQ);
-    uint32_t bm = 0;
-#pragma unroll
-    for (int g = 0; g < 9; ++g)
-      if (tg[g] < 0) bm |= 1u << g;
-    real h[25];
+    const uint32_t bm = bounce_mask(q);
     {
       real dl[DQ];
       load_vec<DQ>(dl, sm.delta + q * DQ);
-      const long long* po = sm.poff + q * 25;
-      static_for<0, 25>([&](auto I) {
-        constexpr int i = I;
-        constexpr V4 cv = c25(i);
-        constexpr int g = qgroup(cv);
-        uint32_t o = off[shift_index(-cv.rx, -cv.ry)];
-        if constexpr (moves_r(i)) {
-          // the pull bounces when q - Qdot leaves the disk: the opposite group 8 - g
-          if ((bm >> (8 - g)) & 1u) o = off[4];
-        }
-        h[i] = src[po[i] + o] + dl[i];
-      });
+#pragma unroll
+      for (int i = 0; i < 25; ++i) h[i] += dl[i];
     }
-    const real* Mq = Min + (size_t)q * P;
-    const real dpx = real(0.5) * (Mq[off[5]] - Mq[off[3]]);
-    const real dpy = real(0.5) * (Mq[off[7]] - Mq[off[1]]);
+    const real dpx = real(0.5) * (mn[0] - mn[1]);
+    const real dpy = real(0.5) * (mn[2] - mn[3]);
+    const bool more = q + 1 < nq;
+    const uint32_t bmn = more ? bounce_mask(q + 1) : 0u;
+    if (more) {
+      const real* Mq = Min + (size_t)(q + 1) * P;
+      mn[0] = Mq[off[5]];
+      mn[1] = Mq[off[3]];
+      mn[2] = Mq[off[7]];
+      mn[3] = Mq[off[1]];
+    }
     real dpsi = 0, rx = 0, ry = 0, qx = 0, qy = 0;
     static_for<0, 25>([&](auto I) {
       constexpr int i = I;
@@ -380,6 +406,7 @@ step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
         acc<-c25(i).rx>(jx_arr, back);
         acc<-c25(i).ry>(jy_arr, back);
       }
+      if (more) h[i] = src[pull_offset(I, q + 1, bmn)];
     });
     __syncthreads();
     // arrivals from the other r-nodes of the tile
@@ -393,7 +420,7 @@ step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
     });
 #pragma unroll
     for (int g = 0; g < 9; ++g) {
-      const int t = g == 4 ? q : tg[g];
+      const int t = g == 4 ? q : sm.tgt[q * GQ + g];
       if (t >= 0) sm.A[t * NT + tid] += grp[g];
     }
     if (ring_thread) {
@@ -410,7 +437,7 @@ step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
       });
 #pragma unroll
       for (int g = 0; g < 9; ++g) {
-        const int t = g == 4 ? q : tg[g];
+        const int t = g == 4 ? q : sm.tgt[q * GQ + g];
         if (t >= 0) sm.Ar[t * RING + tid] += gr[g];
       }
     }
@@ -473,8 +500,9 @@ __global__ void __launch_bounds__(128) fixup_kernel(KernelArgs<real> a, FusedArg
   const int nq = a.nq;
   const size_t P = a.plane;
   const size_t n = (size_t)(ty * TY + ly) * a.pitch + (tx * TX + lx);
-  // contributing neighbour tiles and the ring position of this node in each
-  int ctile[8], cpos[8], nc = 0;
+  // contributing neighbour tiles (at most 3: two edges and a corner) and the
+  // ring position of this node in each
+  int ctile[3] = {0, 0, 0}, cpos[3] = {0, 0, 0}, nc = 0;
   auto tile_of = [&](int dx, int dy) {
     const int ax = (tx + dx + ntx) % ntx, ay = (ty + dy + nty) % nty;
     return ay * ntx + ax;
@@ -488,8 +516,14 @@ __global__ void __launch_bounds__(128) fixup_kernel(KernelArgs<real> a, FusedArg
   if (lx == 0 && ly == TY - 1) { ctile[nc] = tile_of(-1, 1); cpos[nc++] = ring_pos(TX, -1); }
   if (lx == TX - 1 && ly == TY - 1) { ctile[nc] = tile_of(1, 1); cpos[nc++] = ring_pos(-1, -1); }
   const real* ex = fa.exports;
+  size_t eoff[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) eoff[c] = (size_t)ctile[c] * RING + cpos[c];
+  const size_t estride = ntiles * RING;
   auto gather = [&](int j, real v) {
-    for (int c = 0; c < nc; ++c) v += ex[((size_t)j * ntiles + ctile[c]) * RING + cpos[c]];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      if (c < nc) v += ex[(size_t)j * estride + eoff[c]];
     return v;
   };
   real* M = fa.Mout;
@@ -497,14 +531,26 @@ __global__ void __launch_bounds__(128) fixup_kernel(KernelArgs<real> a, FusedArg
   const real jx = gather(nq + 1, M[(size_t)(nq + M_JX) * P + n]) + fa.dvx;
   const real jy = gather(nq + 2, M[(size_t)(nq + M_JY) * P + n]) + fa.dvy;
   real txx = 0, txy = 0, tyy = 0;
-  for (int p = 0; p < nq; ++p) {
-    const real d = gather(p, M[(size_t)p * P + n]) + fa.dpsi[p];
-    M[(size_t)p * P + n] = d;
-    drho += d;
-    const real Qx = a.tab.qx[p], Qy = a.tab.qy[p];
-    txx += d * Qx * Qx;
-    txy += d * Qx * Qy;
-    tyy += d * Qy * Qy;
+  // four Q-nodes at a time: all their loads are issued before any store
+  for (int p0 = 0; p0 < nq; p0 += 4) {
+    real d[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) d[u] = p0 + u < nq ? M[(size_t)(p0 + u) * P + n] : real(0);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (p0 + u < nq) d[u] = gather(p0 + u, d[u]) + fa.dpsi[p0 + u];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int p = p0 + u;
+      if (p < nq) {
+        M[(size_t)p * P + n] = d[u];
+        drho += d[u];
+        const real Qx = a.tab.qx[p], Qy = a.tab.qy[p];
+        txx += d[u] * Qx * Qx;
+        txy += d[u] * Qx * Qy;
+        tyy += d[u] * Qy * Qy;
+      }
+    }
   }
   M[(size_t)(nq + M_DRHO) * P + n] = drho;
   M[(size_t)(nq + M_JX) * P + n] = jx;
