@@ -26,6 +26,25 @@ sys.path.insert(0, ROOT)
 L2_BYTES = 129e6
 
 
+def _measured_traffic(nodes: int):
+    """DRAM bytes of one fused-kernel launch, scaled by r-nodes from the committed ncu
+    summary of the small case; None once the kernel source no longer matches it."""
+    import hashlib
+    import re
+    try:
+        text = open(os.path.join(ROOT, "profiles",
+                                 "step_fused_kernel_kolmogorov_512x512_nq32.md")).read()
+        src = open(os.path.join(ROOT, "paper_2201_10132_gb300", "csrc", "tfkt_fused.cu"),
+                   "rb").read()
+    except OSError:
+        return None
+    h = re.search(r"sha256 prefix `([0-9a-f]+)`", text)
+    b = re.search(r"per r-node: .*?\*\*(\d+) B\*\*", text, re.S)
+    if not h or not b or hashlib.sha256(src).hexdigest()[:len(h.group(1))] != h.group(1):
+        return None
+    return float(b.group(1)) * nodes
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -89,6 +108,26 @@ class ClockSampler:
         sm.sort()
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(smax), "samples": len(sm),
                 "power_w_max": max(power), "reasons": sorted(reasons)}
+
+
+def max_over_ranks(x: float, dist=None, device: str = "cuda") -> float:
+    """The largest value of x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_seed(base_seed: int, rank: int) -> int:
+    """Each rank advances its own independent run (weak scaling): its own seed."""
+    return base_seed + rank
+
+
+def aggregate_glups(world: int, nodes: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput: r-node updates of all ranks over the slowest rank's time."""
+    return world * nodes * steps / seconds / 1e9
 
 
 def oracle_sample(W, target_s: float = 12.0):
@@ -178,7 +217,8 @@ def main():
     p = tfkt.Params.from_workload(W, tfkt.FP32)
     nodes = W.nx * W.ny
     ws = torch.empty(tfkt.required_bytes(p), dtype=torch.uint8, device="cuda")
-    pert = torch.from_numpy(perturbation(W.nx, W.ny, W.seed + rank, W.amp, W.u0)).pin_memory()
+    pert = torch.from_numpy(perturbation(W.nx, W.ny, replica_seed(W.seed, rank), W.amp,
+                                         W.u0)).pin_memory()
     stream = torch.cuda.Stream()
     solver = tfkt.Solver(p, pert.numpy(), workspace=ws, stream=stream.cuda_stream)
     info = solver.info
@@ -199,11 +239,7 @@ def main():
     e1.synchronize()
     barrier()
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dist)
     diag = solver.diagnostics()
     assert all(math.isfinite(v) for v in diag.values()), diag
     solver.close()
@@ -224,12 +260,8 @@ def main():
             s2.diagnostics_into(out_diag.numpy())
         s2.moments_into(tfkt.field_mask(names), host_f.numpy())
         s2.close()
-        t_e2e = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = float(t.item())
-        e2e = {"value": world * nodes * args.steps / t_e2e / 1e9, "unit": "GLUPS",
+        t_e2e = max_over_ranks(time.perf_counter() - t0, dist)
+        e2e = {"value": aggregate_glups(world, nodes, args.steps, t_e2e), "unit": "GLUPS",
                "h2d_bytes_per_step": pert.numel() * 8 / args.steps,
                "d2h_bytes_per_step": (args.steps * out_diag.numel() * 8 + host_f.numel() * 8)
                / args.steps}
@@ -251,7 +283,7 @@ def main():
                              "bytes_per_launch": b,
                              "achieved_gbs": None if b is None else b / (ms_l / 1e3) / 1e9}
         top = max(per, key=lambda k: per[k]["ms_per_launch"] * per[k]["launches"])
-        value = world * nodes * args.steps / (ms / 1e3) / 1e9
+        value = aggregate_glups(world, nodes, args.steps, ms / 1e3)
         ach = per[top]["achieved_gbs"]
         line = {
             "metric": "GLUPS (1e9 r-node updates/s), 4096^2 two-fluid step",
@@ -265,7 +297,8 @@ def main():
                        "parallelism": f"{world} independent runs"},
             "roofline": {"bound": "hbm", "kernel": top + "_kernel", "achieved": ach,
                          "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
-                         "peak_kind": peak_kind, "traffic": None,
+                         "peak_kind": peak_kind,
+                         "traffic": _measured_traffic(nodes) if top == "fused" else None,
                          "bytes_per_launch": per[top]["bytes_per_launch"],
                          "step_model_gbs": nodes * (2 * npl + 2 * nm) * s / (ms / args.steps / 1e3) / 1e9,
                          "kernels": per},
