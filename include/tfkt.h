@@ -48,7 +48,9 @@ typedef enum {
 
 typedef enum {
   TFKT_FP64 = 0,    /* populations stored and updated in double */
-  TFKT_FP32 = 1     /* populations stored as float deviations from rest, updated in float */
+  TFKT_FP32 = 1,    /* populations stored as float deviations from rest, updated in float */
+  TFKT_FP16 = 2     /* populations stored as half deviations from rest (rounded to nearest),
+                       updated in float; moment planes in float */
 } tfkt_precision;
 
 /* Physical description of one Kolmogorov run (Sec. VII definitions:
@@ -172,7 +174,8 @@ tfkt_status tfkt_populations(tfkt_ctx* ctx, double* host_dst, size_t bytes);
            n steps, at W + (n mod 2) * B with B = the population bytes
            (9 + 25 nq) * ny * pitch * element size rounded up to 256
            (nq, pitch from tfkt_get_info; element size 8 for TFKT_FP64,
-           4 for TFKT_FP32).
+           4 for TFKT_FP32, 2 for TFKT_FP16), but never less than
+           TFKT_NFIELDS * ny * nx * 8 bytes.
    dst:    device pointer, popcount(field_mask) * ny * nx doubles; bytes is
            its size.
    stream: cudaStream_t or NULL. The lattice tables are copied from host

@@ -26,10 +26,10 @@ tfkt_status cuda_fail(Ctx* c, cudaError_t e, const char* where) {
   return fail(TFKT_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
-#define TFKT_CUDA(ctx, call)                                     \
-  do {                                                           \
-    cudaError_t e_ = (call);                                     \
-    if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);   \
+#define TFKT_CUDA(ctx, ...)                                             \
+  do {                                                                  \
+    cudaError_t e_ = (__VA_ARGS__);                                     \
+    if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #__VA_ARGS__);   \
   } while (0)
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -52,7 +52,7 @@ tfkt_status map_params(const tfkt_params* p, Lattice* L) {
   if (p->k_periods < 1) return fail(TFKT_EINVAL, "k_periods must be >= 1");
   if (!(p->wi >= 0)) return fail(TFKT_EINVAL, "wi must be >= 0");
   if (p->wi == 0 && p->beta < 1) return fail(TFKT_EINVAL, "wi = 0 needs beta = 1 (no polymer)");
-  if (p->precision != TFKT_FP64 && p->precision != TFKT_FP32)
+  if (p->precision != TFKT_FP64 && p->precision != TFKT_FP32 && p->precision != TFKT_FP16)
     return fail(TFKT_EINVAL, "unknown precision");
   if (p->ic_mode != 0 && p->ic_mode != 1) return fail(TFKT_EINVAL, "ic_mode must be 0 or 1");
   Lattice l;
@@ -106,6 +106,16 @@ tfkt_status map_params(const tfkt_params* p, Lattice* L) {
 }
 
 size_t real_size(const Lattice& L) { return L.precision == TFKT_FP64 ? 8 : 4; }
+double polymer_scale(const Lattice& L) {
+  if (L.precision != TFKT_FP16 || !(L.psi_tot > 0)) return 1.0;
+  // typical stored value w_i psi0(q) ~ psi_tot / (36 nq): scale it to about one
+  const double target = 36.0 * L.nq / L.psi_tot;
+  return std::ldexp(1.0, (int)std::lround(std::log2(target)));
+}
+
+size_t store_size(const Lattice& L) {
+  return L.precision == TFKT_FP64 ? 8 : (L.precision == TFKT_FP16 ? 2 : 4);
+}
 
 int diag_blocks_for(const Lattice& L) {
   const size_t N = (size_t)L.nx * L.ny;
@@ -117,7 +127,10 @@ int diag_blocks_for(const Lattice& L) {
 size_t layout(const Lattice& L, Workspace* w) {
   const size_t sz = real_size(L), A = 256;
   size_t o = 0;
-  const size_t pop = (size_t)L.npl * L.plane * sz;
+  // a population buffer also stages field output (doubles) and the initial perturbation
+  const size_t N = (size_t)L.nx * L.ny;
+  size_t pop = (size_t)L.npl * L.plane * store_size(L);
+  if (pop < (size_t)TFKT_NFIELDS * N * sizeof(double)) pop = (size_t)TFKT_NFIELDS * N * sizeof(double);
   w->off_pop[0] = o;
   o = align_up(o + pop, A);
   w->off_pop[1] = o;
@@ -209,8 +222,8 @@ KernelArgs<real> make_args(const Ctx* c, const HostTables* ht = nullptr) {
   const Lattice& L = c->L;
   char* base = (char*)c->ws.base;
   KernelArgs<real> a{};
-  a.src = (const real*)(base + c->ws.off_pop[c->cur]);
-  a.dst = (real*)(base + c->ws.off_pop[c->cur ^ 1]);
+  a.src = base + c->ws.off_pop[c->cur];
+  a.dst = base + c->ws.off_pop[c->cur ^ 1];
   a.M = (real*)(base + (c->mcur ? c->ws.off_M2 : c->ws.off_M));
   a.U = (real*)(base + c->ws.off_U);
   a.perturb = nullptr;
@@ -234,6 +247,8 @@ KernelArgs<real> make_args(const Ctx* c, const HostTables* ht = nullptr) {
   a.psi_tot0 = (real)L.psi_tot;
   a.l2 = (real)(L.ell * L.ell);
   a.H = (real)L.H;
+  a.pscale = (real)polymer_scale(L);
+  a.pinv = (real)(1.0 / polymer_scale(L));
   // tables
   char* tb = base + c->ws.off_tab;
   size_t o = 0;
@@ -306,7 +321,7 @@ tfkt_status upload_tables(Ctx* c, const HostTables& t) {
   return TFKT_OK;
 }
 
-template <typename real>
+template <typename real, typename S>
 tfkt_status init_state(Ctx* c, const double* perturb) {
   const Lattice& L = c->L;
   KernelArgs<real> a = make_args<real>(c);
@@ -318,21 +333,21 @@ tfkt_status init_state(Ctx* c, const double* perturb) {
                                  cudaMemcpyHostToDevice, c->stream));
   }
   a.perturb = dpert;
-  a.dst = (real*)((char*)c->ws.base + c->ws.off_pop[0]);
-  TFKT_CUDA(c, launch_init<real>(a, c->stream));
+  a.dst = (char*)c->ws.base + c->ws.off_pop[0];
+  TFKT_CUDA(c, launch_init<real, S>(a, c->stream));
   c->cur = 0;
   KernelArgs<real> m = make_args<real>(c);
-  TFKT_CUDA(c, launch_moments<real>(m, c->stream));
+  TFKT_CUDA(c, launch_moments<real, S>(m, c->stream));
   c->m_valid = true;
   TFKT_CUDA(c, cudaStreamSynchronize(c->stream));
   return TFKT_OK;
 }
 
-template <typename real>
+template <typename real, typename S>
 tfkt_status ensure_moments(Ctx* c) {
   if (c->m_valid) return TFKT_OK;
   KernelArgs<real> a = make_args<real>(c);
-  TFKT_CUDA(c, launch_moments<real>(a, c->stream));
+  TFKT_CUDA(c, launch_moments<real, S>(a, c->stream));
   c->m_valid = true;
   return TFKT_OK;
 }
@@ -340,19 +355,19 @@ tfkt_status ensure_moments(Ctx* c) {
 // One step. Fused path: the step kernel also produces the next state's
 // moment planes (completed at tile borders by the fix-up kernel), so the
 // moments stay valid. Two-pass path: moments kernel, then the step kernel.
-template <typename real>
+template <typename real, typename S>
 tfkt_status do_step(Ctx* c, int64_t n) {
   for (int64_t k = 0; k < n; ++k) {
-    tfkt_status s = ensure_moments<real>(c);
+    tfkt_status s = ensure_moments<real, S>(c);
     if (s != TFKT_OK) return s;
     KernelArgs<real> a = make_args<real>(c);
     if (c->fused) {
       FusedArgs<real> f = make_fused<real>(c);
-      TFKT_CUDA(c, launch_step_fused<real>(a, f, c->stream));
+      TFKT_CUDA(c, launch_step_fused<real, S>(a, f, c->stream));
       TFKT_CUDA(c, launch_fixup<real>(a, f, c->stream));
       c->mcur ^= 1;
     } else {
-      TFKT_CUDA(c, launch_step<real>(a, c->stream));
+      TFKT_CUDA(c, launch_step<real, S>(a, c->stream));
       c->m_valid = false;
     }
     c->cur ^= 1;
@@ -362,7 +377,7 @@ tfkt_status do_step(Ctx* c, int64_t n) {
 }
 
 // tfkt_step with an event pair around each launch (profiling only).
-template <typename real>
+template <typename real, typename S>
 tfkt_status do_step_profiled(Ctx* c, int64_t n, double* ms, int64_t* launches) {
   cudaEvent_t ev[2 * TFKT_NKERNELS];
   for (auto& e : ev) TFKT_CUDA(c, cudaEventCreate(&e));
@@ -388,7 +403,7 @@ tfkt_status do_step_profiled(Ctx* c, int64_t n, double* ms, int64_t* launches) {
   for (int64_t k = 0; k < n; ++k) {
     if (!c->m_valid) {
       KernelArgs<real> a = make_args<real>(c);
-      tfkt_status s = timed(TFKT_K_MOMENTS, [&] { return launch_moments<real>(a, c->stream); });
+      tfkt_status s = timed(TFKT_K_MOMENTS, [&] { return launch_moments<real, S>(a, c->stream); });
       if (s != TFKT_OK) return s;
       c->m_valid = true;
     }
@@ -396,13 +411,13 @@ tfkt_status do_step_profiled(Ctx* c, int64_t n, double* ms, int64_t* launches) {
     if (c->fused) {
       FusedArgs<real> f = make_fused<real>(c);
       tfkt_status s =
-          timed(TFKT_K_FUSED, [&] { return launch_step_fused<real>(a, f, c->stream); });
+          timed(TFKT_K_FUSED, [&] { return launch_step_fused<real, S>(a, f, c->stream); });
       if (s != TFKT_OK) return s;
       s = timed(TFKT_K_FIXUP, [&] { return launch_fixup<real>(a, f, c->stream); });
       if (s != TFKT_OK) return s;
       c->mcur ^= 1;
     } else {
-      tfkt_status s = timed(TFKT_K_STEP, [&] { return launch_step<real>(a, c->stream); });
+      tfkt_status s = timed(TFKT_K_STEP, [&] { return launch_step<real, S>(a, c->stream); });
       if (s != TFKT_OK) return s;
       c->m_valid = false;
     }
@@ -416,10 +431,10 @@ tfkt_status do_step_profiled(Ctx* c, int64_t n, double* ms, int64_t* launches) {
   return TFKT_OK;
 }
 
-template <typename real>
+template <typename real, typename S>
 tfkt_status do_fields(Ctx* c, uint32_t mask, double* dst, int dst_is_device) {
   const Lattice& L = c->L;
-  tfkt_status s = ensure_moments<real>(c);
+  tfkt_status s = ensure_moments<real, S>(c);
   if (s != TFKT_OK) return s;
   KernelArgs<real> a = make_args<real>(c);
   TFKT_CUDA(c, launch_velocity<real>(a, c->stream));
@@ -435,10 +450,10 @@ tfkt_status do_fields(Ctx* c, uint32_t mask, double* dst, int dst_is_device) {
   return TFKT_OK;
 }
 
-template <typename real>
+template <typename real, typename S>
 tfkt_status do_psi(Ctx* c, double* dst, int dst_is_device) {
   const Lattice& L = c->L;
-  tfkt_status s = ensure_moments<real>(c);
+  tfkt_status s = ensure_moments<real, S>(c);
   if (s != TFKT_OK) return s;
   KernelArgs<real> a = make_args<real>(c);
   const size_t bytes = (size_t)L.nq * L.nx * L.ny * sizeof(double);
@@ -451,14 +466,14 @@ tfkt_status do_psi(Ctx* c, double* dst, int dst_is_device) {
   return TFKT_OK;
 }
 
-template <typename real>
+template <typename real, typename S>
 tfkt_status do_populations(Ctx* c, double* host) {
   const Lattice& L = c->L;
   KernelArgs<real> a = make_args<real>(c);
   const size_t N = (size_t)L.nx * L.ny;
   double* tmp = nullptr;
   TFKT_CUDA(c, cudaMallocAsync((void**)&tmp, (size_t)L.npl * N * sizeof(double), c->stream));
-  cudaError_t e = launch_populations<real>(a, tmp, c->stream);
+  cudaError_t e = launch_populations<real, S>(a, tmp, c->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(host, tmp, (size_t)L.npl * N * sizeof(double), cudaMemcpyDeviceToHost,
                         c->stream);
@@ -469,9 +484,9 @@ tfkt_status do_populations(Ctx* c, double* host) {
   return TFKT_OK;
 }
 
-template <typename real>
+template <typename real, typename S>
 tfkt_status do_diag(Ctx* c, double* out) {
-  tfkt_status s = ensure_moments<real>(c);
+  tfkt_status s = ensure_moments<real, S>(c);
   if (s != TFKT_OK) return s;
   KernelArgs<real> a = make_args<real>(c);
   TFKT_CUDA(c, launch_velocity<real>(a, c->stream));
@@ -486,8 +501,12 @@ tfkt_status do_diag(Ctx* c, double* out) {
   return TFKT_OK;
 }
 
-#define DISPATCH(c, fn, ...) \
-  ((c)->L.precision == TFKT_FP64 ? fn<double>(__VA_ARGS__) : fn<float>(__VA_ARGS__))
+// Compute and storage types of a context: FP64 (double, double), FP32
+// (float, float), FP16 storage computed in FP32 (float, __half).
+#define DISPATCH(c, fn, ...)                                       \
+  ((c)->L.precision == TFKT_FP64   ? fn<double, double>(__VA_ARGS__) \
+   : (c)->L.precision == TFKT_FP32 ? fn<float, float>(__VA_ARGS__)   \
+                                   : fn<float, __half>(__VA_ARGS__))
 
 tfkt_status check_ctx(const Ctx* c) {
   if (!c) return fail(TFKT_EINVAL, "context is NULL");
@@ -635,7 +654,7 @@ tfkt_status tfkt_get_info(const tfkt_ctx* c, tfkt_info* info) {
   i.workspace_bytes = c->ws.bytes;
   i.pitch = L.pitch;
   // each population read once and written once, each moment plane read and written once
-  i.bytes_per_node_step = (size_t)L.npl * 2 * real_size(L) + (size_t)L.nm * 2 * real_size(L);
+  i.bytes_per_node_step = (size_t)L.npl * 2 * store_size(L) + (size_t)L.nm * 2 * real_size(L);
   *info = i;
   return TFKT_OK;
 }

@@ -177,7 +177,7 @@ __device__ __forceinline__ void velocity_at(const KernelArgs<real>& a, const rea
   uy = (jy + real(0.5) * ey) / rho;
 }
 
-template <typename real>
+template <typename real, typename S>
 __global__ void __launch_bounds__(NT, 2)
 step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -189,8 +189,8 @@ step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
   const size_t P = a.plane;
   const real* __restrict__ Min = fa.Min;
   real* __restrict__ Mout = fa.Mout;
-  const real* __restrict__ src = a.src;
-  real* __restrict__ dst = a.dst;
+  const S* __restrict__ src = (const S*)a.src;
+  S* __restrict__ dst = (S*)a.dst;
 
   // pull offsets within a plane (32-bit: a plane holds < 2^31 elements)
   const int xm = x == 0 ? a.nx - 1 : x - 1, xp = x == a.nx - 1 ? 0 : x + 1;
@@ -274,7 +274,9 @@ step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
   real h[25], mn[4];
   if (nq > 0) {
     const uint32_t bm0 = bounce_mask(0);
-    static_for<0, 25>([&](auto I) { h[decltype(I)::value] = src[pull_offset(I, 0, bm0)]; });
+    static_for<0, 25>([&](auto I) {
+      h[decltype(I)::value] = from_store<real>(src[pull_offset(I, 0, bm0)]);
+    });
     mn[0] = Min[off[5]];
     mn[1] = Min[off[3]];
     mn[2] = Min[off[7]];
@@ -287,7 +289,7 @@ step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
     real drs = 0, jsx = 0, jsy = 0;
     static_for<0, 9>([&](auto I) {
       constexpr int i = I;
-      hs[i] = src[(size_t)i * P + off[shift_index(-c9x(i), -c9y(i))]];
+      hs[i] = from_store<real>(src[(size_t)i * P + off[shift_index(-c9x(i), -c9y(i))]]);
       drs += hs[i];
       acc<c9x(i)>(jsx, hs[i]);
       acc<c9y(i)>(jsy, hs[i]);
@@ -311,7 +313,7 @@ step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
                                                       real(4.5) * (a.omr * cus * cus + a.r * cu * cu) -
                                                       real(1.5) * sq));
       const real hp = a.om2b * hs[i] + a.tb * feq_dev + a.omb * real(w9(i)) * gx * force;
-      dst[(size_t)i * P + n] = hp;
+      dst[(size_t)i * P + n] = to_store<S>(hp);
       if constexpr (i == 0) ms_arr += hp;
       else sm.hb[(i - 1) * HSZ + hcell] = hp;
     });
@@ -342,7 +344,7 @@ step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
       real dl[DQ];
       load_vec<DQ>(dl, sm.delta + q * DQ);
 #pragma unroll
-      for (int i = 0; i < 25; ++i) h[i] += dl[i];
+      for (int i = 0; i < 25; ++i) h[i] = h[i] * a.pinv + dl[i];   // unscale, shift to this Q-node
     }
     const real dpx = real(0.5) * (mn[0] - mn[1]);
     const real dpy = real(0.5) * (mn[2] - mn[3]);
@@ -376,7 +378,7 @@ step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
     const real mry = real(3) * (a.omr * (a.c2 * ry + jrey) * a.inv_c2p1 + a.r * jrey);
     const real mqx = real(3) * (a.omr * (a.c2 * qx + jqex) * a.inv_c2p1 + a.r * jqex);
     const real mqy = real(3) * (a.omr * (a.c2 * qy + jqey) * a.inv_c2p1 + a.r * jqey);
-    real* dq = dst + (size_t)(9 + 25 * q) * P + n;
+    S* dq = dst + (size_t)(9 + 25 * q) * P + n;
     real grp[9];
 #pragma unroll
     for (int g = 0; g < 9; ++g) grp[g] = real(0);
@@ -388,7 +390,7 @@ step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
       acc<c25(i).qx>(d, mqx);
       acc<c25(i).qy>(d, mqy);
       const real hp = a.om2b * h[i] + a.tb * real(w25(i)) * d;
-      dq[(size_t)i * P] = hp;
+      dq[(size_t)i * P] = to_store<S>(hp * a.pscale);
       constexpr int g = qgroup(c25(i));
       const bool b = (bm >> g) & 1u;
       if constexpr (!moves_r(i)) {
@@ -406,7 +408,7 @@ step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
         acc<-c25(i).rx>(jx_arr, back);
         acc<-c25(i).ry>(jy_arr, back);
       }
-      if (more) h[i] = src[pull_offset(I, q + 1, bmn)];
+      if (more) h[i] = from_store<real>(src[pull_offset(I, q + 1, bmn)]);
     });
     __syncthreads();
     // arrivals from the other r-nodes of the tile
@@ -576,13 +578,13 @@ bool fused_supported(int nx, int ny, int nq, size_t real_bytes) {
   return nx % TX == 0 && ny % TY == 0 && fused_smem_bytes(nq, real_bytes) <= 227 * 1024;
 }
 
-template <typename real>
+template <typename real, typename S>
 cudaError_t launch_step_fused(const KernelArgs<real>& a, const FusedArgs<real>& f, cudaStream_t s) {
   const size_t smem = fused_smem_bytes(a.nq, sizeof(real));
-  cudaError_t e = cudaFuncSetAttribute(step_fused_kernel<real>,
+  cudaError_t e = cudaFuncSetAttribute(step_fused_kernel<real, S>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  step_fused_kernel<real><<<dim3(a.nx / TX, a.ny / TY), dim3(TX, TY), smem, s>>>(a, f);
+  step_fused_kernel<real, S><<<dim3(a.nx / TX, a.ny / TY), dim3(TX, TY), smem, s>>>(a, f);
   return cudaGetLastError();
 }
 
@@ -629,12 +631,15 @@ void fused_tables(const Lattice& L, const HostTables& t, std::vector<int>& tgt,
     }
 }
 
-#define TFKT_INSTANTIATE_FUSED(real)                                                           \
-  template cudaError_t launch_step_fused<real>(const KernelArgs<real>&, const FusedArgs<real>&, \
-                                               cudaStream_t);                                  \
-  template cudaError_t launch_fixup<real>(const KernelArgs<real>&, const FusedArgs<real>&,     \
+template cudaError_t launch_step_fused<double, double>(const KernelArgs<double>&,
+                                                        const FusedArgs<double>&, cudaStream_t);
+template cudaError_t launch_step_fused<float, float>(const KernelArgs<float>&,
+                                                      const FusedArgs<float>&, cudaStream_t);
+template cudaError_t launch_step_fused<float, __half>(const KernelArgs<float>&,
+                                                       const FusedArgs<float>&, cudaStream_t);
+template cudaError_t launch_fixup<double>(const KernelArgs<double>&, const FusedArgs<double>&,
                                           cudaStream_t);
-TFKT_INSTANTIATE_FUSED(float)
-TFKT_INSTANTIATE_FUSED(double)
+template cudaError_t launch_fixup<float>(const KernelArgs<float>&, const FusedArgs<float>&,
+                                         cudaStream_t);
 
 }  // namespace tfkt

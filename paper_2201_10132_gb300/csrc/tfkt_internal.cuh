@@ -2,6 +2,7 @@
 // arguments and launchers. Not part of the C-ABI (include/tfkt.h is).
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -83,10 +84,25 @@ struct Tables {
   const real* urow;      // [ny] initial base flow U_x(y)
 };
 
+// Conversions between the storage type S of the populations and the compute
+// type real (FP16 storage is computed in FP32; round to nearest on store).
+template <typename real, typename S>
+__host__ __device__ __forceinline__ real from_store(S v) { return (real)v; }
+template <>
+__host__ __device__ __forceinline__ float from_store<float, __half>(__half v) { return __half2float(v); }
+template <>
+__host__ __device__ __forceinline__ double from_store<double, __half>(__half v) {
+  return (double)__half2float(v);
+}
+template <typename S, typename real>
+__host__ __device__ __forceinline__ S to_store(real v) { return (S)v; }
+template <>
+__host__ __device__ __forceinline__ __half to_store<__half, float>(float v) { return __float2half_rn(v); }
+
 template <typename real>
 struct KernelArgs {
-  const real* __restrict__ src;  // populations read (pull)
-  real* __restrict__ dst;        // populations written
+  const void* src;               // populations read (pull), storage type of the context
+  void* dst;                     // populations written
   real* M;                       // moment planes
   real* U;                       // scratch: 2 planes (U_x, U_y)
   const double* perturb;         // [2][ny][nx] (init only)
@@ -100,6 +116,7 @@ struct KernelArgs {
   real theta0[3];                // (H ell^2 / 2) sum_q psi0 Q Q
   real psi_tot0;
   real l2, H;
+  real pscale, pinv;             // polymer storage scale (a power of two) and its inverse
   Tables<real> tab;
 };
 
@@ -142,7 +159,12 @@ struct Ctx {
 tfkt_status fail(tfkt_status s, const std::string& msg);
 size_t align_up(size_t v, size_t a);
 tfkt_status map_params(const tfkt_params* p, Lattice* L);
-size_t real_size(const Lattice& L);
+size_t real_size(const Lattice& L);   // bytes of the compute type (moment planes, tables)
+size_t store_size(const Lattice& L);  // bytes of the population storage type
+// Polymer populations are stored as (deviation x scale): a power of two that
+// brings them to order one in FP16 storage (exact, so FP16 keeps its full 11
+// bits instead of falling into the subnormal range); 1 for FP32 and FP64.
+double polymer_scale(const Lattice& L);
 struct HostTables {
   std::vector<double> qx, qy, psi0, delta, arow, urow;
   std::vector<int> pull;
@@ -150,11 +172,11 @@ struct HostTables {
 HostTables build_tables(const Lattice& L);
 
 // Launchers (tfkt_kernels.cu). Each returns the launch status.
-template <typename real>
+template <typename real, typename S>
 cudaError_t launch_init(const KernelArgs<real>& a, cudaStream_t s);
-template <typename real>
+template <typename real, typename S>
 cudaError_t launch_moments(const KernelArgs<real>& a, cudaStream_t s);
-template <typename real>
+template <typename real, typename S>
 cudaError_t launch_step(const KernelArgs<real>& a, cudaStream_t s);
 template <typename real>
 cudaError_t launch_velocity(const KernelArgs<real>& a, cudaStream_t s);
@@ -162,7 +184,7 @@ template <typename real>
 cudaError_t launch_fields(const KernelArgs<real>& a, uint32_t mask, double* out, cudaStream_t s);
 template <typename real>
 cudaError_t launch_psi(const KernelArgs<real>& a, double* out, cudaStream_t s);
-template <typename real>
+template <typename real, typename S>
 cudaError_t launch_populations(const KernelArgs<real>& a, double* out, cudaStream_t s);
 template <typename real>
 cudaError_t launch_diag(const KernelArgs<real>& a, double* partials, int nblocks, double* out,
@@ -175,7 +197,7 @@ bool fused_supported(int nx, int ny, int nq, size_t real_bytes);
 void fused_tables(const Lattice& L, const HostTables& t, std::vector<int>& tgt,
                   std::vector<double>& dpsi, double& dvx, double& dvy,
                   std::vector<long long>& poff);
-template <typename real>
+template <typename real, typename S>
 cudaError_t launch_step_fused(const KernelArgs<real>& a, const FusedArgs<real>& f, cudaStream_t s);
 template <typename real>
 cudaError_t launch_fixup(const KernelArgs<real>& a, const FusedArgs<real>& f, cudaStream_t s);

@@ -71,8 +71,9 @@ __device__ __forceinline__ void mixture_velocity(const KernelArgs<real>& a, int 
 // U = base flow + perturbation, J^r_eq = psi U, J^Q_eq = psi (Q . grad U -
 // kappa Q) (grad_r psi = 0). Each value is written to the slot that the
 // first pull reads for it, so the first step starts from exactly this state.
-template <typename real>
+template <typename real, typename S>
 __global__ void __launch_bounds__(256) init_kernel(KernelArgs<real> a) {
+  S* __restrict__ dst = (S*)a.dst;
   const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
   if (x >= a.nx || y >= a.ny) return;
   const int nx = a.nx, ny = a.ny;
@@ -98,7 +99,7 @@ __global__ void __launch_bounds__(256) init_kernel(KernelArgs<real> a) {
   for (int i = 0; i < 9; ++i) {
     const real cu = real(c9x(i)) * ux + real(c9y(i)) * uy;
     const real h = real(w9(i)) * (real(3) * cu + real(4.5) * cu * cu - real(1.5) * usq);
-    a.dst[(size_t)i * P + off.o[shift_index(-c9x(i), -c9y(i))]] = h;
+    dst[(size_t)i * P + off.o[shift_index(-c9x(i), -c9y(i))]] = to_store<S>(h);
   }
   for (int q = 0; q < a.nq; ++q) {
     const real Qx = a.tab.qx[q], Qy = a.tab.qy[q], psi = a.tab.psi0[q];
@@ -113,7 +114,7 @@ __global__ void __launch_bounds__(256) init_kernel(KernelArgs<real> a) {
       const int e = a.tab.pull[q * 25 + i];
       const size_t o = e >= 0 ? off.o[shift_index(-c.rx, -c.ry)] : off.o[4];
       const int p = e >= 0 ? e : ~e;
-      a.dst[(size_t)p * P + o] = h - a.tab.delta[q * 25 + i];
+      dst[(size_t)p * P + o] = to_store<S>((h - a.tab.delta[q * 25 + i]) * a.pscale);
     }
   }
 }
@@ -121,18 +122,18 @@ __global__ void __launch_bounds__(256) init_kernel(KernelArgs<real> a) {
 // --------------------------------------------------------------- moments
 // Pull-read every population of node (x, y) and write its moments to M
 // (Sec. VI-A / VI-B moment definitions; Theta of Sec. III for Hookean springs).
-template <typename real>
+template <typename real, typename S>
 __global__ void __launch_bounds__(256) moments_kernel(KernelArgs<real> a) {
   const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
   if (x >= a.nx || y >= a.ny) return;
   const Offsets off = node_offsets(x, y, a.nx, a.ny, a.pitch);
   const size_t P = a.plane;
   const size_t n = off.o[4];
-  const real* __restrict__ src = a.src;
+  const S* __restrict__ src = (const S*)a.src;
   real drho = 0, jx = 0, jy = 0;
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
-    const real h = src[(size_t)i * P + off.o[shift_index(-c9x(i), -c9y(i))]];
+    const real h = from_store<real>(src[(size_t)i * P + off.o[shift_index(-c9x(i), -c9y(i))]]);
     drho += h;
     jx += real(c9x(i)) * h;
     jy += real(c9y(i)) * h;
@@ -146,7 +147,7 @@ __global__ void __launch_bounds__(256) moments_kernel(KernelArgs<real> a) {
       const int e = a.tab.pull[q * 25 + i];
       const size_t o = e >= 0 ? off.o[shift_index(-c.rx, -c.ry)] : off.o[4];
       const int p = e >= 0 ? e : ~e;
-      const real h = src[(size_t)p * P + o] + a.tab.delta[q * 25 + i];
+      const real h = from_store<real>(src[(size_t)p * P + o]) * a.pinv + a.tab.delta[q * 25 + i];
       dpsi += h;
       rx += real(c.rx) * h;
       ry += real(c.ry) * h;
@@ -181,7 +182,7 @@ __global__ void __launch_bounds__(256) moments_kernel(KernelArgs<real> a) {
 // with the quadratic solvent equilibria (Eq. dis_eq), the linear polymer
 // equilibria (Eqs. feq_rq_space, fstar_rq_space) and the Guo source S_i of the
 // force density rho a (solvent only).
-template <typename real>
+template <typename real, typename S>
 __global__ void __launch_bounds__(256) step_kernel(KernelArgs<real> a) {
   __shared__ real sUx[TY + 2][TX + 2];
   __shared__ real sUy[TY + 2][TX + 2];
@@ -210,8 +211,8 @@ __global__ void __launch_bounds__(256) step_kernel(KernelArgs<real> a) {
   const int nq = a.nq;
   const real rho = a.rho0 + a.M[(size_t)(nq + M_DRHO) * P + n];
   const real force = rho * a.tab.arow[y];
-  const real* __restrict__ src = a.src;
-  real* __restrict__ dst = a.dst;
+  const S* __restrict__ src = (const S*)a.src;
+  S* __restrict__ dst = (S*)a.dst;
 
   // ---- solvent
   {
@@ -219,7 +220,7 @@ __global__ void __launch_bounds__(256) step_kernel(KernelArgs<real> a) {
     real drs = 0, jsx = 0, jsy = 0;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-      h[i] = src[(size_t)i * P + off.o[shift_index(-c9x(i), -c9y(i))]];
+      h[i] = from_store<real>(src[(size_t)i * P + off.o[shift_index(-c9x(i), -c9y(i))]]);
       drs += h[i];
       jsx += real(c9x(i)) * h[i];
       jsy += real(c9y(i)) * h[i];
@@ -239,7 +240,7 @@ __global__ void __launch_bounds__(256) step_kernel(KernelArgs<real> a) {
                                      real(4.5) * (a.omr * cus * cus + a.r * cu * cu) -
                                      real(1.5) * sq));
       const real srcterm = real(w9(i)) * (real(3) * (cx - Ux) + real(9) * cu * cx) * force;
-      dst[(size_t)i * P + n] = a.om2b * h[i] + a.tb * feq_dev + a.omb * srcterm;
+      dst[(size_t)i * P + n] = to_store<S>(a.om2b * h[i] + a.tb * feq_dev + a.omb * srcterm);
     }
   }
 
@@ -257,7 +258,7 @@ __global__ void __launch_bounds__(256) step_kernel(KernelArgs<real> a) {
       const int e = a.tab.pull[q * 25 + i];
       const size_t o = e >= 0 ? off.o[shift_index(-c.rx, -c.ry)] : off.o[4];
       const int p = e >= 0 ? e : ~e;
-      h[i] = src[(size_t)p * P + o] + a.tab.delta[q * 25 + i];
+      h[i] = from_store<real>(src[(size_t)p * P + o]) * a.pinv + a.tab.delta[q * 25 + i];
       dpsi += h[i];
       rx += real(c.rx) * h[i];
       ry += real(c.ry) * h[i];
@@ -276,13 +277,13 @@ __global__ void __launch_bounds__(256) step_kernel(KernelArgs<real> a) {
     const real mry = a.omr * (a.c2 * ry + jrey) * a.inv_c2p1 + a.r * jrey;
     const real mqx = a.omr * (a.c2 * qx + jqex) * a.inv_c2p1 + a.r * jqex;
     const real mqy = a.omr * (a.c2 * qy + jqey) * a.inv_c2p1 + a.r * jqey;
-    real* dq = dst + (size_t)(9 + 25 * q) * P + n;
+    S* dq = dst + (size_t)(9 + 25 * q) * P + n;
 #pragma unroll
     for (int i = 0; i < 25; ++i) {
       const V4 c = c25(i);
       const real fdev = real(w25(i)) * (dpsi + real(3) * (mrx * real(c.rx) + mry * real(c.ry) +
                                                            mqx * real(c.qx) + mqy * real(c.qy)));
-      dq[(size_t)i * P] = a.om2b * h[i] + a.tb * fdev;
+      dq[(size_t)i * P] = to_store<S>((a.om2b * h[i] + a.tb * fdev) * a.pscale);
     }
   }
 }
@@ -361,17 +362,20 @@ __global__ void __launch_bounds__(256) psi_kernel(KernelArgs<real> a, double* ou
 }
 
 // Stored populations with the storage shift added back, as doubles.
-template <typename real>
+template <typename real, typename S>
 __global__ void __launch_bounds__(256) populations_kernel(KernelArgs<real> a, double* out) {
+  const S* src = (const S*)a.src;
   const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
   if (x >= a.nx || y >= a.ny) return;
   const size_t n = (size_t)y * a.pitch + x, k = (size_t)y * a.nx + x,
                N = (size_t)a.nx * a.ny;
-  for (int i = 0; i < 9; ++i) out[(size_t)i * N + k] = w9(i) + double(a.src[(size_t)i * a.plane + n]);
+  for (int i = 0; i < 9; ++i)
+    out[(size_t)i * N + k] = w9(i) + from_store<double>(src[(size_t)i * a.plane + n]);
   for (int q = 0; q < a.nq; ++q)
     for (int i = 0; i < 25; ++i) {
       const int p = 9 + 25 * q + i;
-      out[(size_t)p * N + k] = w25(i) * double(a.tab.psi0[q]) + double(a.src[(size_t)p * a.plane + n]);
+      out[(size_t)p * N + k] = w25(i) * double(a.tab.psi0[q]) +
+                               from_store<double>(src[(size_t)p * a.plane + n]) * double(a.pinv);
     }
 }
 
@@ -432,19 +436,19 @@ inline dim3 node_grid(int nx, int ny) { return dim3((nx + TX - 1) / TX, (ny + TY
 
 }  // namespace
 
-template <typename real>
+template <typename real, typename S>
 cudaError_t launch_init(const KernelArgs<real>& a, cudaStream_t s) {
-  init_kernel<real><<<node_grid(a.nx, a.ny), dim3(TX, TY), 0, s>>>(a);
+  init_kernel<real, S><<<node_grid(a.nx, a.ny), dim3(TX, TY), 0, s>>>(a);
   return cudaGetLastError();
 }
-template <typename real>
+template <typename real, typename S>
 cudaError_t launch_moments(const KernelArgs<real>& a, cudaStream_t s) {
-  moments_kernel<real><<<node_grid(a.nx, a.ny), dim3(TX, TY), 0, s>>>(a);
+  moments_kernel<real, S><<<node_grid(a.nx, a.ny), dim3(TX, TY), 0, s>>>(a);
   return cudaGetLastError();
 }
-template <typename real>
+template <typename real, typename S>
 cudaError_t launch_step(const KernelArgs<real>& a, cudaStream_t s) {
-  step_kernel<real><<<node_grid(a.nx, a.ny), dim3(TX, TY), 0, s>>>(a);
+  step_kernel<real, S><<<node_grid(a.nx, a.ny), dim3(TX, TY), 0, s>>>(a);
   return cudaGetLastError();
 }
 template <typename real>
@@ -462,9 +466,9 @@ cudaError_t launch_psi(const KernelArgs<real>& a, double* out, cudaStream_t s) {
   psi_kernel<real><<<node_grid(a.nx, a.ny), dim3(TX, TY), 0, s>>>(a, out);
   return cudaGetLastError();
 }
-template <typename real>
+template <typename real, typename S>
 cudaError_t launch_populations(const KernelArgs<real>& a, double* out, cudaStream_t s) {
-  populations_kernel<real><<<node_grid(a.nx, a.ny), dim3(TX, TY), 0, s>>>(a, out);
+  populations_kernel<real, S><<<node_grid(a.nx, a.ny), dim3(TX, TY), 0, s>>>(a, out);
   return cudaGetLastError();
 }
 template <typename real>
@@ -477,19 +481,23 @@ cudaError_t launch_diag(const KernelArgs<real>& a, double* partials, int nblocks
   return cudaGetLastError();
 }
 
+#define TFKT_INSTANTIATE_POP(real, S)                                                          \
+  template cudaError_t launch_init<real, S>(const KernelArgs<real>&, cudaStream_t);           \
+  template cudaError_t launch_moments<real, S>(const KernelArgs<real>&, cudaStream_t);        \
+  template cudaError_t launch_step<real, S>(const KernelArgs<real>&, cudaStream_t);           \
+  template cudaError_t launch_populations<real, S>(const KernelArgs<real>&, double*,          \
+                                                   cudaStream_t);
 #define TFKT_INSTANTIATE(real)                                                                 \
-  template cudaError_t launch_init<real>(const KernelArgs<real>&, cudaStream_t);              \
-  template cudaError_t launch_moments<real>(const KernelArgs<real>&, cudaStream_t);           \
-  template cudaError_t launch_step<real>(const KernelArgs<real>&, cudaStream_t);              \
   template cudaError_t launch_velocity<real>(const KernelArgs<real>&, cudaStream_t);          \
   template cudaError_t launch_fields<real>(const KernelArgs<real>&, uint32_t, double*,        \
                                            cudaStream_t);                                     \
   template cudaError_t launch_psi<real>(const KernelArgs<real>&, double*, cudaStream_t);      \
-  template cudaError_t launch_populations<real>(const KernelArgs<real>&, double*,             \
-                                                cudaStream_t);                                \
   template cudaError_t launch_diag<real>(const KernelArgs<real>&, double*, int, double*,      \
                                          cudaStream_t);
 TFKT_INSTANTIATE(float)
 TFKT_INSTANTIATE(double)
+TFKT_INSTANTIATE_POP(double, double)
+TFKT_INSTANTIATE_POP(float, float)
+TFKT_INSTANTIATE_POP(float, __half)
 
 }  // namespace tfkt

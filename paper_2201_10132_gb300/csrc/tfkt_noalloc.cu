@@ -41,7 +41,7 @@ tfkt_status scratch_address(void** out) {
   return TFKT_OK;
 }
 
-template <typename real>
+template <typename real, typename S>
 tfkt_status moments_noalloc(const Lattice& L, const void* pops, uint32_t mask, double* dst,
                             cudaStream_t stream) {
   // scratch layout: M planes, U planes, then the tables
@@ -87,7 +87,7 @@ tfkt_status moments_noalloc(const Lattice& L, const void* pops, uint32_t mask, d
   if (e != cudaSuccess) return fail(TFKT_ECUDA, std::string("sync: ") + cudaGetErrorString(e));
 
   KernelArgs<real> a{};
-  a.src = (const real*)pops;
+  a.src = pops;
   a.dst = nullptr;
   a.M = (real*)(b + off_M);
   a.U = (real*)(b + off_U);
@@ -103,6 +103,8 @@ tfkt_status moments_noalloc(const Lattice& L, const void* pops, uint32_t mask, d
   a.psi_tot0 = (real)L.psi_tot;
   a.l2 = (real)(L.ell * L.ell);
   a.H = (real)L.H;
+  a.pscale = (real)polymer_scale(L);
+  a.pinv = (real)(1.0 / polymer_scale(L));
   a.tab.qx = (const real*)(b + off_t[0]);
   a.tab.qy = (const real*)(b + off_t[1]);
   a.tab.psi0 = (const real*)(b + off_t[2]);
@@ -113,7 +115,7 @@ tfkt_status moments_noalloc(const Lattice& L, const void* pops, uint32_t mask, d
   // every scratch value read below is written first by these kernels: the
   // moments kernel writes all M planes of every node, the velocity kernel both
   // U planes of every node, so nothing needs clearing between calls
-  if ((e = launch_moments<real>(a, stream)) != cudaSuccess ||
+  if ((e = launch_moments<real, S>(a, stream)) != cudaSuccess ||
       (e = launch_velocity<real>(a, stream)) != cudaSuccess ||
       (e = launch_fields<real>(a, mask, dst, stream)) != cudaSuccess)
     return fail(TFKT_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
@@ -134,7 +136,9 @@ extern "C" tfkt_status tfkt_moments_noalloc(const tfkt_params* p, const void* po
   if (field_mask == 0 || (field_mask >> TFKT_NFIELDS) != 0) return fail(TFKT_EINVAL, "bad field mask");
   const size_t need = (size_t)__builtin_popcount(field_mask) * L.nx * L.ny * sizeof(double);
   if (bytes < need) return fail(TFKT_EINVAL, "dst too small");
-  return L.precision == TFKT_FP64
-             ? moments_noalloc<double>(L, pops, field_mask, dst, (cudaStream_t)stream)
-             : moments_noalloc<float>(L, pops, field_mask, dst, (cudaStream_t)stream);
+  if (L.precision == TFKT_FP64)
+    return moments_noalloc<double, double>(L, pops, field_mask, dst, (cudaStream_t)stream);
+  if (L.precision == TFKT_FP32)
+    return moments_noalloc<float, float>(L, pops, field_mask, dst, (cudaStream_t)stream);
+  return moments_noalloc<float, __half>(L, pops, field_mask, dst, (cudaStream_t)stream);
 }

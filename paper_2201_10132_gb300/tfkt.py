@@ -15,7 +15,7 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_build", "libtfkt.so")
 
-FP64, FP32 = 0, 1
+FP64, FP32, FP16 = 0, 1, 2
 FIELDS = ["rho_s", "psi_tot", "ux", "uy", "cxx", "cxy", "cyy", "thxx", "thxy", "thyy", "qrms",
           "vort"]
 KERNELS = ["moments", "step", "fused", "fixup"]

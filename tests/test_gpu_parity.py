@@ -137,6 +137,30 @@ def test_fp32_within_tolerance(T, oracle_mod, case):
         assert err < 2e-5, (k, err)
 
 
+@pytest.mark.parametrize("case", [CASES[1], CASES[7], CASES[9]])
+def test_fp16_storage_within_tolerance(T, oracle_mod, case):
+    """FP16 storage (half deviations, polymer scaled by a power of two, FP32
+    arithmetic): each stored value is rounded to 11 bits every step, so the
+    velocity error after n steps is about sqrt(n) 2^-12 times the deviation scale
+    (~0.15 w_i) summed over ~25 nq + 9 terms; allowed: 3e-3 of the velocity
+    scale and 3e-3 of each other field's largest magnitude for n <= 25."""
+    from paper_2201_10132_gb300.inputs import perturbation
+    nx, ny, S, R, re, wi, beta, kp, tau2, ic, steps = case
+    pert = perturbation(nx, ny, 7, 0.05, 0.05)
+    p = T.Params(nx, ny, S, R, re, wi, beta, 0.05, kp, tau2, 0.0, ic, T.FP16)
+    o = _oracle_run(oracle_mod, nx, ny, S, R, re, wi, beta, kp, tau2, pert, ic, steps)
+    with T.Solver(p, pert) as s:
+        s.step(steps)
+        g = s.moments()
+    f = o.fields()
+    uscale = max(np.abs(f["ux"]).max(), np.abs(f["uy"]).max())
+    errs = {}
+    for k in FIELDS:
+        scale = uscale if k in ("ux", "uy", "vort") else np.abs(f[k]).max()
+        errs[k] = np.abs(g[k] - f[k]).max() / scale
+    assert max(errs.values()) < 3e-3, errs
+
+
 def test_full_size_tiled_matches_oracle(T, oracle_mod):
     """The 4096^2, N_Q = 32 throughput workload in its benchmark launch configuration
     (FP32), started from a perturbation that repeats every 64 nodes: with the
