@@ -177,6 +177,50 @@ def run_reference(args, W):
     print(json.dumps(line), flush=True)
 
 
+def precision_sweep(W, steps: int):
+    """FP64 vs FP32 vs FP16 storage from the identical seeded state: per-field relative
+    L2 / Linf errors against the FP64 run after `steps` steps, the growth rate of
+    sum U_y^2 (the instability indicator) over the run, and the fused-kernel time."""
+    import numpy as np
+    import torch
+    from paper_2201_10132_gb300 import tfkt
+    from paper_2201_10132_gb300.inputs import perturbation
+    pert = perturbation(W.nx, W.ny, W.seed, W.amp, W.u0)
+    names = ["ux", "uy", "rho_s", "cxy", "thxy"]
+    out, ref = {}, None
+    for label, prec in (("fp64", tfkt.FP64), ("fp32", tfkt.FP32), ("fp16", tfkt.FP16)):
+        p = tfkt.Params.from_workload(W, prec)
+        ws = torch.empty(tfkt.required_bytes(p), dtype=torch.uint8, device="cuda")
+        s = tfkt.Solver(p, pert, workspace=ws)
+        e0 = s.diagnostics()["ey2"]
+        kms = np.zeros(len(tfkt.KERNELS))
+        n = np.zeros(len(tfkt.KERNELS), np.int64)
+        s.step_profiled(steps, kms, n)
+        e1 = s.diagnostics()["ey2"]
+        f = s.moments(names)
+        s.close()
+        del s, ws
+        torch.cuda.empty_cache()
+        k = tfkt.KERNELS.index("fused")
+        r = {"fused_ms": kms[k] / max(n[k], 1), "ey2_rate": math.log(e1 / e0) / steps}
+        if ref is None:
+            ref = f
+        else:
+            uscale = max(np.abs(ref["ux"]).max(), np.abs(ref["uy"]).max())
+            for name in names:
+                d = f[name] - ref[name]
+                scale = uscale if name in ("ux", "uy") else np.abs(ref[name]).max()
+                r[name + "_linf"] = float(np.abs(d).max() / scale)
+                r[name + "_l2"] = float(np.sqrt(np.mean(d * d)) /
+                                        max(np.sqrt(np.mean(ref[name] ** 2)), 1e-300))
+            r["ey2_rate_rel_err"] = abs(r["ey2_rate"] - out["fp64"]["ey2_rate"]) / max(
+                abs(out["fp64"]["ey2_rate"]), 1e-300)
+        out[label] = r
+    for label in ("fp32", "fp16"):
+        out[label]["speedup_vs_fp32"] = out["fp32"]["fused_ms"] / out[label]["fused_ms"]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -186,11 +230,20 @@ def main():
     ap.add_argument("--workload", default="kolmogorov-4096x4096-nq32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--precision-sweep", type=int, default=0, metavar="STEPS",
+                    help="instead of the throughput line: FP64 vs FP32 vs FP16 errors and times")
     args = ap.parse_args()
     from paper_2201_10132_gb300.inputs import WORKLOADS
     W = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, W)
+
+    if args.precision_sweep:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        print(json.dumps({"precision_sweep": precision_sweep(W, args.precision_sweep),
+                          "workload": W.name, "steps": args.precision_sweep}), flush=True)
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
