@@ -221,6 +221,35 @@ def precision_sweep(W, steps: int):
     return out
 
 
+def ensemble_throughput(n_runs: int, steps: int, warmup: int):
+    """Aggregate GLUPS of a seeded ensemble advanced as one batch (one launch of the
+    fused kernel and one of its fix-up per step, replayed from a CUDA graph)."""
+    import torch
+    from paper_2201_10132_gb300 import tfkt
+    from paper_2201_10132_gb300.inputs import ensemble, perturbation
+    runs = ensemble(n_runs)
+    params = [tfkt.Params.from_workload(w, tfkt.FP32) for w in runs]
+    perts = [perturbation(w.nx, w.ny, w.seed, w.amp, w.u0) for w in runs]
+    ws = torch.empty(tfkt.batch_required_bytes(params), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.Stream()
+    nodes = sum(w.nx * w.ny for w in runs)
+    with tfkt.Batch(params, perts, workspace=ws, stream=stream.cuda_stream) as b:
+        b.step(warmup)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.step(steps)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        diag = [b.run(i).diagnostics() for i in (0, n_runs - 1)]
+    assert all(math.isfinite(v) for d in diag for v in d.values())
+    return {"runs": n_runs, "r_nodes": nodes, "steps": steps, "ms_per_step": ms / steps,
+            "value": aggregate_glups(1, nodes, steps, ms / 1e3), "unit": "GLUPS",
+            "workspace_gb": ws.numel() / 1e9, "nq": 9}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -230,6 +259,8 @@ def main():
     ap.add_argument("--workload", default="kolmogorov-4096x4096-nq32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--ensemble", type=int, default=0, metavar="RUNS",
+                    help="instead of the throughput line: a seeded ensemble advanced as one batch")
     ap.add_argument("--precision-sweep", type=int, default=0, metavar="STEPS",
                     help="instead of the throughput line: FP64 vs FP32 vs FP16 errors and times")
     args = ap.parse_args()
@@ -238,6 +269,12 @@ def main():
     if args.impl == "reference":
         return run_reference(args, W)
 
+    if args.ensemble:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        print(json.dumps({"ensemble": ensemble_throughput(args.ensemble, args.steps,
+                                                          args.warmup)}), flush=True)
+        return
     if args.precision_sweep:
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))

@@ -207,6 +207,37 @@ tfkt_status tfkt_sync(tfkt_ctx* ctx);
    Synchronises first. NULL is accepted. */
 tfkt_status tfkt_destroy(tfkt_ctx* ctx);
 
+/* ---- Batched ensembles -------------------------------------------------
+   Many independent Kolmogorov runs (their own grid size, Re, Wi, beta,
+   forcing and seed) advanced together: every step is one launch of the fused
+   kernel over the tiles of all runs plus one launch of its border fix-up,
+   replayed from a CUDA graph two steps at a time. The paper runs one case at
+   a time; batching is this library's addition. Requirements: every run uses
+   TFKT_FP32 and has nx a multiple of 32 and ny a multiple of 8 (the fused
+   path); otherwise TFKT_EINVAL. */
+typedef struct tfkt_batch tfkt_batch;
+
+/* Device bytes for the batch (the runs' workspaces and the launch tables). */
+tfkt_status tfkt_batch_required_bytes(const tfkt_params* runs, int32_t n, size_t* bytes);
+
+/* Create n runs. perturbs: n host pointers to [2][ny][nx] perturbations (or
+   NULL entries, or perturbs NULL). dev_workspace/bytes as in tfkt_create. The
+   batch uses the caller's stream if it is not NULL, else one it creates (a CUDA
+   graph cannot capture the legacy default stream). */
+tfkt_status tfkt_batch_create(const tfkt_params* runs, int32_t n, const double* const* perturbs,
+                              void* dev_workspace, size_t workspace_bytes, void* stream,
+                              tfkt_batch** out);
+
+/* Advance every run by n >= 0 steps (asynchronous on the batch stream). */
+tfkt_status tfkt_batch_step(tfkt_batch* b, int64_t n);
+
+/* The context of run i (0 <= i < n), for tfkt_moments, tfkt_diagnostics,
+   tfkt_psi, tfkt_populations and tfkt_get_info; owned by the batch: do not
+   call tfkt_step or tfkt_destroy on it. */
+tfkt_status tfkt_batch_run(tfkt_batch* b, int32_t i, tfkt_ctx** run);
+
+tfkt_status tfkt_batch_destroy(tfkt_batch* b);
+
 const char* tfkt_status_string(tfkt_status s);
 /* Text of the last error seen by this thread ("" if none). */
 const char* tfkt_last_error(void);

@@ -521,6 +521,24 @@ using namespace tfkt;
 
 struct tfkt_ctx : public Ctx {};
 
+namespace tfkt {
+Ctx* ctx_of(tfkt_ctx* c) { return c; }
+size_t ctx_layout(const Lattice& L) {
+  Workspace w;
+  return layout(L, &w);
+}
+template <typename real>
+KernelArgs<real> ctx_args(const Ctx* c) {
+  return make_args<real>(c);
+}
+template <typename real>
+FusedArgs<real> ctx_fused(const Ctx* c) {
+  return make_fused<real>(c);
+}
+template KernelArgs<float> ctx_args<float>(const Ctx*);
+template FusedArgs<float> ctx_fused<float>(const Ctx*);
+}  // namespace tfkt
+
 extern "C" {
 
 tfkt_status tfkt_required_bytes(const tfkt_params* p, size_t* bytes) {

@@ -1,0 +1,229 @@
+// Batched ensembles: independent runs sharing one launch of the fused kernel
+// (and one of its border fix-up) per step, replayed from a CUDA graph.
+#include <cuda_runtime.h>
+
+#include <new>
+#include <string>
+#include <vector>
+
+#include "tfkt_internal.cuh"
+
+struct tfkt_batch {
+  std::vector<tfkt_ctx*> runs;
+  void* ws = nullptr;
+  bool owned = false;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  tfkt::BatchRun<float>* d_runs = nullptr;  // in the workspace
+  int* d_tile_start = nullptr;             // in the workspace, n + 1 entries
+  int total_tiles = 0, max_nq = 0;
+  int parity = 0;                          // buffer parity shared by all runs
+  cudaGraphExec_t graph = nullptr;         // two steps: parity 0 then 1
+  int64_t step = 0;
+};
+
+namespace tfkt {
+namespace {
+
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+tfkt_status check_runs(const tfkt_params* runs, int32_t n, std::vector<Lattice>& L) {
+  if (!runs || n < 1) return fail(TFKT_EINVAL, "a batch needs at least one run");
+  L.resize(n);
+  for (int32_t i = 0; i < n; ++i) {
+    tfkt_status s = map_params(&runs[i], &L[i]);
+    if (s != TFKT_OK) return s;
+    if (runs[i].precision != TFKT_FP32) return fail(TFKT_EINVAL, "batched runs must use TFKT_FP32");
+    if (!fused_supported(L[i].nx, L[i].ny, L[i].nq, 4))
+      return fail(TFKT_EINVAL, "batched runs need nx % 32 == 0 and ny % 8 == 0 (run " +
+                                   std::to_string(i) + ")");
+  }
+  return TFKT_OK;
+}
+
+// Workspace: the runs' workspaces one after another, then the launch tables.
+size_t batch_layout(const std::vector<Lattice>& L, std::vector<size_t>& off, size_t* off_tab) {
+  size_t o = 0;
+  off.resize(L.size());
+  for (size_t i = 0; i < L.size(); ++i) {
+    off[i] = o;
+    o = align256(o + ctx_layout(L[i]));
+  }
+  *off_tab = o;
+  o = align256(o + L.size() * sizeof(BatchRun<float>));
+  o = align256(o + (L.size() + 1) * sizeof(int));
+  return o;
+}
+
+void release(tfkt_batch* b) {
+  for (tfkt_ctx* c : b->runs)
+    if (c) tfkt_destroy(c);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->owned && b->ws) cudaFree(b->ws);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+tfkt_status plain_step(tfkt_batch* b) {
+  cudaError_t e = launch_batch_step(b->d_runs, b->d_tile_start, (int)b->runs.size(),
+                                    b->total_tiles, b->max_nq, b->parity, b->stream);
+  if (e != cudaSuccess) return fail(TFKT_ECUDA, std::string("batch step: ") + cudaGetErrorString(e));
+  b->parity ^= 1;
+  return TFKT_OK;
+}
+
+}  // namespace
+}  // namespace tfkt
+
+using namespace tfkt;
+
+extern "C" {
+
+tfkt_status tfkt_batch_required_bytes(const tfkt_params* runs, int32_t n, size_t* bytes) {
+  if (!bytes) return fail(TFKT_EINVAL, "bytes is NULL");
+  std::vector<Lattice> L;
+  tfkt_status s = check_runs(runs, n, L);
+  if (s != TFKT_OK) return s;
+  std::vector<size_t> off;
+  size_t tab;
+  *bytes = batch_layout(L, off, &tab);
+  return TFKT_OK;
+}
+
+tfkt_status tfkt_batch_create(const tfkt_params* runs, int32_t n, const double* const* perturbs,
+                              void* dev_workspace, size_t workspace_bytes, void* stream,
+                              tfkt_batch** out) {
+  if (!out) return fail(TFKT_EINVAL, "out is NULL");
+  *out = nullptr;
+  std::vector<Lattice> L;
+  tfkt_status s = check_runs(runs, n, L);
+  if (s != TFKT_OK) return s;
+  std::vector<size_t> off;
+  size_t off_tab;
+  const size_t need = batch_layout(L, off, &off_tab);
+  tfkt_batch* b = new (std::nothrow) tfkt_batch();
+  if (!b) return fail(TFKT_ENOMEM, "host allocation failed");
+  if (dev_workspace) {
+    if (workspace_bytes < need || ((uintptr_t)dev_workspace) % 256) {
+      delete b;
+      return fail(TFKT_ENOMEM, "workspace too small or not 256-byte aligned: need " +
+                                   std::to_string(need) + " bytes");
+    }
+    b->ws = dev_workspace;
+  } else {
+    cudaError_t e = cudaMalloc(&b->ws, need);
+    if (e != cudaSuccess) {
+      delete b;
+      cudaGetLastError();
+      return fail(TFKT_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    b->owned = true;
+  }
+  if (stream) {
+    b->stream = (cudaStream_t)stream;
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      release(b);
+      return fail(TFKT_ECUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+    }
+    b->own_stream = true;
+  }
+  std::vector<BatchRun<float>> host(n);
+  std::vector<int> tile_start(n + 1, 0);
+  for (int32_t i = 0; i < n; ++i) {
+    tfkt_ctx* c = nullptr;
+    s = tfkt_create(&runs[i], perturbs ? perturbs[i] : nullptr, (char*)b->ws + off[i],
+                    ctx_layout(L[i]), b->stream, &c);
+    if (s != TFKT_OK) {
+      release(b);
+      return s;
+    }
+    b->runs.push_back(c);
+    Ctx* x = ctx_of(c);
+    for (int p = 0; p < 2; ++p) {
+      x->cur = x->mcur = p;
+      host[i].a[p] = ctx_args<float>(x);
+      host[i].f[p] = ctx_fused<float>(x);
+    }
+    x->cur = x->mcur = 0;
+    host[i].ntx = L[i].nx / TX;
+    host[i].nty = L[i].ny / TY;
+    tile_start[i + 1] = tile_start[i] + host[i].ntx * host[i].nty;
+    if (L[i].nq > b->max_nq) b->max_nq = L[i].nq;
+  }
+  b->total_tiles = tile_start[n];
+  b->d_runs = (BatchRun<float>*)((char*)b->ws + off_tab);
+  b->d_tile_start = (int*)((char*)b->ws + align256(off_tab + n * sizeof(BatchRun<float>)));
+  cudaError_t e = cudaMemcpy(b->d_runs, host.data(), n * sizeof(BatchRun<float>),
+                             cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->d_tile_start, tile_start.data(), (n + 1) * sizeof(int),
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = prepare_batch(b->max_nq);
+  if (e != cudaSuccess) {
+    release(b);
+    return fail(TFKT_ECUDA, std::string("batch tables: ") + cudaGetErrorString(e));
+  }
+  *out = b;
+  return TFKT_OK;
+}
+
+tfkt_status tfkt_batch_step(tfkt_batch* b, int64_t n) {
+  if (!b) return fail(TFKT_EINVAL, "batch is NULL");
+  if (n < 0) return fail(TFKT_EINVAL, "n must be >= 0");
+  tfkt_status s = TFKT_OK;
+  int64_t left = n;
+  if (left > 0 && b->parity == 1) {
+    s = plain_step(b);
+    --left;
+  }
+  if (left >= 2 && !b->graph) {
+    // capture two steps (parity 0 then 1) once
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t e1 = launch_batch_step(b->d_runs, b->d_tile_start, (int)b->runs.size(),
+                                         b->total_tiles, b->max_nq, 0, b->stream);
+      cudaError_t e2 = launch_batch_step(b->d_runs, b->d_tile_start, (int)b->runs.size(),
+                                         b->total_tiles, b->max_nq, 1, b->stream);
+      e = cudaStreamEndCapture(b->stream, &g);
+      if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(TFKT_ECUDA, std::string("graph: ") + cudaGetErrorString(e));
+  }
+  while (s == TFKT_OK && left >= 2) {
+    cudaError_t e = cudaGraphLaunch(b->graph, b->stream);
+    if (e != cudaSuccess) return fail(TFKT_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+    left -= 2;
+  }
+  if (s == TFKT_OK && left == 1) s = plain_step(b);
+  if (s != TFKT_OK) return s;
+  b->step += n;
+  // keep every run's view of the state current
+  for (tfkt_ctx* c : b->runs) {
+    Ctx* x = ctx_of(c);
+    x->cur = x->mcur = b->parity;
+    x->step = b->step;
+  }
+  return TFKT_OK;
+}
+
+tfkt_status tfkt_batch_run(tfkt_batch* b, int32_t i, tfkt_ctx** run) {
+  if (!b || !run || i < 0 || i >= (int32_t)b->runs.size())
+    return fail(TFKT_EINVAL, "bad batch, run index or output pointer");
+  *run = b->runs[i];
+  return TFKT_OK;
+}
+
+tfkt_status tfkt_batch_destroy(tfkt_batch* b) {
+  if (!b) return TFKT_OK;
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  release(b);
+  if (e != cudaSuccess) return fail(TFKT_ECUDA, std::string("destroy: ") + cudaGetErrorString(e));
+  return TFKT_OK;
+}
+
+}  // extern "C"

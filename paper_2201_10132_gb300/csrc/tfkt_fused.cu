@@ -177,14 +177,16 @@ __device__ __forceinline__ void velocity_at(const KernelArgs<real>& a, const rea
   uy = (jy + real(0.5) * ey) / rho;
 }
 
+// One tile (btx, bty) of an ntx x nty tile grid; shared by the single-run and
+// the batched kernels.
 template <typename real, typename S>
-__global__ void __launch_bounds__(NT, 2)
-step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const FusedArgs<real>& fa,
+                                           int btx, int bty, int ntx, int nty,
+                                           unsigned char* smem_raw) {
   const int nq = a.nq;
   Smem<real> sm = carve<real>(smem_raw, nq);
   const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * TX + lx;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int x0 = btx * TX, y0 = bty * TY;
   const int x = x0 + lx, y = y0 + ly;
   const size_t P = a.plane;
   const real* __restrict__ Min = fa.Min;
@@ -472,8 +474,8 @@ step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
     Mout[(size_t)(nq + M_JY) * P + n] = jy_arr;
   }
   if (ring_thread) {
-    const size_t ntiles = (size_t)gridDim.x * gridDim.y;
-    const size_t tile = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+    const size_t ntiles = (size_t)ntx * nty;
+    const size_t tile = (size_t)bty * ntx + btx;
     real* ex = fa.exports;
     for (int p = 0; p < nq; ++p) ex[((size_t)p * ntiles + tile) * RING + tid] = sm.Ar[p * RING + tid];
     ex[((size_t)(nq + 0) * ntiles + tile) * RING + tid] = ms_r;
@@ -482,12 +484,20 @@ step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
   }
 }
 
+template <typename real, typename S>
+__global__ void __launch_bounds__(NT, 2)
+step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  fused_body<real, S>(a, fa, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y, smem_raw);
+}
+
 // Completes the border nodes of every tile: own partial sums plus the ring
 // exports of the neighbouring tiles (left, right, down, up, then the four
 // diagonal neighbours at corners), plus the constant shift terms; then
 // delta rho and delta Theta.
 template <typename real>
-__global__ void __launch_bounds__(128) fixup_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
+__device__ __forceinline__ void fixup_body(const KernelArgs<real>& a, const FusedArgs<real>& fa,
+                                           int tx, int ty, int ntx, int nty) {
   constexpr int NB = 2 * TX + 2 * (TY - 2);
   const int k = threadIdx.x;
   if (k >= NB) return;
@@ -496,8 +506,6 @@ __global__ void __launch_bounds__(128) fixup_kernel(KernelArgs<real> a, FusedArg
   else if (k < 2 * TX) { lx = k - TX; ly = TY - 1; }
   else if (k < 2 * TX + TY - 2) { lx = 0; ly = 1 + (k - 2 * TX); }
   else { lx = TX - 1; ly = 1 + (k - 2 * TX - (TY - 2)); }
-  const int ntx = gridDim.x, nty = gridDim.y;
-  const int tx = blockIdx.x, ty = blockIdx.y;
   const size_t ntiles = (size_t)ntx * nty;
   const int nq = a.nq;
   const size_t P = a.plane;
@@ -562,6 +570,69 @@ __global__ void __launch_bounds__(128) fixup_kernel(KernelArgs<real> a, FusedArg
   M[(size_t)(nq + M_THYY) * P + n] = a.hl2h * tyy;
 }
 
+template <typename real>
+__global__ void __launch_bounds__(128) fixup_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
+  fixup_body<real>(a, fa, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
+}
+
+// ---------------------------------------------------------------- batches
+// Many independent runs in one launch: block b is tile b of the concatenated
+// tile lists; it finds its run, copies that run's arguments (for the current
+// buffer parity) into shared memory and advances the tile like the
+// single-run kernel.
+__device__ __forceinline__ int find_run(const int* tile_start, int nruns, int t) {
+  int lo = 0, hi = nruns - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tile_start[mid] <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename T>
+__device__ __forceinline__ void copy_words(T* dst, const T* src, int tid, int nthreads) {
+  static_assert(sizeof(T) % 4 == 0, "");
+  const int* s = (const int*)src;
+  int* d = (int*)dst;
+  for (int k = tid; k < (int)(sizeof(T) / 4); k += nthreads) d[k] = s[k];
+}
+
+template <typename real, typename S>
+__global__ void __launch_bounds__(NT, 2)
+step_fused_batch_kernel(const BatchRun<real>* runs, const int* tile_start, int nruns, int parity) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ KernelArgs<real> sa;
+  __shared__ FusedArgs<real> sf;
+  __shared__ int s_run;
+  const int tid = threadIdx.y * TX + threadIdx.x;
+  if (tid == 0) s_run = find_run(tile_start, nruns, blockIdx.x);
+  __syncthreads();
+  const BatchRun<real>& br = runs[s_run];
+  copy_words(&sa, &br.a[parity], tid, NT);
+  copy_words(&sf, &br.f[parity], tid, NT);
+  __syncthreads();
+  const int local = blockIdx.x - tile_start[s_run];
+  fused_body<real, S>(sa, sf, local % br.ntx, local / br.ntx, br.ntx, br.nty, smem_raw);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(128) fixup_batch_kernel(const BatchRun<real>* runs,
+                                                          const int* tile_start, int nruns,
+                                                          int parity) {
+  __shared__ KernelArgs<real> sa;
+  __shared__ FusedArgs<real> sf;
+  __shared__ int s_run;
+  if (threadIdx.x == 0) s_run = find_run(tile_start, nruns, blockIdx.x);
+  __syncthreads();
+  const BatchRun<real>& br = runs[s_run];
+  copy_words(&sa, &br.a[parity], threadIdx.x, blockDim.x);
+  copy_words(&sf, &br.f[parity], threadIdx.x, blockDim.x);
+  __syncthreads();
+  const int local = blockIdx.x - tile_start[s_run];
+  fixup_body<real>(sa, sf, local % br.ntx, local / br.ntx, br.ntx, br.nty);
+}
+
 }  // namespace
 
 size_t fused_smem_bytes(int nq, size_t real_bytes) {
@@ -591,6 +662,23 @@ cudaError_t launch_step_fused(const KernelArgs<real>& a, const FusedArgs<real>& 
 template <typename real>
 cudaError_t launch_fixup(const KernelArgs<real>& a, const FusedArgs<real>& f, cudaStream_t s) {
   fixup_kernel<real><<<dim3(a.nx / TX, a.ny / TY), 128, 0, s>>>(a, f);
+  return cudaGetLastError();
+}
+
+cudaError_t prepare_batch(int max_nq) {
+  const size_t smem = fused_smem_bytes(max_nq, sizeof(float));
+  return cudaFuncSetAttribute(step_fused_batch_kernel<float, float>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t launch_batch_step(const BatchRun<float>* runs, const int* tile_start, int nruns,
+                              int total_tiles, int max_nq, int parity, cudaStream_t s) {
+  const size_t smem = fused_smem_bytes(max_nq, sizeof(float));
+  step_fused_batch_kernel<float, float><<<total_tiles, dim3(TX, TY), smem, s>>>(runs, tile_start,
+                                                                               nruns, parity);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  fixup_batch_kernel<float><<<total_tiles, 128, 0, s>>>(runs, tile_start, nruns, parity);
   return cudaGetLastError();
 }
 

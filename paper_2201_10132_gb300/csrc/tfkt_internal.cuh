@@ -132,6 +132,15 @@ struct FusedArgs {
   real dvx, dvy;        // r-momentum of all pull shift differences
 };
 
+// One run of a batch: its kernel arguments for both buffer parities.
+template <typename real>
+struct BatchRun {
+  KernelArgs<real> a[2];
+  FusedArgs<real> f[2];
+  int ntx, nty;
+  int pad[2];
+};
+
 struct Workspace {
   void* base = nullptr;
   size_t bytes = 0;
@@ -201,6 +210,18 @@ template <typename real, typename S>
 cudaError_t launch_step_fused(const KernelArgs<real>& a, const FusedArgs<real>& f, cudaStream_t s);
 template <typename real>
 cudaError_t launch_fixup(const KernelArgs<real>& a, const FusedArgs<real>& f, cudaStream_t s);
+
+// Batched fused step (FP32): all tiles of all runs in one launch of each kernel.
+cudaError_t prepare_batch(int max_nq);
+cudaError_t launch_batch_step(const BatchRun<float>* runs, const int* tile_start, int nruns,
+                              int total_tiles, int max_nq, int parity, cudaStream_t s);
+// Access to a context's internals and argument builders (tfkt_api.cu).
+Ctx* ctx_of(tfkt_ctx* c);
+size_t ctx_layout(const Lattice& L);
+template <typename real>
+KernelArgs<real> ctx_args(const Ctx* c);
+template <typename real>
+FusedArgs<real> ctx_fused(const Ctx* c);
 
 constexpr int TX = 32;   // tile width (one warp along x)
 constexpr int TY = 8;    // tile height

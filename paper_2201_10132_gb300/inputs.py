@@ -105,3 +105,24 @@ KOLMOGOROV_1024 = Workload("kolmogorov-1024x1024-nq32", 1024, 1024, 6, 3.0, 10.0
 KOLMOGOROV_512 = Workload("kolmogorov-512x512-nq32", 512, 512, 6, 3.0, 10.0, 1.0, 0.2, 0.05,
                           8, 0, 1e-3)
 WORKLOADS = {w.name: w for w in (KOLMOGOROV_64, KOLMOGOROV_512, KOLMOGOROV_1024, KOLMOGOROV_4096)}
+
+
+def ensemble(n: int = 256, seed: int = 0, q_side: int = 3, q_radius: float = 1.5):
+    """A seeded ensemble of independent Kolmogorov runs: square grids drawn from
+    {128, 256, 512, 1024}, Re uniform in [1, 20], Wi uniform in [0.1, 2], beta from
+    {0.1, 0.2, 0.5}, forcing wavelength 64 nodes, a small Q-grid (3 x 3 masked to
+    R = 1.5: 9 nodes) so that ~89 M r-nodes fit in memory in FP32. Wi is kept away
+    from 0, where the dilute polymer density psi_tot = 3 eta_p / lambda_H diverges."""
+    rng = splitmix64(seed ^ 0x5EED)
+    u = lambda: (next(rng) >> 11) * 2.0 ** -53
+    sizes = (128, 256, 512, 1024)
+    betas = (0.1, 0.2, 0.5)
+    runs = []
+    for k in range(n):
+        side = sizes[int(u() * 4) % 4]
+        re = 1.0 + 19.0 * u()
+        wi = 0.1 + 1.9 * u()
+        beta = betas[int(u() * 3) % 3]
+        runs.append(Workload(f"ensemble-{k}", side, side, q_side, q_radius, re, wi, beta, 0.05,
+                             side // 64, seed * 100003 + k, 1e-3))
+    return runs

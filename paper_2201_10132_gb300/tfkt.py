@@ -105,6 +105,17 @@ def lib() -> ctypes.CDLL:
         L.tfkt_lattice.argtypes = [ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
         L.tfkt_sync.argtypes = [P]
         L.tfkt_destroy.argtypes = [P]
+        L.tfkt_batch_required_bytes.argtypes = [ctypes.POINTER(_Params), ctypes.c_int32,
+                                                 ctypes.POINTER(ctypes.c_size_t)]
+        L.tfkt_batch_create.argtypes = [ctypes.POINTER(_Params), ctypes.c_int32,
+                                         ctypes.POINTER(D), P, ctypes.c_size_t, P,
+                                         ctypes.POINTER(P)]
+        L.tfkt_batch_step.argtypes = [P, ctypes.c_int64]
+        L.tfkt_batch_run.argtypes = [P, ctypes.c_int32, ctypes.POINTER(P)]
+        L.tfkt_batch_destroy.argtypes = [P]
+        for n in ("tfkt_batch_required_bytes", "tfkt_batch_create", "tfkt_batch_step",
+                  "tfkt_batch_run", "tfkt_batch_destroy"):
+            getattr(L, n).restype = S
         L.tfkt_status_string.argtypes = [S]
         L.tfkt_status_string.restype = ctypes.c_char_p
         L.tfkt_last_error.restype = ctypes.c_char_p
@@ -253,3 +264,76 @@ class Solver:
         buf = np.empty((9 + 25 * nq, ny, nx), np.float64)
         _check(lib().tfkt_populations(self._h, _dptr(buf), buf.nbytes), "tfkt_populations")
         return buf
+
+
+def batch_required_bytes(runs) -> int:
+    arr = (_Params * len(runs))(*[r._c() for r in runs])
+    n = ctypes.c_size_t()
+    _check(lib().tfkt_batch_required_bytes(arr, len(runs), ctypes.byref(n)),
+           "tfkt_batch_required_bytes")
+    return n.value
+
+
+class _RunView(Solver):
+    """A run of a batch: the context calls of Solver, without ownership."""
+
+    def __init__(self, handle, params):
+        self.params = params
+        self._workspace = None
+        self._h = handle
+        self.info = self.get_info()
+
+    def close(self):
+        self._h = ctypes.c_void_p()
+
+    def step(self, n: int = 1):
+        raise TfktError(1, "step", "advance a batch with Batch.step")
+
+
+class Batch:
+    """tfkt_batch: independent runs advanced together by one launch per kernel per step."""
+
+    def __init__(self, runs, perturbs=None, workspace=None, stream: int | None = None):
+        self.params = list(runs)
+        n = len(self.params)
+        arr = (_Params * n)(*[r._c() for r in self.params])
+        self._perturbs = None
+        pp = None
+        if perturbs is not None:
+            self._perturbs = [None if p is None else np.ascontiguousarray(p, dtype=np.float64)
+                              for p in perturbs]
+            pp = (ctypes.POINTER(ctypes.c_double) * n)(
+                *[_dptr(p) if p is not None else ctypes.POINTER(ctypes.c_double)()
+                  for p in self._perturbs])
+        self._workspace = workspace
+        ws_ptr = workspace.data_ptr() if workspace is not None else None
+        ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+        h = ctypes.c_void_p()
+        _check(lib().tfkt_batch_create(arr, n, pp, ws_ptr, ws_bytes, stream, ctypes.byref(h)),
+               "tfkt_batch_create")
+        self._h = h
+
+    def step(self, n: int = 1):
+        _check(lib().tfkt_batch_step(self._h, int(n)), "tfkt_batch_step")
+
+    def run(self, i: int) -> Solver:
+        r = ctypes.c_void_p()
+        _check(lib().tfkt_batch_run(self._h, int(i), ctypes.byref(r)), "tfkt_batch_run")
+        return _RunView(r, self.params[i])
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _check(lib().tfkt_batch_destroy(self._h), "tfkt_batch_destroy")
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
