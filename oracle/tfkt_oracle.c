@@ -34,6 +34,7 @@ struct orc_state {
   int* qgi; int* qgj;     /* grid indices of node q */
   double* Qx; double* Qy; /* Q lattice coordinates of node q */
   double* psi0;           /* initial psi(q) */
+  double* phi;            /* spring factor of Q-node q: 1 (Hookean) or 1/(1 - Q^2/Q0^2) (FENE) */
   int cs[9][2]; double ws[9]; int opps[9];
   int cp[25][4]; double wp[25]; int oppp[25];
   double* gs; double* gp;         /* pre-collision g (after streaming) */
@@ -111,7 +112,7 @@ void orc_d4q25(int32_t* c, double* w, int32_t* opp) {
 int orc_map_params(const orc_phys* in, orc_lattice* out) {
   if (in->nx < 1 || in->ny < 1 || in->q_side < 1 || !(in->q_radius > 0)) return -1;
   if (!(in->re > 0) || !(in->beta > 0) || in->beta > 1 || !(in->u0 > 0)) return -1;
-  if (in->k_periods < 1 || in->wi < 0) return -1;
+  if (in->k_periods < 1 || in->wi < 0 || in->fene_b < 0) return -1;
   if (in->wi == 0 && in->beta < 1) return -1;
   memset(out, 0, sizeof *out);
   out->nx = in->nx;
@@ -137,6 +138,7 @@ int orc_map_params(const orc_phys* in, orc_lattice* out) {
   out->eta_p = eta_p;
   out->u0 = in->u0;
   out->a0 = nu * in->u0 * kf * kf;
+  out->fene_b = in->fene_b;
   if (in->wi > 0) {
     double lam = in->wi * l / in->u0;
     out->lambda_h = lam;
@@ -151,6 +153,8 @@ int orc_map_params(const orc_phys* in, orc_lattice* out) {
     out->sigma_q2 = 1.0;
     out->psi_tot = 0;
   }
+  /* FENE: every kept Q-node must lie strictly inside |Q| < Q0 = sqrt(b) sigma_Q */
+  if (in->fene_b > 0 && in->q_radius * in->q_radius >= in->fene_b * out->sigma_q2) return -1;
   return 0;
 }
 
@@ -195,9 +199,23 @@ orc_state* orc_create(const orc_lattice* lat) {
     }
   st->nq = nq;
   st->psi0 = (double*)xcalloc((size_t)nq, sizeof(double));
+  st->phi = (double*)xcalloc((size_t)nq, sizeof(double));
+  /* Spring law: Hookean F = H Q, or FENE F = H Q / (1 - |Q|^2 / Q0^2) with
+     Q0^2 = b kT/H = b sigma_Q^2 in Q-lattice units (Sec. VI-D). The initial psi
+     is the equilibrium of the spring: a Gaussian, or (1 - |Q|^2/Q0^2)^(b/2)
+     (Eq. initail_condition), normalised on the masked grid. */
   double gsum = 0;
   for (int q = 0; q < nq; ++q) {
-    double g = exp(-(st->Qx[q] * st->Qx[q] + st->Qy[q] * st->Qy[q]) / (2.0 * lat->sigma_q2));
+    double q2 = st->Qx[q] * st->Qx[q] + st->Qy[q] * st->Qy[q];
+    double g;
+    if (lat->fene_b > 0) {
+      double s = 1.0 - q2 / (lat->fene_b * lat->sigma_q2);
+      st->phi[q] = 1.0 / s;
+      g = pow(s, 0.5 * lat->fene_b);
+    } else {
+      st->phi[q] = 1.0;
+      g = exp(-q2 / (2.0 * lat->sigma_q2));
+    }
     st->psi0[q] = g;
     gsum += g;
   }
@@ -242,7 +260,7 @@ orc_state* orc_create(const orc_lattice* lat) {
 
 void orc_destroy(orc_state* st) {
   if (!st) return;
-  void* ptrs[] = {st->qmap, st->qgi, st->qgj, st->Qx, st->Qy, st->psi0, st->gs, st->gp,
+  void* ptrs[] = {st->qmap, st->qgi, st->qgj, st->Qx, st->Qy, st->psi0, st->phi, st->gs, st->gp,
                   st->gs_post, st->gp_post, st->rho_s, st->jsx, st->jsy, st->psi, st->jr,
                   st->jq, st->dq, st->psitot, st->jpx, st->jpy, st->ex, st->ey, st->ux,
                   st->uy, st->gux, st->guy};
@@ -370,7 +388,8 @@ static void macro(orc_state* st) {
      F(Q) [(Q . grad_r) psi2]. reading: the lattice psi counts beads, psi = 2 psi2
      to this order, so D(r,q) = (1/2) F(Q) [(Q . grad_r) psi]; this keeps the
      density equation of Appendix A (centre-of-mass diffusivity kT/(2 zeta)).
-     F = H Q (Hookean), both in r-lengths: Q_phys = ell Q. Central differences
+     F = H phi_q Q (phi_q = 1 Hookean, 1/(1 - Q^2/Q0^2) FENE), both in r-lengths:
+     Q_phys = ell Q. Central differences
      (reading: stencil unspecified). */
 #pragma omp parallel for schedule(static)
   for (int y = 0; y < ny; ++y)
@@ -383,8 +402,8 @@ static void macro(orc_state* st) {
         double dpx = 0.5 * (st->psi[nxp * nq + q] - st->psi[nxm * nq + q]);
         double dpy = 0.5 * (st->psi[nyp * nq + q] - st->psi[nym * nq + q]);
         double qgrad = st->Qx[q] * dpx + st->Qy[q] * dpy;
-        double dx = Hl2h * st->Qx[q] * qgrad;
-        double dy = Hl2h * st->Qy[q] * qgrad;
+        double dx = Hl2h * st->phi[q] * st->Qx[q] * qgrad;
+        double dy = Hl2h * st->phi[q] * st->Qy[q] * qgrad;
         st->dq[(n * nq + q) * 2] = dx;
         st->dq[(n * nq + q) * 2 + 1] = dy;
         ex += dx;
@@ -476,8 +495,8 @@ void orc_collide(orc_state* st) {
         double jrey = psi * Uy + tau2 * st->dq[nqq * 2 + 1];
         /* J^Q_eq = psi (Q . grad U) - psi 2F/zeta; in Q lattice units the
            spacing ell cancels and 2F/zeta = kappa Q with kappa = 2 H tau2. */
-        double jqex = psi * (Qx * G00 + Qy * G10 - kappa * Qx);
-        double jqey = psi * (Qx * G01 + Qy * G11 - kappa * Qy);
+        double jqex = psi * (Qx * G00 + Qy * G10 - kappa * st->phi[q] * Qx);
+        double jqey = psi * (Qx * G01 + Qy * G11 - kappa * st->phi[q] * Qy);
         double jrfx = (c2 * st->jr[nqq * 2] + jrex) / (c2 + 1.0);
         double jrfy = (c2 * st->jr[nqq * 2 + 1] + jrey) / (c2 + 1.0);
         double jqfx = (c2 * st->jq[nqq * 2] + jqex) / (c2 + 1.0);
@@ -570,8 +589,8 @@ void orc_init(orc_state* st, const double* perturb, int32_t ic_mode) {
         double psi = st->psi0[q];
         double Qx = st->Qx[q], Qy = st->Qy[q];
         double jrx = psi * Ux, jry = psi * Uy;
-        double jqx = psi * (Qx * G00 + Qy * G10 - st->L.kappa * Qx);
-        double jqy = psi * (Qx * G01 + Qy * G11 - st->L.kappa * Qy);
+        double jqx = psi * (Qx * G00 + Qy * G10 - st->L.kappa * st->phi[q] * Qx);
+        double jqy = psi * (Qx * G01 + Qy * G11 - st->L.kappa * st->phi[q] * Qy);
         for (int i = 0; i < 25; ++i)
           st->gp[(n * nq + q) * 25 + i] = feq_polymer(st->wp[i], psi, st->cp[i], jrx, jry, jqx, jqy);
       }
@@ -582,20 +601,23 @@ void orc_init(orc_state* st, const double* perturb, int32_t ic_mode) {
 
 /* Fields of the current g (Sec. VII diagnostics): rho_S, psi_tot, U; the
    conformation C = ell^2 sum_q psi Q Q / psi_tot (r-lengths); the elastic
-   stress Theta = (H ell^2 / 2) sum_q psi Q Q (Sec. III, Eq. IDef for Hookean
-   springs, psi counting beads); Q_rms = sqrt(<psi Q^2> / <psi>); vorticity d_x U_y - d_y U_x. */
+   stress Theta = (ell^2 / 2) sum_q psi Q F(Q) (Sec. III, Eq. IDef; (H ell^2 / 2)
+   sum_q phi_q psi Q Q with the spring factor phi_q, psi counting beads); Q_rms = sqrt(<psi Q^2> / <psi>); vorticity d_x U_y - d_y U_x. */
 void orc_fields(orc_state* st, double* out, double* psi_out, double* e_out) {
   macro(st);
   const int nx = st->nx, ny = st->ny, nq = st->nq;
   size_t N = (size_t)nx * ny;
   const double l2 = st->L.ell * st->L.ell, H = st->L.H;
   for (size_t n = 0; n < N; ++n) {
-    double sxx = 0, sxy = 0, syy = 0;
+    double sxx = 0, sxy = 0, syy = 0, fxx = 0, fxy = 0, fyy = 0;
     for (int q = 0; q < nq; ++q) {
       double p = st->psi[n * nq + q];
       sxx += p * st->Qx[q] * st->Qx[q];
       sxy += p * st->Qx[q] * st->Qy[q];
       syy += p * st->Qy[q] * st->Qy[q];
+      fxx += st->phi[q] * p * st->Qx[q] * st->Qx[q];
+      fxy += st->phi[q] * p * st->Qx[q] * st->Qy[q];
+      fyy += st->phi[q] * p * st->Qy[q] * st->Qy[q];
     }
     double pt = st->psitot[n];
     out[ORC_F_RHO_S * N + n] = st->rho_s[n];
@@ -607,9 +629,9 @@ void orc_fields(orc_state* st, double* out, double* psi_out, double* e_out) {
     out[ORC_F_CXX * N + n] = cxx;
     out[ORC_F_CXY * N + n] = cxy;
     out[ORC_F_CYY * N + n] = cyy;
-    out[ORC_F_THXX * N + n] = 0.5 * H * l2 * sxx;
-    out[ORC_F_THXY * N + n] = 0.5 * H * l2 * sxy;
-    out[ORC_F_THYY * N + n] = 0.5 * H * l2 * syy;
+    out[ORC_F_THXX * N + n] = 0.5 * H * l2 * fxx;
+    out[ORC_F_THXY * N + n] = 0.5 * H * l2 * fxy;
+    out[ORC_F_THYY * N + n] = 0.5 * H * l2 * fyy;
     out[ORC_F_QRMS * N + n] = sqrt(cxx + cyy);
     /* d_x U_y - d_y U_x */
     out[ORC_F_VORT * N + n] = st->guy[n * 2] - st->gux[n * 2 + 1];

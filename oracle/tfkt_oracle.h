@@ -32,6 +32,7 @@ typedef struct {
   int32_t k_periods;       /* forcing a0 sin(2 pi k_periods y / ny) */
   double tau2;             /* momentum relaxation time; <= 0 -> tau2 = tau1 */
   double ell;              /* Q-lattice spacing in r-lengths; <= 0 -> sqrt(2) */
+  double fene_b;           /* FENE extensibility b in units of kT/H; 0 -> Hookean */
 } orc_phys;
 
 /* Lattice-unit parameters used by the step. */
@@ -48,6 +49,7 @@ typedef struct {
   double kf;               /* forcing wavenumber 2 pi k_periods / ny */
   double u0;               /* laminar amplitude (initial condition, mode 1) */
   double nu, nu_s, eta_p, lambda_h; /* reported, not used by the step */
+  double fene_b;           /* FENE b (units of kT/H); 0 -> Hookean springs */
 } orc_lattice;
 
 typedef struct orc_state orc_state;
