@@ -383,7 +383,8 @@ def main():
             "config": {"workload": W.name, "nx": W.nx, "ny": W.ny, "nq": info["nq"],
                        "re": W.re, "wi": W.wi, "beta": W.beta, "k_periods": W.k_periods,
                        "storage": "fp32 deviations from rest",
-                       "l2": "inputs larger than L2 (populations 54 GB per buffer)",
+                       "l2": f"inputs larger than L2 (populations {nodes * npl * s / 1e9:.2f} GB "
+                             "per buffer, L2 129 MB)",
                        "parallelism": f"{world} independent runs"},
             "roofline": {"bound": "hbm", "kernel": top + "_kernel", "achieved": ach,
                          "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,

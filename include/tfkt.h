@@ -67,6 +67,14 @@ typedef struct {
   double ell;            /* Q-lattice spacing in r-lengths; <= 0 selects sqrt(2) */
   int32_t ic_mode;       /* 0: start from rest; 1: start from the laminar profile */
   int32_t precision;     /* tfkt_precision */
+  double fene_b;         /* 0: Hookean springs; > 0: FENE springs of extensibility b
+                            (Sec. VI-D), force H Q / (1 - Q^2/Q0^2) with Q0^2 = b kT/H;
+                            every Q-node must lie inside Q0 (q_radius^2 < b sigma_q2,
+                            else EINVAL). The drift of a Q-node grows as 1/(1 - Q^2/Q0^2):
+                            nodes where kappa |Q| / (1 - Q^2/Q0^2) exceeds about 1, or
+                            where the bead-force flux makes the node strongly
+                            anti-diffusive in r, make the step unstable; keep the disk
+                            well inside Q0. */
 } tfkt_params;
 
 /* Derived lattice parameters and layout of a context. */
@@ -82,6 +90,7 @@ typedef struct {
   size_t workspace_bytes;
   size_t pitch;          /* elements per stored row (>= nx, multiple of 32) */
   size_t bytes_per_node_step; /* algorithmic HBM bytes of one node update, fused model */
+  double fene_b;         /* 0 for Hookean springs */
 } tfkt_info;
 
 typedef struct tfkt_ctx tfkt_ctx;
@@ -102,7 +111,7 @@ enum {
   TFKT_F_PSI_TOT,     /* sum_q psi */
   TFKT_F_UX, TFKT_F_UY,          /* mixture velocity U of f (Sec. VI-C) */
   TFKT_F_CXX, TFKT_F_CXY, TFKT_F_CYY,   /* conformation ell^2 sum psi QQ / psi_tot */
-  TFKT_F_THXX, TFKT_F_THXY, TFKT_F_THYY, /* stress (H ell^2 / 2) sum psi QQ */
+  TFKT_F_THXX, TFKT_F_THXY, TFKT_F_THYY, /* stress (ell^2 / 2) sum psi Q F(Q) */
   TFKT_F_QRMS,        /* sqrt(<psi Q^2> / <psi>) in r-lengths (Sec. VII) */
   TFKT_F_VORT,        /* d_x U_y - d_y U_x, central differences */
   TFKT_NFIELDS
@@ -118,8 +127,9 @@ enum {
    buffers, the moment fields, scratch). EINVAL for invalid parameters. */
 tfkt_status tfkt_required_bytes(const tfkt_params* p, size_t* bytes);
 
-/* Create a context and its initial state (Sec. VI-D initial condition with
-   Hookean dumbbells: psi is the discretely normalised Gaussian in Q, g = f^eq).
+/* Create a context and its initial state (Sec. VI-D initial condition: psi is
+   the equilibrium of the spring, the Gaussian for Hookean dumbbells or
+   (1 - Q^2/Q0^2)^(b/2) for FENE ones, discretely normalised; g = f^eq).
    perturb: host array [2][ny][nx] of the initial velocity perturbation
             (u'_x plane then u'_y plane), or NULL; copied during the call.
    dev_workspace: device memory of at least tfkt_required_bytes bytes, owned

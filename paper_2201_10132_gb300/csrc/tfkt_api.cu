@@ -40,7 +40,9 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 // zeta = m_B / tau2 (Appendix A), Q-drift 2 H / zeta = kappa, Q spacing
 // ell = sqrt(2) from the Q-diffusivity 2 kT / zeta of Eq. Smoluchowski_new11,
 // and psi_tot from eta_p = (H ell^2 / 2) psi_tot sigma_Q^2 lambda_H
-// (psi counts beads).
+// (psi counts beads). FENE springs keep this mapping (H, lambda_H and the
+// stress scale n kT lambda_H of the Hookean dumbbell of the same H) and add
+// Q0^2 = b kT/H = b sigma_Q^2, inside which every Q-node must lie.
 tfkt_status map_params(const tfkt_params* p, Lattice* L) {
   if (!p) return fail(TFKT_EINVAL, "params is NULL");
   if (p->nx < 1 || p->ny < 1) return fail(TFKT_EINVAL, "nx and ny must be >= 1");
@@ -55,6 +57,7 @@ tfkt_status map_params(const tfkt_params* p, Lattice* L) {
   if (p->precision != TFKT_FP64 && p->precision != TFKT_FP32 && p->precision != TFKT_FP16)
     return fail(TFKT_EINVAL, "unknown precision");
   if (p->ic_mode != 0 && p->ic_mode != 1) return fail(TFKT_EINVAL, "ic_mode must be 0 or 1");
+  if (!(p->fene_b >= 0)) return fail(TFKT_EINVAL, "fene_b must be >= 0 (0: Hookean)");
   Lattice l;
   l.nx = p->nx;
   l.ny = p->ny;
@@ -62,6 +65,7 @@ tfkt_status map_params(const tfkt_params* p, Lattice* L) {
   l.q_radius = p->q_radius;
   l.ic_mode = p->ic_mode;
   l.precision = p->precision;
+  l.fene_b = p->fene_b;
   const double kf = 2.0 * M_PI * p->k_periods / p->ny;
   const double len = 1.0 / kf;
   l.kf = kf;
@@ -96,6 +100,8 @@ tfkt_status map_params(const tfkt_params* p, Lattice* L) {
       if (qx * qx + qy * qy <= R2) ++nq;
     }
   if (nq < 1) return fail(TFKT_EINVAL, "the Q-disk holds no node");
+  if (l.fene_b > 0 && p->q_radius * p->q_radius >= l.fene_b * l.sigma_q2)
+    return fail(TFKT_EINVAL, "FENE: q_radius must be < Q0 = sqrt(fene_b sigma_q2)");
   l.nq = nq;
   l.pitch = align_up((size_t)l.nx, 32);
   l.plane = (size_t)l.ny * l.pitch;
@@ -140,8 +146,8 @@ size_t layout(const Lattice& L, Workspace* w) {
   w->off_U = o;
   o = align_up(o + 2 * L.plane * sz, A);
   w->off_tab = o;
-  const size_t tab = (3 * (size_t)L.nq + 25 * (size_t)L.nq + 2 * (size_t)L.ny) * sz +
-                     25 * (size_t)L.nq * sizeof(int) + 8 * A;
+  const size_t tab = (5 * (size_t)L.nq + 25 * (size_t)L.nq + 2 * (size_t)L.ny) * sz +
+                     25 * (size_t)L.nq * sizeof(int) + 10 * A;
   o = align_up(o + tab, A);
   w->off_part = o;
   o = align_up(o + (size_t)diag_blocks_for(L) * TFKT_NDIAG * sizeof(double), A);
@@ -168,7 +174,8 @@ int opposite25(int i) {
 }
 
 // Q-nodes (cell-centred S x S grid inside the disk |Q| <= R, Sec. VI-D),
-// the initial Gaussian psi0(q) (Hookean equilibrium, normalised on the
+// the spring force per unit H, phi_q Q, the initial psi0(q) (the spring's
+// equilibrium: Gaussian, or (1 - Q^2/Q0^2)^(b/2) for FENE, normalised on the
 // masked grid to psi_tot), the pull table with bounce-back at the disk edge,
 // the forcing a(y) = a0 sin(kf y) (Sec. VII) and the initial base flow.
 HostTables build_tables(const Lattice& L) {
@@ -188,7 +195,18 @@ HostTables build_tables(const Lattice& L) {
     }
   double gsum = 0;
   for (int q = 0; q < L.nq; ++q) {
-    const double g = std::exp(-(t.qx[q] * t.qx[q] + t.qy[q] * t.qy[q]) / (2.0 * L.sigma_q2));
+    const double q2 = t.qx[q] * t.qx[q] + t.qy[q] * t.qy[q];
+    double g, phi;
+    if (L.fene_b > 0) {
+      const double u = 1.0 - q2 / (L.fene_b * L.sigma_q2);
+      phi = 1.0 / u;
+      g = std::pow(u, 0.5 * L.fene_b);
+    } else {
+      phi = 1.0;
+      g = std::exp(-q2 / (2.0 * L.sigma_q2));
+    }
+    t.fx.push_back(L.fene_b > 0 ? phi * t.qx[q] : t.qx[q]);
+    t.fy.push_back(L.fene_b > 0 ? phi * t.qy[q] : t.qy[q]);
     t.psi0.push_back(g);
     gsum += g;
   }
@@ -260,6 +278,8 @@ KernelArgs<real> make_args(const Ctx* c, const HostTables* ht = nullptr) {
   const size_t nq = L.nq;
   a.tab.qx = (const real*)take(nq * sizeof(real));
   a.tab.qy = (const real*)take(nq * sizeof(real));
+  a.tab.fx = (const real*)take(nq * sizeof(real));
+  a.tab.fy = (const real*)take(nq * sizeof(real));
   a.tab.psi0 = (const real*)take(nq * sizeof(real));
   a.tab.pull = (const int*)take(nq * 25 * sizeof(int));
   a.tab.delta = (const real*)take(nq * 25 * sizeof(real));
@@ -311,6 +331,8 @@ tfkt_status upload_tables(Ctx* c, const HostTables& t) {
   };
   TFKT_CUDA(c, put(a.tab.qx, t.qx));
   TFKT_CUDA(c, put(a.tab.qy, t.qy));
+  TFKT_CUDA(c, put(a.tab.fx, t.fx));
+  TFKT_CUDA(c, put(a.tab.fy, t.fy));
   TFKT_CUDA(c, put(a.tab.psi0, t.psi0));
   TFKT_CUDA(c, cudaMemcpy((void*)a.tab.pull, t.pull.data(), t.pull.size() * sizeof(int),
                           cudaMemcpyHostToDevice));
@@ -668,6 +690,7 @@ tfkt_status tfkt_get_info(const tfkt_ctx* c, tfkt_info* info) {
   i.nu_s = L.nu_s;
   i.eta_p = L.eta_p;
   i.lambda_h = L.lambda_h;
+  i.fene_b = L.fene_b;
   i.step = c->step;
   i.workspace_bytes = c->ws.bytes;
   i.pitch = L.pitch;

@@ -368,13 +368,13 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
       acc<c25(i).qx>(qx, h[i]);
       acc<c25(i).qy>(qy, h[i]);
     });
-    const real Qx = a.tab.qx[q], Qy = a.tab.qy[q];
+    const real Qx = a.tab.qx[q], Qy = a.tab.qy[q], Fx = a.tab.fx[q], Fy = a.tab.fy[q];
     const real psi = a.tab.psi0[q] + dpsi;
     const real qg = Qx * dpx + Qy * dpy;
-    const real jrex = psi * Ux + a.tau2 * a.hl2h * Qx * qg;
-    const real jrey = psi * Uy + a.tau2 * a.hl2h * Qy * qg;
-    const real jqex = psi * (Qx * G00 + Qy * G10 - a.kappa * Qx);
-    const real jqey = psi * (Qx * G01 + Qy * G11 - a.kappa * Qy);
+    const real jrex = psi * Ux + a.tau2 * a.hl2h * Fx * qg;
+    const real jrey = psi * Uy + a.tau2 * a.hl2h * Fy * qg;
+    const real jqex = psi * (Qx * G00 + Qy * G10 - a.kappa * Fx);
+    const real jqey = psi * (Qx * G01 + Qy * G11 - a.kappa * Fy);
     // 3 x the momenta of the mixed equilibrium (1 - r) f* + r f^eq
     const real mrx = real(3) * (a.omr * (a.c2 * rx + jrex) * a.inv_c2p1 + a.r * jrex);
     const real mry = real(3) * (a.omr * (a.c2 * ry + jrey) * a.inv_c2p1 + a.r * jrey);
@@ -456,10 +456,10 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
       const real d = sm.A[p * NT + tid] + fa.dpsi[p];
       Mout[(size_t)p * P + n] = d;
       drho += d;
-      const real Qx = a.tab.qx[p], Qy = a.tab.qy[p];
-      txx += d * Qx * Qx;
-      txy += d * Qx * Qy;
-      tyy += d * Qy * Qy;
+      const real Qx = a.tab.qx[p], Qy = a.tab.qy[p], Fx = a.tab.fx[p], Fy = a.tab.fy[p];
+      txx += d * Fx * Qx;
+      txy += d * Fx * Qy;
+      tyy += d * Fy * Qy;
     }
     Mout[(size_t)(nq + M_DRHO) * P + n] = drho;
     Mout[(size_t)(nq + M_JX) * P + n] = jx_arr + fa.dvx;
@@ -555,10 +555,10 @@ __device__ __forceinline__ void fixup_body(const KernelArgs<real>& a, const Fuse
       if (p < nq) {
         M[(size_t)p * P + n] = d[u];
         drho += d[u];
-        const real Qx = a.tab.qx[p], Qy = a.tab.qy[p];
-        txx += d[u] * Qx * Qx;
-        txy += d[u] * Qx * Qy;
-        tyy += d[u] * Qy * Qy;
+        const real Qx = a.tab.qx[p], Qy = a.tab.qy[p], Fx = a.tab.fx[p], Fy = a.tab.fy[p];
+        txx += d[u] * Fx * Qx;
+        txy += d[u] * Fx * Qy;
+        tyy += d[u] * Fy * Qy;
       }
     }
   }

@@ -63,6 +63,7 @@ struct Lattice {
   double tau1 = 0, tau2 = 0, H = 0, kappa = 0, ell = 0, psi_tot = 0, sigma_q2 = 0;
   double a0 = 0, kf = 0, u0 = 0, nu = 0, nu_s = 0, eta_p = 0, lambda_h = 0;
   int ic_mode = 0, precision = 0;
+  double fene_b = 0;  // 0: Hookean springs; > 0: FENE extensibility b
   size_t pitch = 0;   // elements per stored row
   size_t plane = 0;   // elements per plane (ny * pitch)
   int npl = 0;        // population planes: 9 + 25 nq
@@ -77,6 +78,8 @@ template <typename real>
 struct Tables {
   const real* qx;        // [nq] Q_x (Q lattice units)
   const real* qy;        // [nq]
+  const real* fx;        // [nq] phi_q Q_x: spring force / H (phi_q = 1 Hookean,
+  const real* fy;        //      1 / (1 - Q^2/Q0^2) FENE); equal to Q bit for bit when Hookean
   const real* psi0;      // [nq] storage shift of the polymer: w_i psi0(q)
   const int* pull;       // [nq*25]: >= 0 source plane (shifted by -c_r); < 0: ~plane, bounce-back
   const real* delta;     // [nq*25]: w_i (psi0(q - Qdot_i) - psi0(q)), 0 for bounce-back
@@ -113,7 +116,6 @@ struct KernelArgs {
   real r, omr;                   // tau1 / tau2, 1 - tau1 / tau2
   real kappa, hl2h;              // kappa, H ell^2 / 2
   real rho0;                     // 1 + psi_tot: total density of the rest state
-  real theta0[3];                // (H ell^2 / 2) sum_q psi0 Q Q
   real psi_tot0;
   real l2, H;
   real pscale, pinv;             // polymer storage scale (a power of two) and its inverse
@@ -175,7 +177,7 @@ size_t store_size(const Lattice& L);  // bytes of the population storage type
 // bits instead of falling into the subnormal range); 1 for FP32 and FP64.
 double polymer_scale(const Lattice& L);
 struct HostTables {
-  std::vector<double> qx, qy, psi0, delta, arow, urow;
+  std::vector<double> qx, qy, fx, fy, psi0, delta, arow, urow;
   std::vector<int> pull;
 };
 HostTables build_tables(const Lattice& L);

@@ -10,7 +10,7 @@
 //
 // Moment planes M: delta psi(q) (q < nq), then delta rho (total), J_x, J_y
 // (total momentum of g), and delta Theta_xx, xy, yy = (H ell^2 / 2) sum_q
-// delta psi Q Q, all of the pulled (pre-collision) state.
+// delta psi phi_q Q Q, all of the pulled (pre-collision) state.
 #include "tfkt_internal.cuh"
 
 namespace tfkt {
@@ -103,9 +103,10 @@ __global__ void __launch_bounds__(256) init_kernel(KernelArgs<real> a) {
   }
   for (int q = 0; q < a.nq; ++q) {
     const real Qx = a.tab.qx[q], Qy = a.tab.qy[q], psi = a.tab.psi0[q];
+    const real Fx = a.tab.fx[q], Fy = a.tab.fy[q];
     const real jrx = psi * ux, jry = psi * uy;
-    const real jqx = psi * (Qx * G00 + Qy * G10 - a.kappa * Qx);
-    const real jqy = psi * (Qx * G01 + Qy * G11 - a.kappa * Qy);
+    const real jqx = psi * (Qx * G00 + Qy * G10 - a.kappa * Fx);
+    const real jqy = psi * (Qx * G01 + Qy * G11 - a.kappa * Fy);
 #pragma unroll
     for (int i = 0; i < 25; ++i) {
       const V4 c = c25(i);
@@ -121,7 +122,8 @@ __global__ void __launch_bounds__(256) init_kernel(KernelArgs<real> a) {
 
 // --------------------------------------------------------------- moments
 // Pull-read every population of node (x, y) and write its moments to M
-// (Sec. VI-A / VI-B moment definitions; Theta of Sec. III for Hookean springs).
+// (Sec. VI-A / VI-B moment definitions; Theta of Sec. III, Eq. IDef, with the
+// spring force H phi_q Q).
 template <typename real, typename S>
 __global__ void __launch_bounds__(256) moments_kernel(KernelArgs<real> a) {
   const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
@@ -156,10 +158,10 @@ __global__ void __launch_bounds__(256) moments_kernel(KernelArgs<real> a) {
     drho += dpsi;
     jx += rx;
     jy += ry;
-    const real Qx = a.tab.qx[q], Qy = a.tab.qy[q];
-    txx += dpsi * Qx * Qx;
-    txy += dpsi * Qx * Qy;
-    tyy += dpsi * Qy * Qy;
+    const real Qx = a.tab.qx[q], Qy = a.tab.qy[q], Fx = a.tab.fx[q], Fy = a.tab.fy[q];
+    txx += dpsi * Fx * Qx;
+    txy += dpsi * Fx * Qy;
+    tyy += dpsi * Fy * Qy;
   }
   const int nq = a.nq;
   a.M[(size_t)(nq + M_DRHO) * P + n] = drho;
@@ -175,7 +177,8 @@ __global__ void __launch_bounds__(256) moments_kernel(KernelArgs<real> a) {
 //   U from M (tile + 1-node halo in shared memory), grad U by central
 //   differences; solvent J_S(f) = (2 tau2 J_S(g) + rho_S U + tau2 rho a) /
 //   (2 tau2 + 1), u_S = J_S(f) / rho_S; polymer J^r_eq = psi U + tau2 D,
-//   D = (H ell^2 / 2) Q (Q . grad_r psi), J^Q_eq = psi (Q . grad U - kappa Q),
+//   D = (H ell^2 / 2) phi_q Q (Q . grad_r psi), J^Q_eq = psi (Q . grad U - kappa phi_q Q)
+//   (phi_q Q = spring force / H: phi_q = 1 Hookean, 1 / (1 - Q^2/Q0^2) FENE),
 //   J(f) = (2 tau2 J(g) + J_eq) / (2 tau2 + 1);
 //   g' = (1 - 2 beta) g + 2 beta [(1 - tau1/tau2) f* + (tau1/tau2) f^eq]
 //        + (1 - beta) S_i,   beta = 1 / (2 tau1 + 1)
@@ -265,13 +268,13 @@ __global__ void __launch_bounds__(256) step_kernel(KernelArgs<real> a) {
       qx += real(c.qx) * h[i];
       qy += real(c.qy) * h[i];
     }
-    const real Qx = a.tab.qx[q], Qy = a.tab.qy[q];
+    const real Qx = a.tab.qx[q], Qy = a.tab.qy[q], Fx = a.tab.fx[q], Fy = a.tab.fy[q];
     const real psi = a.tab.psi0[q] + dpsi;
     const real qg = Qx * dpx + Qy * dpy;
-    const real jrex = psi * Ux + a.tau2 * a.hl2h * Qx * qg;
-    const real jrey = psi * Uy + a.tau2 * a.hl2h * Qy * qg;
-    const real jqex = psi * (Qx * G00 + Qy * G10 - a.kappa * Qx);
-    const real jqey = psi * (Qx * G01 + Qy * G11 - a.kappa * Qy);
+    const real jrex = psi * Ux + a.tau2 * a.hl2h * Fx * qg;
+    const real jrey = psi * Uy + a.tau2 * a.hl2h * Fy * qg;
+    const real jqex = psi * (Qx * G00 + Qy * G10 - a.kappa * Fx);
+    const real jqey = psi * (Qx * G01 + Qy * G11 - a.kappa * Fy);
     // mixture (1 - r) J(f) + r J_eq of the two equilibria's momenta
     const real mrx = a.omr * (a.c2 * rx + jrex) * a.inv_c2p1 + a.r * jrex;
     const real mry = a.omr * (a.c2 * ry + jrey) * a.inv_c2p1 + a.r * jrey;
@@ -306,14 +309,17 @@ __device__ void node_fields(const KernelArgs<real>& a, int x, int y, double f[TF
   const size_t P = a.plane;
   const size_t n = (size_t)y * a.pitch + x;
   const int nq = a.nq;
-  double pt = 0, sxx = 0, sxy = 0, syy = 0;
+  double pt = 0, sxx = 0, sxy = 0, syy = 0, fxx = 0, fxy = 0, fyy = 0;
   for (int q = 0; q < nq; ++q) {
     const double p = double(a.tab.psi0[q]) + double(a.M[(size_t)q * P + n]);
-    const double Qx = a.tab.qx[q], Qy = a.tab.qy[q];
+    const double Qx = a.tab.qx[q], Qy = a.tab.qy[q], Fx = a.tab.fx[q], Fy = a.tab.fy[q];
     pt += p;
     sxx += p * Qx * Qx;
     sxy += p * Qx * Qy;
     syy += p * Qy * Qy;
+    fxx += p * Fx * Qx;
+    fxy += p * Fx * Qy;
+    fyy += p * Fy * Qy;
   }
   const double rho = double(a.rho0) + double(a.M[(size_t)(nq + M_DRHO) * P + n]);
   const double l2 = a.l2, hh = 0.5 * double(a.H) * l2;
@@ -326,9 +332,9 @@ __device__ void node_fields(const KernelArgs<real>& a, int x, int y, double f[TF
   f[TFKT_F_CXX] = cxx;
   f[TFKT_F_CXY] = cxy;
   f[TFKT_F_CYY] = cyy;
-  f[TFKT_F_THXX] = hh * sxx;
-  f[TFKT_F_THXY] = hh * sxy;
-  f[TFKT_F_THYY] = hh * syy;
+  f[TFKT_F_THXX] = hh * fxx;
+  f[TFKT_F_THXY] = hh * fxy;
+  f[TFKT_F_THYY] = hh * fyy;
   f[TFKT_F_QRMS] = sqrt(cxx + cyy);
   const int xm = x == 0 ? a.nx - 1 : x - 1, xp = x == a.nx - 1 ? 0 : x + 1;
   const int ym = y == 0 ? a.ny - 1 : y - 1, yp = y == a.ny - 1 ? 0 : y + 1;

@@ -51,10 +51,11 @@ tfkt_status moments_noalloc(const Lattice& L, const void* pops, uint32_t mask, d
   o = align_up(o + (size_t)L.nm * L.plane * sz, A);
   const size_t off_U = o;
   o = align_up(o + 2 * L.plane * sz, A);
-  size_t off_t[7];
-  const size_t tsz[7] = {nq * sz, nq * sz, nq * sz, nq * 25 * sizeof(int), nq * 25 * sz,
-                         (size_t)L.ny * sz, (size_t)L.ny * sz};
-  for (int k = 0; k < 7; ++k) {
+  constexpr int NT = 9, KPULL = 5;
+  size_t off_t[NT];
+  const size_t tsz[NT] = {nq * sz, nq * sz, nq * sz, nq * sz, nq * sz, nq * 25 * sizeof(int),
+                          nq * 25 * sz, (size_t)L.ny * sz, (size_t)L.ny * sz};
+  for (int k = 0; k < NT; ++k) {
     off_t[k] = o;
     o = align_up(o + tsz[k], A);
   }
@@ -69,11 +70,12 @@ tfkt_status moments_noalloc(const Lattice& L, const void* pops, uint32_t mask, d
 
   // lattice tables into the scratch (each call rewrites all of them)
   const HostTables t = build_tables(L);
-  const std::vector<double>* src[7] = {&t.qx, &t.qy, &t.psi0, nullptr, &t.delta, &t.arow, &t.urow};
-  std::vector<real> conv[7];
-  for (int k = 0; k < 7; ++k) {
+  const std::vector<double>* src[NT] = {&t.qx,    &t.qy,    &t.fx,   &t.fy,  &t.psi0,
+                                        nullptr, &t.delta, &t.arow, &t.urow};
+  std::vector<real> conv[NT];
+  for (int k = 0; k < NT; ++k) {
     cudaError_t e;
-    if (k == 3) {
+    if (k == KPULL) {
       e = cudaMemcpyAsync(b + off_t[k], t.pull.data(), tsz[k], cudaMemcpyHostToDevice, stream);
     } else {
       conv[k].assign(src[k]->begin(), src[k]->end());
@@ -107,11 +109,13 @@ tfkt_status moments_noalloc(const Lattice& L, const void* pops, uint32_t mask, d
   a.pinv = (real)(1.0 / polymer_scale(L));
   a.tab.qx = (const real*)(b + off_t[0]);
   a.tab.qy = (const real*)(b + off_t[1]);
-  a.tab.psi0 = (const real*)(b + off_t[2]);
-  a.tab.pull = (const int*)(b + off_t[3]);
-  a.tab.delta = (const real*)(b + off_t[4]);
-  a.tab.arow = (const real*)(b + off_t[5]);
-  a.tab.urow = (const real*)(b + off_t[6]);
+  a.tab.fx = (const real*)(b + off_t[2]);
+  a.tab.fy = (const real*)(b + off_t[3]);
+  a.tab.psi0 = (const real*)(b + off_t[4]);
+  a.tab.pull = (const int*)(b + off_t[5]);
+  a.tab.delta = (const real*)(b + off_t[6]);
+  a.tab.arow = (const real*)(b + off_t[7]);
+  a.tab.urow = (const real*)(b + off_t[8]);
   // every scratch value read below is written first by these kernels: the
   // moments kernel writes all M planes of every node, the velocity kernel both
   // U planes of every node, so nothing needs clearing between calls

@@ -36,7 +36,7 @@ class _Params(ctypes.Structure):
                 ("beta", ctypes.c_double), ("u0", ctypes.c_double),
                 ("k_periods", ctypes.c_int32), ("tau2", ctypes.c_double),
                 ("ell", ctypes.c_double), ("ic_mode", ctypes.c_int32),
-                ("precision", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("fene_b", ctypes.c_double)]
 
 
 class _Info(ctypes.Structure):
@@ -48,7 +48,7 @@ class _Info(ctypes.Structure):
                 ("nu", ctypes.c_double), ("nu_s", ctypes.c_double), ("eta_p", ctypes.c_double),
                 ("lambda_h", ctypes.c_double), ("step", ctypes.c_int64),
                 ("workspace_bytes", ctypes.c_size_t), ("pitch", ctypes.c_size_t),
-                ("bytes_per_node_step", ctypes.c_size_t)]
+                ("bytes_per_node_step", ctypes.c_size_t), ("fene_b", ctypes.c_double)]
 
 
 @dataclass
@@ -67,6 +67,7 @@ class Params:
     ell: float = 0.0
     ic_mode: int = 0
     precision: int = FP64
+    fene_b: float = 0.0     # 0: Hookean springs; > 0: FENE extensibility b
 
     def _c(self) -> _Params:
         return _Params(*(getattr(self, f.name) for f in dc_fields(self)))

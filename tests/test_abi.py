@@ -50,10 +50,21 @@ def test_required_bytes_matches_layout(T):
 @pytest.mark.parametrize("kw", [dict(beta=0.0), dict(beta=1.5), dict(re=0.0), dict(u0=0.5),
                                 dict(wi=0.0), dict(tau2=1e-4), dict(q_radius=0.0), dict(nx=0),
                                 dict(q_side=65), dict(precision=7), dict(ic_mode=3),
-                                dict(q_radius=0.1, q_side=2)])
+                                dict(q_radius=0.1, q_side=2), dict(fene_b=-1.0),
+                                dict(fene_b=25.0)])  # the disk reaches past Q0
 def test_invalid_parameters(T, kw):
     args = dict(nx=8, ny=8, q_side=4, q_radius=2.0, re=5.0, wi=0.5, beta=0.2)
     args.update(kw)
     with pytest.raises(T.TfktError) as e:
         T.required_bytes(T.Params(**args))
     assert e.value.status == 1  # TFKT_EINVAL
+
+
+def test_fene_disk_inside_q0_is_accepted(T, oracle_mod):
+    """The library's FENE bound on the disk is the oracle's (R < Q0 = sqrt(b sigma_Q^2))."""
+    lat = oracle_mod.map_params(64, 64, 8, 4.0, 5.0, 0.5, 0.2, 0.05, 1, fene_b=25.0)
+    q0 = (25.0 * lat.sigma_q2) ** 0.5
+    T.required_bytes(T.Params(64, 64, 8, 4.0, 5.0, 0.5, 0.2, fene_b=25.0))
+    T.required_bytes(T.Params(64, 64, 8, 0.999 * q0, 5.0, 0.5, 0.2, fene_b=25.0))
+    with pytest.raises(T.TfktError):
+        T.required_bytes(T.Params(64, 64, 8, 1.001 * q0, 5.0, 0.5, 0.2, fene_b=25.0))

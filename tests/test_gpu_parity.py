@@ -31,8 +31,8 @@ def T():
     return tfkt
 
 
-def _oracle_run(O, nx, ny, S, R, re, wi, beta, kp, tau2, pert, ic, steps):
-    lat = O.map_params(nx, ny, S, R, re, wi, beta, 0.05, kp, tau2)
+def _oracle_run(O, nx, ny, S, R, re, wi, beta, kp, tau2, pert, ic, steps, fene_b=0.0):
+    lat = O.map_params(nx, ny, S, R, re, wi, beta, 0.05, kp, tau2, 0.0, fene_b)
     o = O.Oracle(lat)
     o.init(pert, ic)
     o.step(steps)
@@ -59,16 +59,28 @@ CASES = [
     (96, 16, 6, 3.0, 4.0, 1.0, 0.5, 2, 0.3, 1, 15),      # tau2 > tau1
     (64, 16, 4, 2.0, 3.0, 0.0, 1.0, 1, 0.0, 1, 10),      # Newtonian
     (32, 16, 2, 1.0, 5.0, 0.5, 0.2, 1, 0.0, 1, 9),       # every Q-move bounces
+    # FENE springs (last entry b): disks at ~0.85 Q0 and R ~ 1.5-2.5 sigma_Q, spring
+    # factor up to ~3 at the edge. (A disk of R = 6.6 sigma_Q with b = 60 is
+    # ill-conditioned at this tolerance: one ulp of b moves Theta_xx by 8e-13.)
+    (70, 19, 8, 4.0, 5.0, 4.0, 0.2, 1, 0.0, 0, 12, 7.5),     # two-pass path, ragged
+    (64, 32, 6, 3.0, 5.0, 2.0, 0.2, 1, 0.0, 1, 12, 3.1),     # fused path
+    (64, 32, 6, 3.0, 5.0, 2.0, 0.5, 1, 0.3, 1, 12, 3.1),     # fused, tau2 > tau1
 ]
 FUSED = [c for c in CASES if c[0] % 32 == 0 and c[1] % 8 == 0]
+FENE = [c for c in CASES if len(c) > 11]
 
 
-@pytest.mark.parametrize("case", [CASES[2], CASES[7]])
+def _case(case):
+    """(nx, ny, S, R, re, wi, beta, kp, tau2, ic, steps, fene_b)."""
+    return tuple(case) + (0.0,) * (12 - len(case))
+
+
+@pytest.mark.parametrize("case", [CASES[2], CASES[7], FENE[0], FENE[1]])
 def test_path_dispatch(T, case):
     """Tile-multiple grids run the fused kernel plus its border fix-up; others the
     moments + step pair."""
-    nx, ny, S, R, re, wi, beta, kp, tau2, ic, steps = case
-    p = T.Params(nx, ny, S, R, re, wi, beta, 0.05, kp, tau2, 0.0, ic, T.FP64)
+    nx, ny, S, R, re, wi, beta, kp, tau2, ic, steps, fb = _case(case)
+    p = T.Params(nx, ny, S, R, re, wi, beta, 0.05, kp, tau2, 0.0, ic, T.FP64, fb)
     ms = np.zeros(len(T.KERNELS))
     n = np.zeros(len(T.KERNELS), np.int64)
     with T.Solver(p) as s:
@@ -84,10 +96,10 @@ def test_path_dispatch(T, case):
 @pytest.mark.parametrize("case", CASES)
 def test_fp64_matches_oracle(T, oracle_mod, case):
     from paper_2201_10132_gb300.inputs import perturbation
-    nx, ny, S, R, re, wi, beta, kp, tau2, ic, steps = case
+    nx, ny, S, R, re, wi, beta, kp, tau2, ic, steps, fb = _case(case)
     pert = perturbation(nx, ny, 7, 0.05, 0.05) if nx * ny > 1 else None
-    p = T.Params(nx, ny, S, R, re, wi, beta, 0.05, kp, tau2, 0.0, ic, T.FP64)
-    o = _oracle_run(oracle_mod, nx, ny, S, R, re, wi, beta, kp, tau2, pert, ic, steps)
+    p = T.Params(nx, ny, S, R, re, wi, beta, 0.05, kp, tau2, 0.0, ic, T.FP64, fb)
+    o = _oracle_run(oracle_mod, nx, ny, S, R, re, wi, beta, kp, tau2, pert, ic, steps, fb)
     with T.Solver(p, pert) as s:
         assert s.info["nq"] == o.nq
         s.step(steps)
@@ -118,13 +130,13 @@ def test_fp64_matches_oracle(T, oracle_mod, case):
         assert diag[k] == pytest.approx(od[k], rel=1e-9, abs=1e-13 * max(1.0, od["mass_s"])), k
 
 
-@pytest.mark.parametrize("case", [CASES[1], CASES[2], CASES[3], CASES[7], CASES[9]])
+@pytest.mark.parametrize("case", [CASES[1], CASES[2], CASES[3], CASES[7], CASES[9], FENE[1]])
 def test_fp32_within_tolerance(T, oracle_mod, case):
     from paper_2201_10132_gb300.inputs import perturbation
-    nx, ny, S, R, re, wi, beta, kp, tau2, ic, steps = case
+    nx, ny, S, R, re, wi, beta, kp, tau2, ic, steps, fb = _case(case)
     pert = perturbation(nx, ny, 7, 0.05, 0.05)
-    p = T.Params(nx, ny, S, R, re, wi, beta, 0.05, kp, tau2, 0.0, ic, T.FP32)
-    o = _oracle_run(oracle_mod, nx, ny, S, R, re, wi, beta, kp, tau2, pert, ic, steps)
+    p = T.Params(nx, ny, S, R, re, wi, beta, 0.05, kp, tau2, 0.0, ic, T.FP32, fb)
+    o = _oracle_run(oracle_mod, nx, ny, S, R, re, wi, beta, kp, tau2, pert, ic, steps, fb)
     with T.Solver(p, pert) as s:
         s.step(steps)
         g = s.moments()
@@ -145,10 +157,10 @@ def test_fp16_storage_within_tolerance(T, oracle_mod, case):
     (~0.15 w_i) summed over ~25 nq + 9 terms; allowed: 3e-3 of the velocity
     scale and 3e-3 of each other field's largest magnitude for n <= 25."""
     from paper_2201_10132_gb300.inputs import perturbation
-    nx, ny, S, R, re, wi, beta, kp, tau2, ic, steps = case
+    nx, ny, S, R, re, wi, beta, kp, tau2, ic, steps, fb = _case(case)
     pert = perturbation(nx, ny, 7, 0.05, 0.05)
-    p = T.Params(nx, ny, S, R, re, wi, beta, 0.05, kp, tau2, 0.0, ic, T.FP16)
-    o = _oracle_run(oracle_mod, nx, ny, S, R, re, wi, beta, kp, tau2, pert, ic, steps)
+    p = T.Params(nx, ny, S, R, re, wi, beta, 0.05, kp, tau2, 0.0, ic, T.FP16, fb)
+    o = _oracle_run(oracle_mod, nx, ny, S, R, re, wi, beta, kp, tau2, pert, ic, steps, fb)
     with T.Solver(p, pert) as s:
         s.step(steps)
         g = s.moments()
