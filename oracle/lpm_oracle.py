@@ -32,10 +32,13 @@ steps:
     the solvent then collides exactly as in the plain step (two relaxations,
     Guo source of the force rho a).
  6. The polymer populations of t + 1 (pulled) are reshaped at every node so
-    that their conformation is C_new: psi(q) changes by dpsi = psi (f(q) - 1),
-    f(q) = 1 + sum_ab beta_ab (Q_a Q_b - m_ab), m the node's current second
-    moments, the three beta from the linear system that makes the new second
-    moments equal C_new / ell^2 (psi_tot is unchanged); dpsi enters as the
+    that their conformation is C_new: psi(q) changes by dpsi(q) = psi_tot p0(q)
+    sum_ab w_ab beta_ab (Q_a Q_b - m0_ab) (p0 the normalised equilibrium, m0 its
+    second moments, w = 1, 2, 1), the three beta from the constant 3 x 3 system
+    that makes the change of the second moments (C_new - C) / ell^2 (psi_tot is
+    unchanged; weighting by the equilibrium rather than by the node's own psi
+    keeps the system well conditioned where psi(q) is far from equilibrium or
+    partly negative, as it is in strong shear on a truncated disk); dpsi enters as the
     linear quasi-equilibrium of Sec. VI-B (populations w_i [dpsi + 3 (v_i .
     dpsi U + Qdot_i . dpsi (Q . grad U - kappa Q))]), U and grad U those of the
     reshaped state. The solvent populations are those of the last sub-step.
@@ -155,6 +158,8 @@ class Setup:
         self.c_e = lat.ell ** 2 * (psi0 * self.qx * self.qx).sum() / psi0.sum() if psi0.sum() > 0 \
             else 1.0
         self.qq = np.stack([self.qx * self.qx, self.qx * self.qy, self.qy * self.qy])  # [3, nq]
+        self.p0 = psi0 / psi0.sum() if psi0.sum() > 0 else np.zeros_like(psi0)
+        self.m0 = self.qq @ self.p0                        # equilibrium second moments
         y = np.arange(self.ny)
         self.arow = lat.a0 * np.sin(lat.kf * y)
         self.beta = 1.0 / (2.0 * lat.tau1 + 1.0)
@@ -274,24 +279,28 @@ def advect(s: Setup, F, U):
             fy * ((1 - fx) * F[..., y1, x0] + fx * F[..., y1, x1]))
 
 
-def reshape_factors(s: Setup, psi_q, C_new):
-    """f[ny, nx, nq] with sum_q psi f = sum_q psi and ell^2 sum_q psi f QQ / psi_tot = C_new."""
+def reshape_dpsi(s: Setup, psi_q, C_new):
+    """dpsi[ny, nx, nq]: the change of psi(q) that moves the conformation of psi_q
+    [ny, nx, nq] to C_new [3, ny, nx] at unchanged psi_tot: the equilibrium-weighted
+    second-order form dpsi(q) = psi_tot p0(q) sum_ab w_ab beta_ab (Q_a Q_b - m0_ab)
+    (p0 the normalised equilibrium, m0 its second moments, w = 1, 2, 1 for xx, xy, yy),
+    with beta from M0 beta = (C_new - C) / ell^2, M0 = sum_q p0 QQ (w (QQ - m0))^T a
+    constant, well-conditioned 3 x 3 matrix."""
     l2 = s.lat.ell ** 2
     pt = psi_q.sum(-1)
-    p = psi_q / pt[..., None]                             # [ny, nx, nq]
-    m = np.einsum("yxq,cq->yxc", p, s.qq)                 # [ny, nx, 3]
-    dev = s.qq[None, None] - m[..., None]                 # [ny, nx, 3, nq]
+    C = l2 * np.einsum("yxq,cq->cyx", psi_q, s.qq) / pt[None]
     w = np.array([1.0, 2.0, 1.0])
-    M = np.einsum("yxq,aq,yxbq->yxab", p, s.qq, dev * w[None, None, :, None])
-    rhs = np.moveaxis(C_new, 0, -1) / l2 - m              # [ny, nx, 3]
-    beta = np.linalg.solve(M, rhs[..., None])[..., 0]
-    return 1.0 + np.einsum("yxc,yxcq->yxq", beta * w, dev)
+    dev0 = s.qq - s.m0[:, None]                            # [3, nq]
+    M0 = (s.p0[None, :] * s.qq) @ (w[:, None] * dev0).T    # [3, 3]
+    beta = np.einsum("ab,byx->ayx", np.linalg.inv(M0), (C_new - C) / l2)
+    shape = np.einsum("ayx,aq->yxq", beta * w[:, None, None], dev0)
+    return pt[..., None] * s.p0[None, None, :] * shape
 
 
 def reshape_increment(s: Setup, gs, gp, C_new):
     """Equilibrium-shaped change of the pulled polymer populations gp [ny, nx, nq, 25]
-    that moves their conformation to C_new: dpsi(q) = psi(q) (f(q) - 1), f from
-    reshape_factors, carried as the linear quasi-equilibrium of Sec. VI-B,
+    that moves their conformation to C_new: dpsi from reshape_dpsi, carried as the
+    linear quasi-equilibrium of Sec. VI-B,
     dg_i = w_i [dpsi + 3 (v_i . dpsi U + Qdot_i . dpsi (Q . grad U - kappa Q))],
     with U the mixture velocity of the reshaped state (pulled solvent gs [9, ny, nx]):
     rho U = J_S + J_P + (E + rho a) / 2, E = div Theta of C_new (dg carries no momentum
@@ -299,7 +308,7 @@ def reshape_increment(s: Setup, gs, gp, C_new):
     psi_q = gp.sum(-1)
     if not s.lat.psi_tot > 0:                             # no polymer: nothing to reshape
         return np.zeros_like(gp)
-    dpsi = psi_q * (reshape_factors(s, psi_q, C_new) - 1.0)          # [ny, nx, nq]
+    dpsi = reshape_dpsi(s, psi_q, C_new)                              # [ny, nx, nq]
     c25, w25, _ = O.d4q25()
     psi_tot = psi_q.sum(-1)
     rho_s = gs.sum(0)

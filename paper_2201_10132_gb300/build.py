@@ -14,7 +14,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libtfkt.so")
-SOURCES = ["tfkt_kernels.cu", "tfkt_fused.cu", "tfkt_api.cu", "tfkt_noalloc.cu", "tfkt_batch.cu"]
+SOURCES = ["tfkt_kernels.cu", "tfkt_fused.cu", "tfkt_api.cu", "tfkt_noalloc.cu", "tfkt_batch.cu",
+           "tfkt_mlp.cu", "tfkt_lpm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-I", os.path.join(ROOT, "include"), "-I", CSRC]
@@ -37,7 +38,7 @@ def _stale(target: str, deps: list[str]) -> bool:
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
-    headers.append(os.path.join(ROOT, "include", "tfkt.h"))
+    headers += [os.path.join(ROOT, "include", f) for f in ("tfkt.h", "tfkt_lpm.h")]
     nvcc = _nvcc()
     procs, objs = [], []
     for src in SOURCES:

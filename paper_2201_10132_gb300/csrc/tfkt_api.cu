@@ -559,6 +559,10 @@ FusedArgs<real> ctx_fused(const Ctx* c) {
 }
 template KernelArgs<float> ctx_args<float>(const Ctx*);
 template FusedArgs<float> ctx_fused<float>(const Ctx*);
+tfkt_status ctx_ensure_moments_f32(Ctx* c) {
+  if (c->L.precision != TFKT_FP32) return fail(TFKT_EINVAL, "FP32 context expected");
+  return ensure_moments<float, float>(c);
+}
 }  // namespace tfkt
 
 extern "C" {
@@ -729,6 +733,10 @@ tfkt_status tfkt_destroy(tfkt_ctx* c) {
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (c->ws.owned && c->ws.base) {
     cudaError_t f = cudaFree(c->ws.base);
+    if (e == cudaSuccess) e = f;
+  }
+  if (c->lpm) {
+    cudaError_t f = cudaFree(c->lpm);
     if (e == cudaSuccess) e = f;
   }
   delete c;

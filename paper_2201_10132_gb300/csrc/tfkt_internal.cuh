@@ -164,6 +164,8 @@ struct Ctx {
   bool fused = false;     // grid fits the fused single-pass kernel
   int mcur = 0;           // moment buffer (0: off_M, 1: off_M2) of the current state
   double dvx = 0, dvy = 0;  // r-momentum of all pull shift differences (fused path)
+  void* lpm = nullptr;    // scratch of the learned block (allocated on first use)
+  int64_t lpm_step = -1;  // step whose conformation the learned block's scratch holds
 };
 
 // Host helpers (tfkt_api.cu).
@@ -224,6 +226,8 @@ template <typename real>
 KernelArgs<real> ctx_args(const Ctx* c);
 template <typename real>
 FusedArgs<real> ctx_fused(const Ctx* c);
+// Make the moment planes of an FP32 context current (tfkt_api.cu).
+tfkt_status ctx_ensure_moments_f32(Ctx* c);
 
 constexpr int TX = 32;   // tile width (one warp along x)
 constexpr int TY = 8;    // tile height

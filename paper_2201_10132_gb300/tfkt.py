@@ -51,6 +51,18 @@ class _Info(ctypes.Structure):
                 ("bytes_per_node_step", ctypes.c_size_t), ("fene_b", ctypes.c_double)]
 
 
+class LpmOpts(ctypes.Structure):
+    """Mirror of tfkt_lpm_opts."""
+    _fields_ = [("K", ctypes.c_int32), ("tile", ctypes.c_int32), ("threshold", ctypes.c_float),
+                ("mode", ctypes.c_int32)]
+
+
+LPM_NET, LPM_FROZEN = 0, 1
+MLP_IN, MLP_HID, MLP_OUT = 40, 64, 3
+MLP_NWEIGHTS = MLP_HID * MLP_IN + MLP_HID + MLP_HID * MLP_HID + MLP_HID + MLP_OUT * MLP_HID + MLP_OUT
+MLP_NPARAM = MLP_NWEIGHTS + 2 * MLP_IN + 2 * MLP_OUT
+
+
 @dataclass
 class Params:
     """Mirror of tfkt_params (physical description of one Kolmogorov run)."""
@@ -116,6 +128,23 @@ def lib() -> ctypes.CDLL:
         L.tfkt_batch_destroy.argtypes = [P]
         for n in ("tfkt_batch_required_bytes", "tfkt_batch_create", "tfkt_batch_step",
                   "tfkt_batch_run", "tfkt_batch_destroy"):
+            getattr(L, n).restype = S
+        F = ctypes.POINTER(ctypes.c_float)
+        L.tfkt_mlp_create.argtypes = [F, P, ctypes.POINTER(P)]
+        L.tfkt_mlp_destroy.argtypes = [P]
+        L.tfkt_mlp_get.argtypes = [P, F]
+        L.tfkt_mlp_set.argtypes = [P, F]
+        L.tfkt_mlp_forward.argtypes = [P, P, ctypes.c_int64, P]
+        L.tfkt_mlp_loss_grad.argtypes = [P, P, P, ctypes.c_int64, D, P]
+        L.tfkt_mlp_adam.argtypes = [P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                    ctypes.c_float]
+        L.tfkt_lpm_run.argtypes = [P, P, ctypes.POINTER(LpmOpts), ctypes.c_int64,
+                                   ctypes.POINTER(ctypes.c_int64)]
+        L.tfkt_lpm_features.argtypes = [P, ctypes.c_int32, P, P]
+        L.tfkt_lpm_targets.argtypes = [P, P, P]
+        for n in ("tfkt_mlp_create", "tfkt_mlp_destroy", "tfkt_mlp_get", "tfkt_mlp_set",
+                  "tfkt_mlp_forward", "tfkt_mlp_loss_grad", "tfkt_mlp_adam", "tfkt_lpm_run",
+                  "tfkt_lpm_features", "tfkt_lpm_targets"):
             getattr(L, n).restype = S
         L.tfkt_status_string.argtypes = [S]
         L.tfkt_status_string.restype = ctypes.c_char_p
@@ -338,3 +367,95 @@ class Batch:
 
     def __exit__(self, *exc):
         self.close()
+
+
+# ---------------------------------------------------------------- learned macro-step
+def pack_mlp(W1, b1, W2, b2, W3, b3, mx, sx, mt, st) -> np.ndarray:
+    """The packed FP32 parameter vector of tfkt_lpm.h."""
+    parts = [np.asarray(v, dtype=np.float32).ravel() for v in (W1, b1, W2, b2, W3, b3, mx, sx, mt, st)]
+    out = np.concatenate(parts)
+    assert out.size == MLP_NPARAM
+    return out
+
+
+def unpack_mlp(v: np.ndarray) -> dict:
+    shapes = [("W1", (MLP_HID, MLP_IN)), ("b1", (MLP_HID,)), ("W2", (MLP_HID, MLP_HID)),
+              ("b2", (MLP_HID,)), ("W3", (MLP_OUT, MLP_HID)), ("b3", (MLP_OUT,)),
+              ("mx", (MLP_IN,)), ("sx", (MLP_IN,)), ("mt", (MLP_OUT,)), ("st", (MLP_OUT,))]
+    out, k = {}, 0
+    for name, shp in shapes:
+        n = int(np.prod(shp))
+        out[name] = np.asarray(v[k:k + n], dtype=np.float32).reshape(shp)
+        k += n
+    return out
+
+
+def _fptr(a: np.ndarray):
+    assert a.dtype == np.float32 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+class Mlp:
+    """The learned macro-step's network on the device (tfkt_mlp_*). Device arrays are
+    passed as integer pointers (e.g. torch.Tensor.data_ptr())."""
+
+    def __init__(self, params: np.ndarray, stream: int | None = None):
+        v = np.ascontiguousarray(params, dtype=np.float32)
+        h = ctypes.c_void_p()
+        _check(lib().tfkt_mlp_create(_fptr(v), ctypes.c_void_p(stream or 0), ctypes.byref(h)),
+               "tfkt_mlp_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(lib().tfkt_mlp_destroy(self._h), "tfkt_mlp_destroy")
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get(self) -> np.ndarray:
+        v = np.zeros(MLP_NPARAM, np.float32)
+        _check(lib().tfkt_mlp_get(self._h, _fptr(v)), "tfkt_mlp_get")
+        return v
+
+    def set(self, params: np.ndarray):
+        v = np.ascontiguousarray(params, dtype=np.float32)
+        _check(lib().tfkt_mlp_set(self._h, _fptr(v)), "tfkt_mlp_set")
+
+    def forward(self, X_ptr: int, n: int, Y_ptr: int):
+        _check(lib().tfkt_mlp_forward(self._h, ctypes.c_void_p(X_ptr), n, ctypes.c_void_p(Y_ptr)),
+               "tfkt_mlp_forward")
+
+    def loss_grad(self, X_ptr: int, T_ptr: int, n: int, grad_ptr: int | None = None) -> float:
+        loss = ctypes.c_double()
+        _check(lib().tfkt_mlp_loss_grad(self._h, ctypes.c_void_p(X_ptr), ctypes.c_void_p(T_ptr), n,
+                                        ctypes.byref(loss), ctypes.c_void_p(grad_ptr or 0)),
+               "tfkt_mlp_loss_grad")
+        return loss.value
+
+    def adam(self, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+        _check(lib().tfkt_mlp_adam(self._h, lr, beta1, beta2, eps), "tfkt_mlp_adam")
+
+
+def lpm_run(solver: Solver, net: Mlp | None, nblocks: int, K: int = 8, tile: int = 32,
+            threshold: float = 0.25, mode: int = LPM_NET) -> int:
+    """Run learned blocks on a solver; returns the number of tiles that fell back."""
+    o = LpmOpts(K, tile, threshold, mode)
+    flagged = ctypes.c_int64()
+    _check(lib().tfkt_lpm_run(solver._h, net._h if net is not None else None, ctypes.byref(o),
+                              nblocks, ctypes.byref(flagged)), "tfkt_lpm_run")
+    return int(flagged.value)
+
+
+def lpm_features(solver: Solver, K: int, X_ptr: int, Cdep_ptr: int):
+    _check(lib().tfkt_lpm_features(solver._h, K, ctypes.c_void_p(X_ptr), ctypes.c_void_p(Cdep_ptr)),
+           "tfkt_lpm_features")
+
+
+def lpm_targets(solver: Solver, Cdep_ptr: int, T_ptr: int):
+    _check(lib().tfkt_lpm_targets(solver._h, ctypes.c_void_p(Cdep_ptr), ctypes.c_void_p(T_ptr)),
+           "tfkt_lpm_targets")

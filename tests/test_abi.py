@@ -1,5 +1,5 @@
 """C-ABI checks that need no GPU: the library loads, exports every function that
-include/tfkt.h declares, and rejects invalid parameters before touching a device."""
+include/*.h declares, and rejects invalid parameters before touching a device."""
 import ctypes
 import os
 import re
@@ -17,14 +17,19 @@ def T():
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "tfkt.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(tfkt_[a-z_]+)\s*\(", src)))
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in sorted(os.listdir(inc)):
+        if f.endswith(".h"):
+            src = re.sub(r"/\*.*?\*/", "", open(os.path.join(inc, f)).read(), flags=re.S)
+            names |= set(re.findall(r"\b(tfkt_[a-z_0-9]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_exports_every_declared_symbol(T):
     names = _declared()
-    assert {"tfkt_create", "tfkt_step", "tfkt_moments", "tfkt_destroy"} <= set(names)
+    assert {"tfkt_create", "tfkt_step", "tfkt_moments", "tfkt_destroy", "tfkt_mlp_forward",
+            "tfkt_mlp_loss_grad", "tfkt_lpm_run"} <= set(names)
     lib = ctypes.CDLL(T.LIB_PATH)
     for n in names:
         assert hasattr(lib, n), n
