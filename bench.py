@@ -221,6 +221,71 @@ def precision_sweep(W, steps: int):
     return out
 
 
+def learned_vs_plain(W, nblocks: int, warm: int):
+    """The learned macro-step (1 plain step + K solvent sub-steps per block, the
+    committed network) against the plain FP32 step and the FP64 step on the same
+    seeded workload: time per block against 1 + K plain steps, per-field errors
+    against the plain FP32 run after the blocks, and the growth rate of sum U_y^2
+    over the blocks against the FP64 run. The block without the network (every tile
+    keeping the plain step's conformation) is reported beside it."""
+    import numpy as np
+    import torch
+    from paper_2201_10132_gb300 import tfkt, train_lpm
+    from paper_2201_10132_gb300.inputs import perturbation
+    params, meta = train_lpm.load()
+    K, thr = meta["K"], meta["threshold"]
+    pert = perturbation(W.nx, W.ny, W.seed, W.amp, W.u0)
+    names = ["ux", "uy", "cxx", "cxy", "cyy"]
+    net = tfkt.Mlp(params)
+    res, fields = {}, {}
+    for label in ("fp64", "fp32", "net", "frozen"):
+        p = tfkt.Params.from_workload(W, tfkt.FP64 if label == "fp64" else tfkt.FP32)
+        ws = torch.empty(tfkt.required_bytes(p), dtype=torch.uint8, device="cuda")
+        st = torch.cuda.Stream()
+        s = tfkt.Solver(p, pert, workspace=ws, stream=st.cuda_stream)
+        s.step(warm)
+        ey2, ms, fl = [], 0.0, 0
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        for b in range(nblocks):
+            s.sync()
+            e0.record(st)
+            if label in ("fp64", "fp32"):
+                s.step(1 + K)
+            elif label == "net":
+                fl += tfkt.lpm_run(s, net, 1, K=K, tile=32, threshold=thr)
+            else:
+                tfkt.lpm_run(s, None, 1, K=K, tile=32, threshold=thr, mode=tfkt.LPM_FROZEN)
+            e1.record(st)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+            ey2.append(s.diagnostics()["ey2"])
+        if label != "fp64":
+            fields[label] = s.moments(names)
+        s.close()
+        del s, ws
+        torch.cuda.empty_cache()
+        t = np.arange(1, nblocks + 1) * (1 + K)
+        h = nblocks // 2
+        res[label] = {"ms_per_block": ms / nblocks, "fallback_tiles": fl,
+                      "glups_equivalent": W.nx * W.ny * (1 + K) / (ms / nblocks / 1e3) / 1e9,
+                      "ey2_rate": float(np.polyfit(t[h:], np.log(ey2[h:]), 1)[0])}
+    net.close()
+    ref = fields["fp32"]
+    us = max(np.abs(ref["ux"]).max(), np.abs(ref["uy"]).max())
+    cs = max(np.abs(ref[k]).max() for k in ("cxx", "cxy", "cyy"))
+    for label in ("fp32", "net", "frozen"):
+        r = res[label]
+        r["ey2_rate_rel_err_vs_fp64"] = abs(r["ey2_rate"] / res["fp64"]["ey2_rate"] - 1)
+        r["speedup_vs_fp32"] = res["fp32"]["ms_per_block"] / r["ms_per_block"]
+        if label != "fp32":
+            r["u_linf_vs_fp32"] = max(float(np.abs(fields[label][k] - ref[k]).max()) for k in
+                                      ("ux", "uy")) / us
+            r["c_linf_vs_fp32"] = max(float(np.abs(fields[label][k] - ref[k]).max()) for k in
+                                      ("cxx", "cxy", "cyy")) / cs
+    return {"K": K, "threshold": thr, "blocks": nblocks, "warm_plain_steps": warm, "modes": res}
+
+
 def ensemble_throughput(n_runs: int, steps: int, warmup: int):
     """Aggregate GLUPS of a seeded ensemble advanced as one batch (one launch of the
     fused kernel and one of its fix-up per step, replayed from a CUDA graph)."""
@@ -263,6 +328,10 @@ def main():
                     help="instead of the throughput line: a seeded ensemble advanced as one batch")
     ap.add_argument("--precision-sweep", type=int, default=0, metavar="STEPS",
                     help="instead of the throughput line: FP64 vs FP32 vs FP16 errors and times")
+    ap.add_argument("--learned", type=int, default=0, metavar="BLOCKS",
+                    help="instead of the throughput line: the learned macro-step against the "
+                         "plain step (speed, field and growth-rate errors)")
+    ap.add_argument("--learned-warm", type=int, default=240)
     args = ap.parse_args()
     from paper_2201_10132_gb300.inputs import WORKLOADS
     W = WORKLOADS[args.workload]
@@ -274,6 +343,12 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         print(json.dumps({"ensemble": ensemble_throughput(args.ensemble, args.steps,
                                                           args.warmup)}), flush=True)
+        return
+    if args.learned:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        print(json.dumps({"learned": learned_vs_plain(W, args.learned, args.learned_warm),
+                          "workload": W.name}), flush=True)
         return
     if args.precision_sweep:
         import torch

@@ -204,3 +204,46 @@ def test_rejects_unsupported(T, kw, K):
         with pytest.raises(T.TfktError) as e:
             T.lpm_run(s, None, 1, K=K, mode=T.LPM_FROZEN)
         assert e.value.status == 1
+
+
+def test_trained_network_gains_over_the_block_without_it(T):
+    """The committed network against the same block without it (every tile keeping
+    the plain step's conformation), both against the plain solver, on a flow it was
+    not trained on (256^2, seed 123, laminar start with a 5% perturbation)."""
+    from paper_2201_10132_gb300 import train_lpm
+    from paper_2201_10132_gb300.inputs import Workload, perturbation
+    params, meta = train_lpm.load()
+    K, thr = meta["K"], meta["threshold"]
+    w = Workload("gain-256", 256, 256, 6, 3.0, 10.0, 1.0, 0.2, 0.05, 4, 123, 0.05, ic_mode=1)
+    p = T.Params.from_workload(w, T.FP32)
+    pert = perturbation(w.nx, w.ny, w.seed, w.amp, w.u0)
+    net = T.Mlp(params)
+    sols = {m: T.Solver(p, pert) for m in ("plain", "net", "frozen")}
+    ey2 = {m: [] for m in sols}
+    fl = 0
+    nblk = 40
+    for s in sols.values():
+        s.step(600)
+    for _ in range(nblk):
+        sols["plain"].step(1 + K)
+        fl += T.lpm_run(sols["net"], net, 1, K=K, tile=32, threshold=thr)
+        T.lpm_run(sols["frozen"], None, 1, K=K, tile=32, threshold=thr, mode=T.LPM_FROZEN)
+        for m, s in sols.items():
+            ey2[m].append(s.diagnostics()["ey2"])
+    f = {m: s.moments(["ux", "uy", "cxx", "cxy", "cyy"]) for m, s in sols.items()}
+    us = max(np.abs(f["plain"][k]).max() for k in ("ux", "uy"))
+    cs = max(np.abs(f["plain"][k]).max() for k in ("cxx", "cxy", "cyy"))
+    t = np.arange(1, nblk + 1) * (1 + K)
+    rate = {m: np.polyfit(t[nblk // 2:], np.log(ey2[m][nblk // 2:]), 1)[0] for m in sols}
+    err = {}
+    for m in ("net", "frozen"):
+        err[m] = (max(np.abs(f[m][k] - f["plain"][k]).max() for k in ("ux", "uy")) / us,
+                  max(np.abs(f[m][k] - f["plain"][k]).max() for k in ("cxx", "cxy", "cyy")) / cs,
+                  abs(rate[m] / rate["plain"] - 1))
+    assert fl == 0
+    assert err["net"][0] < 0.5 * err["frozen"][0], err       # velocity
+    assert err["net"][1] < 0.25 * err["frozen"][1], err      # conformation
+    assert err["net"][2] < 0.02 and err["net"][2] < err["frozen"][2], err   # growth rate
+    for s in sols.values():
+        s.close()
+    net.close()
