@@ -385,8 +385,10 @@ tfkt_status do_step(Ctx* c, int64_t n) {
     KernelArgs<real> a = make_args<real>(c);
     if (c->fused) {
       FusedArgs<real> f = make_fused<real>(c);
+      if (c->lpm_pending) f.rshp = (const real*)c->lpm_rshp;
       TFKT_CUDA(c, launch_step_fused<real, S>(a, f, c->stream));
       TFKT_CUDA(c, launch_fixup<real>(a, f, c->stream));
+      c->lpm_pending = false;
       c->mcur ^= 1;
     } else {
       TFKT_CUDA(c, launch_step<real, S>(a, c->stream));
@@ -432,9 +434,11 @@ tfkt_status do_step_profiled(Ctx* c, int64_t n, double* ms, int64_t* launches) {
     KernelArgs<real> a = make_args<real>(c);
     if (c->fused) {
       FusedArgs<real> f = make_fused<real>(c);
+      if (c->lpm_pending) f.rshp = (const real*)c->lpm_rshp;
       tfkt_status s =
           timed(TFKT_K_FUSED, [&] { return launch_step_fused<real, S>(a, f, c->stream); });
       if (s != TFKT_OK) return s;
+      c->lpm_pending = false;
       s = timed(TFKT_K_FIXUP, [&] { return launch_fixup<real>(a, f, c->stream); });
       if (s != TFKT_OK) return s;
       c->mcur ^= 1;
@@ -491,6 +495,10 @@ tfkt_status do_psi(Ctx* c, double* dst, int dst_is_device) {
 template <typename real, typename S>
 tfkt_status do_populations(Ctx* c, double* host) {
   const Lattice& L = c->L;
+  if (c->lpm_pending) {
+    tfkt_status s = ctx_lpm_flush(c);
+    if (s != TFKT_OK) return s;
+  }
   KernelArgs<real> a = make_args<real>(c);
   const size_t N = (size_t)L.nx * L.ny;
   double* tmp = nullptr;

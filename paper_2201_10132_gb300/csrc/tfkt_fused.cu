@@ -179,7 +179,7 @@ __device__ __forceinline__ void velocity_at(const KernelArgs<real>& a, const rea
 
 // One tile (btx, bty) of an ntx x nty tile grid; shared by the single-run and
 // the batched kernels.
-template <typename real, typename S>
+template <typename real, typename S, bool RESHAPE = false>
 __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const FusedArgs<real>& fa,
                                            int btx, int bty, int ntx, int nty,
                                            unsigned char* smem_raw) {
@@ -339,6 +339,16 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
   }
   __syncthreads();
 
+  // a learned block's pending increment: dpsi(q) = p0(q) (B0 Qx^2 + B1 Qx Qy + B2 Qy^2 + B3)
+  real B0 = 0, B1 = 0, B2 = 0, B3 = 0, rpt0 = 0;
+  if constexpr (RESHAPE) {
+    B0 = fa.rshp[n];
+    B1 = fa.rshp[P + n];
+    B2 = fa.rshp[2 * P + n];
+    B3 = fa.rshp[3 * P + n];
+    rpt0 = real(1) / a.psi_tot0;
+  }
+
   // ---- polymer, one Q-node at a time
   for (int q = 0; q < nq; ++q) {
     const uint32_t bm = bounce_mask(q);
@@ -347,6 +357,24 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
       load_vec<DQ>(dl, sm.delta + q * DQ);
 #pragma unroll
       for (int i = 0; i < 25; ++i) h[i] = h[i] * a.pinv + dl[i];   // unscale, shift to this Q-node
+    }
+    if constexpr (RESHAPE) {
+      // added as the linear quasi-equilibrium w_i [dpsi + 3 (v_i . dpsi U + Qdot_i . dpsi
+      // (Q . grad U - kappa Q))] with this step's U and grad U (Hookean springs)
+      const real Qx = a.tab.qx[q], Qy = a.tab.qy[q];
+      const real dps = a.tab.psi0[q] * rpt0 * (B0 * Qx * Qx + B1 * Qx * Qy + B2 * Qy * Qy + B3);
+      const real t1 = real(3) * dps * Ux, t2 = real(3) * dps * Uy;
+      const real t3 = real(3) * dps * (Qx * G00 + Qy * G10 - a.kappa * Qx);
+      const real t4 = real(3) * dps * (Qx * G01 + Qy * G11 - a.kappa * Qy);
+      static_for<0, 25>([&](auto I) {
+        constexpr int i = I;
+        real v = dps;
+        acc<c25(i).rx>(v, t1);
+        acc<c25(i).ry>(v, t2);
+        acc<c25(i).qx>(v, t3);
+        acc<c25(i).qy>(v, t4);
+        h[i] += real(w25(i)) * v;
+      });
     }
     const real dpx = real(0.5) * (mn[0] - mn[1]);
     const real dpy = real(0.5) * (mn[2] - mn[3]);
@@ -484,11 +512,11 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
   }
 }
 
-template <typename real, typename S>
+template <typename real, typename S, bool RESHAPE>
 __global__ void __launch_bounds__(NT, 2)
 step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  fused_body<real, S>(a, fa, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y, smem_raw);
+  fused_body<real, S, RESHAPE>(a, fa, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y, smem_raw);
 }
 
 // Completes the border nodes of every tile: own partial sums plus the ring
@@ -652,10 +680,23 @@ bool fused_supported(int nx, int ny, int nq, size_t real_bytes) {
 template <typename real, typename S>
 cudaError_t launch_step_fused(const KernelArgs<real>& a, const FusedArgs<real>& f, cudaStream_t s) {
   const size_t smem = fused_smem_bytes(a.nq, sizeof(real));
-  cudaError_t e = cudaFuncSetAttribute(step_fused_kernel<real, S>,
+  const dim3 grid(a.nx / TX, a.ny / TY), block(TX, TY);
+  if (f.rshp) {
+    // a learned block's increment rides on this step's pull (FP32 storage only)
+    if constexpr (std::is_same<real, float>::value && std::is_same<S, float>::value) {
+      cudaError_t e = cudaFuncSetAttribute(step_fused_kernel<real, S, true>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      step_fused_kernel<real, S, true><<<grid, block, smem, s>>>(a, f);
+      return cudaGetLastError();
+    } else {
+      return cudaErrorInvalidValue;
+    }
+  }
+  cudaError_t e = cudaFuncSetAttribute(step_fused_kernel<real, S, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  step_fused_kernel<real, S><<<dim3(a.nx / TX, a.ny / TY), dim3(TX, TY), smem, s>>>(a, f);
+  step_fused_kernel<real, S, false><<<grid, block, smem, s>>>(a, f);
   return cudaGetLastError();
 }
 

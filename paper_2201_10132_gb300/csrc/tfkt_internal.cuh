@@ -132,6 +132,10 @@ struct FusedArgs {
   const real* dpsi;     // [nq] sum over i of the pull shift differences of Q-node q
   const long long* poff;  // [nq*25] element offset of each pull's source plane
   real dvx, dvy;        // r-momentum of all pull shift differences
+  // Pending increment of a learned block (or null): per node the coefficients
+  // B0..B3 (4 planes) of dpsi(q) = p0(q) (B0 Qx^2 + B1 Qx Qy + B2 Qy^2 + B3), added to
+  // the pulled polymer populations as a linear quasi-equilibrium (FP32 only).
+  const real* rshp;
 };
 
 // One run of a batch: its kernel arguments for both buffer parities.
@@ -166,6 +170,8 @@ struct Ctx {
   double dvx = 0, dvy = 0;  // r-momentum of all pull shift differences (fused path)
   void* lpm = nullptr;    // scratch of the learned block (allocated on first use)
   int64_t lpm_step = -1;  // step whose conformation the learned block's scratch holds
+  bool lpm_pending = false;        // an increment waits to be added at the next pull
+  const float* lpm_rshp = nullptr; // its coefficient planes
 };
 
 // Host helpers (tfkt_api.cu).
@@ -228,6 +234,8 @@ template <typename real>
 FusedArgs<real> ctx_fused(const Ctx* c);
 // Make the moment planes of an FP32 context current (tfkt_api.cu).
 tfkt_status ctx_ensure_moments_f32(Ctx* c);
+// Add a pending learned-block increment to the stored populations (tfkt_lpm.cu).
+tfkt_status ctx_lpm_flush(Ctx* c);
 
 constexpr int TX = 32;   // tile width (one warp along x)
 constexpr int TY = 8;    // tile height

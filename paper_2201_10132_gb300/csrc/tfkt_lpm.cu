@@ -340,7 +340,9 @@ __global__ void __launch_bounds__(256) reshape_kernel(KernelArgs<float> a, LpmAr
 // to (x, q, i): dg_i = w_i [dpsi + 3 (v_i . dpsi U + Qdot_i . dpsi (Q . grad U - kappa Q))],
 // dpsi from reshape_kernel's coefficients, U and grad U those of the reshaped
 // state (a.U). The pull is a permutation of the stored slots, so every slot is
-// written by one thread.
+// written by one thread. (The block itself leaves the increment to the next
+// step's pull, which adds the same values; this kernel serves readers of the
+// stored populations in between.)
 __global__ void __launch_bounds__(256) apply_kernel(KernelArgs<float> a, LpmArgs l) {
   const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
   if (x >= a.nx || y >= a.ny) return;
@@ -361,15 +363,21 @@ __global__ void __launch_bounds__(256) apply_kernel(KernelArgs<float> a, LpmArgs
     const float jrx = dpsi * ux, jry = dpsi * uy;
     const float jqx = dpsi * (qx * G00 + qy * G10 - l.kappa * qx);
     const float jqy = dpsi * (qx * G01 + qy * G11 - l.kappa * qy);
+    size_t slot[25];
+    float v[25];
+#pragma unroll
+    for (int i = 0; i < 25; ++i) {     // every load of the Q-node before any store
+      const V4 c = c25(i);
+      const int e = a.tab.pull[q * 25 + i];
+      slot[i] = (size_t)(e >= 0 ? e : ~e) * P + (e >= 0 ? nb.o[shift_index(-c.rx, -c.ry)] : nb.o[4]);
+      v[i] = pop[slot[i]];
+    }
 #pragma unroll
     for (int i = 0; i < 25; ++i) {
       const V4 c = c25(i);
       const float dg = float(w25(i)) *
                        (dpsi + 3.f * (float(c.rx) * jrx + float(c.ry) * jry + float(c.qx) * jqx + float(c.qy) * jqy));
-      const int e = a.tab.pull[q * 25 + i];
-      const size_t o = e >= 0 ? nb.o[shift_index(-c.rx, -c.ry)] : nb.o[4];
-      const size_t plane = (size_t)(e >= 0 ? e : ~e);
-      pop[plane * P + o] += dg * a.pscale;
+      pop[slot[i]] = v[i] + dg * a.pscale;
     }
   }
 }
@@ -455,6 +463,23 @@ tfkt_status setup(Ctx* c, int K, LpmArgs* l) {
 }
 
 }  // namespace
+
+// Add the pending increment to the stored populations now (for readers of the
+// populations): U and grad U of the reshaped state, then the slot updates.
+tfkt_status ctx_lpm_flush(Ctx* c) {
+  if (!c->lpm_pending) return TFKT_OK;
+  LpmArgs l;
+  tfkt_status s = setup(c, 2, &l);
+  if (s != TFKT_OK) return s;
+  const Lattice& L = c->L;
+  KernelArgs<float> a = ctx_args<float>(c);
+  LPM_CUDA(launch_velocity<float>(a, c->stream));
+  apply_kernel<<<node_grid2(L.nx, L.ny), dim3(TX, TY), 0, c->stream>>>(a, l);
+  LPM_CUDA(cudaGetLastError());
+  c->lpm_pending = false;
+  return TFKT_OK;
+}
+
 }  // namespace tfkt
 
 using namespace tfkt;
@@ -505,9 +530,9 @@ extern "C" tfkt_status tfkt_lpm_run(tfkt_ctx* cc, const tfkt_mlp* net, const tfk
     a = ctx_args<float>(c);
     reshape_kernel<<<grid, blk, 0, st>>>(a, l);
     LPM_CUDA(cudaGetLastError());
-    LPM_CUDA(launch_velocity<float>(a, st));
-    apply_kernel<<<grid, blk, 0, st>>>(a, l);
-    LPM_CUDA(cudaGetLastError());
+    // the increment rides on the next step's pull (tfkt_step, or the next block)
+    c->lpm_pending = true;
+    c->lpm_rshp = l.p + (size_t)L_B * L.plane;
     c->step += o->K;
     c->lpm_step = c->step;
   }

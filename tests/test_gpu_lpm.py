@@ -247,3 +247,25 @@ def test_trained_network_gains_over_the_block_without_it(T):
     for s in sols.values():
         s.close()
     net.close()
+
+
+def test_pending_increment_flush_equals_fused_pull(T, L, oracle_mod):
+    """A block leaves its increment to the next step's pull; reading the populations
+    in between adds it to the stored populations instead. Both orders give the same
+    next state."""
+    O = oracle_mod
+    vec, _, _ = _random_net(L, T, 9, out_scale=0.2)
+    m = T.Mlp(vec)
+    out = []
+    for flush in (False, True):
+        o, s, _ = _pair(T, O, L, 64, 32, 1.0, 40, 3, K=4, tile=16)
+        T.lpm_run(s, m, 2, K=4, tile=16, threshold=1e9)
+        if flush:
+            s.populations()
+        s.step(2)
+        out.append(s.moments(["ux", "uy", "cxx", "cxy", "cyy", "psi_tot"]))
+        s.close()
+    for k in out[0]:
+        scale = np.abs(out[0][k]).max()
+        assert np.abs(out[0][k] - out[1][k]).max() <= 1e-5 * scale, k
+    m.close()
