@@ -221,7 +221,7 @@ def precision_sweep(W, steps: int):
     return out
 
 
-def learned_vs_plain(W, nblocks: int, warm: int):
+def learned_vs_plain(W, nblocks: int, warm: int, only: bool = False):
     """The learned macro-step (1 plain step + K solvent sub-steps per block, the
     committed network) against the plain FP32 step and the FP64 step on the same
     seeded workload: time per block against 1 + K plain steps, per-field errors
@@ -238,7 +238,7 @@ def learned_vs_plain(W, nblocks: int, warm: int):
     names = ["ux", "uy", "cxx", "cxy", "cyy"]
     net = tfkt.Mlp(params)
     res, fields = {}, {}
-    for label in ("fp64", "fp32", "net", "frozen"):
+    for label in (("net",) if only else ("fp64", "fp32", "net", "frozen")):
         p = tfkt.Params.from_workload(W, tfkt.FP64 if label == "fp64" else tfkt.FP32)
         ws = torch.empty(tfkt.required_bytes(p), dtype=torch.uint8, device="cuda")
         st = torch.cuda.Stream()
@@ -271,6 +271,8 @@ def learned_vs_plain(W, nblocks: int, warm: int):
                       "glups_equivalent": W.nx * W.ny * (1 + K) / (ms / nblocks / 1e3) / 1e9,
                       "ey2_rate": float(np.polyfit(t[h:], np.log(ey2[h:]), 1)[0])}
     net.close()
+    if only:
+        return {"K": K, "threshold": thr, "blocks": nblocks, "warm_plain_steps": warm, "modes": res}
     ref = fields["fp32"]
     us = max(np.abs(ref["ux"]).max(), np.abs(ref["uy"]).max())
     cs = max(np.abs(ref[k]).max() for k in ("cxx", "cxy", "cyy"))
@@ -332,6 +334,8 @@ def main():
                     help="instead of the throughput line: the learned macro-step against the "
                          "plain step (speed, field and growth-rate errors)")
     ap.add_argument("--learned-warm", type=int, default=240)
+    ap.add_argument("--learned-only", action="store_true",
+                    help="time the learned block alone (no reference runs; for profiling)")
     args = ap.parse_args()
     from paper_2201_10132_gb300.inputs import WORKLOADS
     W = WORKLOADS[args.workload]
@@ -347,7 +351,8 @@ def main():
     if args.learned:
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-        print(json.dumps({"learned": learned_vs_plain(W, args.learned, args.learned_warm),
+        print(json.dumps({"learned": learned_vs_plain(W, args.learned, args.learned_warm,
+                                                      args.learned_only),
                           "workload": W.name}), flush=True)
         return
     if args.precision_sweep:
