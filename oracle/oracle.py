@@ -47,7 +47,8 @@ class _Phys(ctypes.Structure):
                 ("q_radius", ctypes.c_double), ("re", ctypes.c_double), ("wi", ctypes.c_double),
                 ("beta", ctypes.c_double), ("u0", ctypes.c_double),
                 ("k_periods", ctypes.c_int32), ("tau2", ctypes.c_double),
-                ("ell", ctypes.c_double), ("fene_b", ctypes.c_double)]
+                ("ell", ctypes.c_double), ("fene_b", ctypes.c_double),
+                ("qe_model", ctypes.c_int32)]
 
 
 class Lattice(ctypes.Structure):
@@ -58,7 +59,7 @@ class Lattice(ctypes.Structure):
                 ("sigma_q2", ctypes.c_double), ("a0", ctypes.c_double), ("kf", ctypes.c_double),
                 ("u0", ctypes.c_double), ("nu", ctypes.c_double), ("nu_s", ctypes.c_double),
                 ("eta_p", ctypes.c_double), ("lambda_h", ctypes.c_double),
-                ("fene_b", ctypes.c_double)]
+                ("fene_b", ctypes.c_double), ("qe_model", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -108,9 +109,10 @@ def _dp(a: np.ndarray | None):
 
 
 def map_params(nx, ny, q_side, q_radius, re, wi, beta, u0, k_periods=1, tau2=0.0,
-               ell=0.0, fene_b=0.0) -> Lattice:
-    """Physical (Re, Wi, beta, U0, grid) -> lattice parameters; ValueError if invalid."""
-    p = _Phys(nx, ny, q_side, q_radius, re, wi, beta, u0, k_periods, tau2, ell, fene_b)
+               ell=0.0, fene_b=0.0, qe_model=0) -> Lattice:
+    """Physical (Re, Wi, beta, U0, grid) -> lattice parameters; ValueError if invalid.
+    tau2: the momentum relaxation time (<= 0: equal to the stress relaxation time)."""
+    p = _Phys(nx, ny, q_side, q_radius, re, wi, beta, u0, k_periods, tau2, ell, fene_b, qe_model)
     out = Lattice()
     if lib().orc_map_params(ctypes.byref(p), ctypes.byref(out)) != 0:
         raise ValueError("invalid physical parameters")

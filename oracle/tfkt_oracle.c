@@ -113,6 +113,7 @@ int orc_map_params(const orc_phys* in, orc_lattice* out) {
   if (in->nx < 1 || in->ny < 1 || in->q_side < 1 || !(in->q_radius > 0)) return -1;
   if (!(in->re > 0) || !(in->beta > 0) || in->beta > 1 || !(in->u0 > 0)) return -1;
   if (in->k_periods < 1 || in->wi < 0 || in->fene_b < 0) return -1;
+  if (in->qe_model != 0 && in->qe_model != 1) return -1;
   if (in->wi == 0 && in->beta < 1) return -1;
   memset(out, 0, sizeof *out);
   out->nx = in->nx;
@@ -124,9 +125,24 @@ int orc_map_params(const orc_phys* in, orc_lattice* out) {
   double l = 1.0 / kf;
   double nu = in->u0 * l / in->re;
   double nu_s = in->beta * nu;
-  double tau1 = 3.0 * nu_s;
-  double tau2 = in->tau2 > 0 ? in->tau2 : tau1;
-  if (tau2 < tau1) return -1;
+  /* reading: the viscosity comes from the stress relaxation time, nu_s = c_s^2 tau_s,
+     and the drag / diffusion from the momentum relaxation time tau_m (the tau2
+     input, default tau_s). Quasi-conserved momenta (Eq. quasieq1) need tau_s <=
+     tau_m and relax the stress first (tau1 = tau_s, tau2 = tau_m); quasi-conserved
+     stresses (Eq. quasieq2) need tau_m <= tau_s and swap the roles (Sec. V:
+     viscosity from tau2, diffusion from tau1). */
+  double tau_s = 3.0 * nu_s;
+  double tau_m = in->tau2 > 0 ? in->tau2 : tau_s;
+  double tau1, tau2;
+  if (in->qe_model == 0) {
+    if (tau_m < tau_s) return -1;
+    tau1 = tau_s;
+    tau2 = tau_m;
+  } else {
+    if (tau_m > tau_s) return -1;
+    tau1 = tau_m;
+    tau2 = tau_s;
+  }
   double ell = in->ell > 0 ? in->ell : sqrt(2.0);
   double eta_p = (1.0 - in->beta) * nu;
   out->kf = kf;
@@ -139,12 +155,13 @@ int orc_map_params(const orc_phys* in, orc_lattice* out) {
   out->u0 = in->u0;
   out->a0 = nu * in->u0 * kf * kf;
   out->fene_b = in->fene_b;
+  out->qe_model = in->qe_model;
   if (in->wi > 0) {
     double lam = in->wi * l / in->u0;
     out->lambda_h = lam;
-    out->H = 1.0 / (4.0 * lam * tau2);
-    out->kappa = 2.0 * out->H * tau2;
-    out->sigma_q2 = tau2 / (3.0 * out->kappa);
+    out->H = 1.0 / (4.0 * lam * tau_m);
+    out->kappa = 2.0 * out->H * tau_m;
+    out->sigma_q2 = tau_m / (3.0 * out->kappa);
     out->psi_tot = eta_p / (0.5 * out->H * ell * ell * out->sigma_q2 * lam);
   } else {
     out->lambda_h = 0;
@@ -443,8 +460,14 @@ static void macro(orc_state* st) {
 
 /* ------------------------------------------------------------- the step */
 
+static void collide_stress_qe(orc_state* st);
+
 void orc_collide(orc_state* st) {
   macro(st);
+  if (st->L.qe_model == 1) {
+    collide_stress_qe(st);
+    return;
+  }
   const int nx = st->nx, ny = st->ny, nq = st->nq;
   const double tau1 = st->L.tau1, tau2 = st->L.tau2, kappa = st->L.kappa;
   const double b = 1.0 / (2.0 * tau1 + 1.0); /* beta = dt / (2 tau1 + dt) */
@@ -507,6 +530,112 @@ void orc_collide(orc_state* st) {
           double fstar = feq_polymer(st->wp[i], psi, st->cp[i], jrfx, jrfy, jqfx, jqfy);
           double feq = feq_polymer(st->wp[i], psi, st->cp[i], jrex, jrey, jqex, jqey);
           fpost[i] = (1.0 - 2.0 * b) * f[i] + 2.0 * b * ((1.0 - r) * fstar + r * feq);
+        }
+      }
+    }
+  }
+}
+
+/* Collision with the component stresses quasi-conserved (Sec. V, Eq. quasieq2;
+   Sec. VI: f*_S with P_S, f**_P with P^r, P^rQ, P^Q). The targets carry the
+   equilibrium momenta (rho_S U for the solvent, J^r_eq and J^Q_eq for the
+   polymer, as in the momentum model but with the momentum relaxation time
+   tau1 = tau_m) and the current stresses of f; the trapezoidal g-scheme then
+   reads g' = (1 - 2 beta) g + 2 beta [(1 - tau1/tau2) f** + (tau1/tau2) f^eq] with
+   beta = 1/(2 tau1 + 1). The stresses of f follow from those of g as the
+   momenta do in the other model, g = f - (Omega + S)/2 with Omega moving the
+   stress at the rate 1/tau2 only and the Guo source S (force F = (rho a, 0) on
+   the solvent) adding F U + U F: P_S(f) = (2 tau2 P_S(g) + P_eq + tau2 (F U + U F))
+   / (2 tau2 + 1); the polymer carries no source, so P(f) = (2 tau2 P(g) + P_eq) /
+   (2 tau2 + 1) for its three blocks.
+   reading: the printed quasi-equilibria lack the Hermite normalisations; they
+   are the ones that give <f**, vv> = P (1/(2 c_s^4) = 9/2 for the diagonal
+   blocks, 1/c_s^4 = 9 for the r-Q block), as the text requires of f**.
+   reading: the forcing enters as in the momentum model (Guo source on the
+   solvent, half-force shift of U). */
+static void collide_stress_qe(orc_state* st) {
+  const int nx = st->nx, ny = st->ny, nq = st->nq;
+  const double tau1 = st->L.tau1, tau2 = st->L.tau2, kappa = st->L.kappa;
+  const double b = 1.0 / (2.0 * tau1 + 1.0);
+  const double r = tau1 / tau2;
+  const double c2 = 2.0 * tau2;
+  const double cs2 = 1.0 / 3.0;
+#pragma omp parallel for schedule(static)
+  for (int y = 0; y < ny; ++y) {
+    double a = forcing(st, y);
+    for (int x = 0; x < nx; ++x) {
+      size_t n = (size_t)y * nx + x;
+      double Ux = st->ux[n], Uy = st->uy[n];
+      double rho_s = st->rho_s[n];
+      double rho = rho_s + st->psitot[n];
+      double G00, G01, G10, G11;
+      if (st->imposed) {
+        G00 = st->G[0][0]; G01 = st->G[0][1]; G10 = st->G[1][0]; G11 = st->G[1][1];
+      } else {
+        G00 = st->gux[n * 2]; G01 = st->guy[n * 2]; G10 = st->gux[n * 2 + 1]; G11 = st->guy[n * 2 + 1];
+      }
+      /* solvent: P_S(g), P_eq = rho_S (c_s^2 I + U U), P_S(f) */
+      const double* g = st->gs + n * 9;
+      double* gpost = st->gs_post + n * 9;
+      double pxx = 0, pxy = 0, pyy = 0;
+      for (int i = 0; i < 9; ++i) {
+        int cx = st->cs[i][0], cy = st->cs[i][1];
+        pxx += g[i] * cx * cx;
+        pxy += g[i] * cx * cy;
+        pyy += g[i] * cy * cy;
+      }
+      double exx = rho_s * (cs2 + Ux * Ux), exy = rho_s * Ux * Uy, eyy = rho_s * (cs2 + Uy * Uy);
+      double Fx = rho * a; /* F = (rho a, 0): F U + U F = (2 Fx Ux, Fx Uy; Fx Uy, 0) */
+      double fxx = (c2 * pxx + exx + tau2 * 2.0 * Fx * Ux) / (c2 + 1.0);
+      double fxy = (c2 * pxy + exy + tau2 * Fx * Uy) / (c2 + 1.0);
+      double fyy = (c2 * pyy + eyy) / (c2 + 1.0);
+      for (int i = 0; i < 9; ++i) {
+        int cx = st->cs[i][0], cy = st->cs[i][1];
+        /* f*_S = w [rho_S + rho_S c.U / c_s^2 + (P_S - rho_S c_s^2 I):(cc - c_s^2 I) / (2 c_s^4)] */
+        double hxx = cx * cx - cs2, hxy = (double)(cx * cy), hyy = cy * cy - cs2;
+        double pneq = (fxx - rho_s * cs2) * hxx + 2.0 * fxy * hxy + (fyy - rho_s * cs2) * hyy;
+        double fss = st->ws[i] * (rho_s + 3.0 * rho_s * (cx * Ux + cy * Uy) + 4.5 * pneq);
+        double feq = feq_solvent(st->ws[i], rho_s, cx, cy, Ux, Uy);
+        double cu = cx * Ux + cy * Uy;
+        double src = st->ws[i] * (3.0 * (cx - Ux) + 9.0 * cu * cx) * rho * a;
+        gpost[i] = (1.0 - 2.0 * b) * g[i] + 2.0 * b * ((1.0 - r) * fss + r * feq) + (1.0 - b) * src;
+      }
+      /* polymer, per Q-node */
+      for (int q = 0; q < nq; ++q) {
+        size_t nqq = n * nq + q;
+        double psi = st->psi[nqq];
+        double Qx = st->Qx[q], Qy = st->Qy[q];
+        double jrex = psi * Ux + tau1 * st->dq[nqq * 2];
+        double jrey = psi * Uy + tau1 * st->dq[nqq * 2 + 1];
+        double jqex = psi * (Qx * G00 + Qy * G10 - kappa * st->phi[q] * Qx);
+        double jqey = psi * (Qx * G01 + Qy * G11 - kappa * st->phi[q] * Qy);
+        const double* f = st->gp + nqq * 25;
+        double* fpost = st->gp_post + nqq * 25;
+        /* second moments of g: P^r (vv), P^rQ (v Qdot), P^Q (Qdot Qdot); c = (vx, vy, Qx', Qy') */
+        double P[4][4];
+        for (int u = 0; u < 4; ++u)
+          for (int v = 0; v < 4; ++v) P[u][v] = 0.0;
+        for (int i = 0; i < 25; ++i)
+          for (int u = 0; u < 4; ++u)
+            for (int v = 0; v < 4; ++v) P[u][v] += f[i] * st->cp[i][u] * st->cp[i][v];
+        /* P(f) = (2 tau2 P(g) + P_eq) / (2 tau2 + 1), P_eq = psi c_s^2 I (linear equilibrium) */
+        for (int u = 0; u < 4; ++u)
+          for (int v = 0; v < 4; ++v) P[u][v] = (c2 * P[u][v] + (u == v ? psi * cs2 : 0.0)) / (c2 + 1.0);
+        for (int i = 0; i < 25; ++i) {
+          const int* c = st->cp[i];
+          /* (P^r - psi c_s^2 I):(vv - c_s^2 I) / (2 c_s^4) + (P^Q - psi c_s^2 I):(QQ - c_s^2 I) / (2 c_s^4)
+             + P^rQ : (v Qdot) / c_s^4 */
+          double sdiag = 0.0, scross = 0.0;
+          for (int blk = 0; blk < 2; ++blk)
+            for (int u = 2 * blk; u < 2 * blk + 2; ++u)
+              for (int v = 2 * blk; v < 2 * blk + 2; ++v)
+                sdiag += (P[u][v] - (u == v ? psi * cs2 : 0.0)) * (c[u] * c[v] - (u == v ? cs2 : 0.0));
+          for (int u = 0; u < 2; ++u)
+            for (int v = 2; v < 4; ++v) scross += P[u][v] * c[u] * c[v];
+          double fss = feq_polymer(st->wp[i], psi, c, jrex, jrey, jqex, jqey) +
+                       st->wp[i] * (4.5 * sdiag + 9.0 * scross);
+          double feq = feq_polymer(st->wp[i], psi, c, jrex, jrey, jqex, jqey);
+          fpost[i] = (1.0 - 2.0 * b) * f[i] + 2.0 * b * ((1.0 - r) * fss + r * feq);
         }
       }
     }

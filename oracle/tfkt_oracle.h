@@ -33,6 +33,8 @@ typedef struct {
   double tau2;             /* momentum relaxation time; <= 0 -> tau2 = tau1 */
   double ell;              /* Q-lattice spacing in r-lengths; <= 0 -> sqrt(2) */
   double fene_b;           /* FENE extensibility b in units of kT/H; 0 -> Hookean */
+  int32_t qe_model;        /* 0: component momenta quasi-conserved (Sec. V, Eq. quasieq1);
+                              1: component stresses quasi-conserved (Eq. quasieq2) */
 } orc_phys;
 
 /* Lattice-unit parameters used by the step. */
@@ -50,6 +52,9 @@ typedef struct {
   double u0;               /* laminar amplitude (initial condition, mode 1) */
   double nu, nu_s, eta_p, lambda_h; /* reported, not used by the step */
   double fene_b;           /* FENE b (units of kT/H); 0 -> Hookean springs */
+  int32_t qe_model;        /* 0: momentum quasi-equilibrium (tau1 = stress, tau2 = momentum
+                              relaxation); 1: stress quasi-equilibrium (tau1 = momentum,
+                              tau2 = stress relaxation) */
 } orc_lattice;
 
 typedef struct orc_state orc_state;
