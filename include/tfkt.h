@@ -53,6 +53,15 @@ typedef enum {
                        updated in float; moment planes in float */
 } tfkt_precision;
 
+/* Quasi-equilibrium of the collision (Sec. V): which variables the fast
+   relaxation keeps. */
+typedef enum {
+  TFKT_QE_MOMENTUM = 0,  /* component momenta (Eq. quasieq1): the stress relaxes at tau1,
+                            the momenta at tau2 (Schmidt numbers up to Sc*) */
+  TFKT_QE_STRESS = 1     /* component stresses (Eq. quasieq2): the momenta relax at tau1,
+                            the stress at tau2 (Schmidt numbers from Sc* up) */
+} tfkt_qe_model;
+
 /* Physical description of one Kolmogorov run (Sec. VII definitions:
    Re = U0 l / nu, Wi = U0 lambda_H / l, beta = eta_s / (eta_s + eta_p),
    l = ny / (2 pi k_periods), forcing amplitude nu U0 / l^2). */
@@ -63,7 +72,9 @@ typedef struct {
   double re, wi, beta;   /* Re > 0; Wi >= 0 (Wi = 0 only with beta = 1); 0 < beta <= 1 */
   double u0;             /* laminar peak velocity, 0 < u0 <= 0.2 */
   int32_t k_periods;     /* forcing periods across ny, >= 1 */
-  double tau2;           /* momentum relaxation time; <= 0 selects tau2 = tau1; else >= tau1 */
+  double tau2;           /* momentum relaxation time tau_m (drag, bead diffusion, Q-drift);
+                            <= 0 selects the stress relaxation time 3 beta nu; the momentum
+                            model needs tau_m >= 3 beta nu, the stress model tau_m <= 3 beta nu */
   double ell;            /* Q-lattice spacing in r-lengths; <= 0 selects sqrt(2) */
   int32_t ic_mode;       /* 0: start from rest; 1: start from the laminar profile */
   int32_t precision;     /* tfkt_precision */
@@ -75,12 +86,16 @@ typedef struct {
                             where the bead-force flux makes the node strongly
                             anti-diffusive in r, make the step unstable; keep the disk
                             well inside Q0. */
+  int32_t qe_model;      /* tfkt_qe_model: which variables the collision holds
+                            quasi-conserved (Sec. V); the stress model takes the
+                            two-pass kernels */
 } tfkt_params;
 
 /* Derived lattice parameters and layout of a context. */
 typedef struct {
   int32_t nx, ny, nq, precision;
-  double tau1, tau2;     /* stress and momentum relaxation times */
+  double tau1, tau2;     /* fast and slow relaxation times of the update (momentum model:
+                            stress, momentum; stress model: momentum, stress) */
   double H, kappa;       /* spring constant; Q-drift rate kappa = 2 H tau2 */
   double ell, psi_tot;   /* Q spacing; sum_q psi per r-node (psi counts beads) */
   double sigma_q2;       /* variance of the initial Gaussian in Q (Q lattice units) */
@@ -91,6 +106,7 @@ typedef struct {
   size_t pitch;          /* elements per stored row (>= nx, multiple of 32) */
   size_t bytes_per_node_step; /* algorithmic HBM bytes of one node update, fused model */
   double fene_b;         /* 0 for Hookean springs */
+  int32_t qe_model;
 } tfkt_info;
 
 typedef struct tfkt_ctx tfkt_ctx;

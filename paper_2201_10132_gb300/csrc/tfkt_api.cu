@@ -58,6 +58,8 @@ tfkt_status map_params(const tfkt_params* p, Lattice* L) {
     return fail(TFKT_EINVAL, "unknown precision");
   if (p->ic_mode != 0 && p->ic_mode != 1) return fail(TFKT_EINVAL, "ic_mode must be 0 or 1");
   if (!(p->fene_b >= 0)) return fail(TFKT_EINVAL, "fene_b must be >= 0 (0: Hookean)");
+  if (p->qe_model != TFKT_QE_MOMENTUM && p->qe_model != TFKT_QE_STRESS)
+    return fail(TFKT_EINVAL, "unknown qe_model");
   Lattice l;
   l.nx = p->nx;
   l.ny = p->ny;
@@ -66,23 +68,36 @@ tfkt_status map_params(const tfkt_params* p, Lattice* L) {
   l.ic_mode = p->ic_mode;
   l.precision = p->precision;
   l.fene_b = p->fene_b;
+  l.qe_model = p->qe_model;
   const double kf = 2.0 * M_PI * p->k_periods / p->ny;
   const double len = 1.0 / kf;
   l.kf = kf;
   l.u0 = p->u0;
   l.nu = p->u0 * len / p->re;
   l.nu_s = p->beta * l.nu;
-  l.tau1 = 3.0 * l.nu_s;
-  l.tau2 = p->tau2 > 0 ? p->tau2 : l.tau1;
-  if (l.tau2 < l.tau1) return fail(TFKT_EINVAL, "tau2 must be >= tau1 (tau1 = 3 beta nu)");
+  // the viscosity comes from the stress relaxation time tau_s = 3 nu_s, the drag and
+  // diffusion from the momentum relaxation time tau_m (tau2 input, default tau_s);
+  // the momentum model relaxes the stress first (tau1 = tau_s <= tau2 = tau_m), the
+  // stress model the momenta (tau1 = tau_m <= tau2 = tau_s), Sec. V
+  const double tau_s = 3.0 * l.nu_s;
+  l.tau_m = p->tau2 > 0 ? p->tau2 : tau_s;
+  if (l.qe_model == TFKT_QE_MOMENTUM) {
+    if (l.tau_m < tau_s) return fail(TFKT_EINVAL, "momentum model: tau2 must be >= 3 beta nu");
+    l.tau1 = tau_s;
+    l.tau2 = l.tau_m;
+  } else {
+    if (l.tau_m > tau_s) return fail(TFKT_EINVAL, "stress model: tau2 must be <= 3 beta nu");
+    l.tau1 = l.tau_m;
+    l.tau2 = tau_s;
+  }
   l.ell = p->ell > 0 ? p->ell : std::sqrt(2.0);
   l.eta_p = (1.0 - p->beta) * l.nu;
   l.a0 = l.nu * p->u0 * kf * kf;
   if (p->wi > 0) {
     l.lambda_h = p->wi * len / p->u0;
-    l.H = 1.0 / (4.0 * l.lambda_h * l.tau2);
-    l.kappa = 2.0 * l.H * l.tau2;
-    l.sigma_q2 = l.tau2 / (3.0 * l.kappa);
+    l.H = 1.0 / (4.0 * l.lambda_h * l.tau_m);
+    l.kappa = 2.0 * l.H * l.tau_m;
+    l.sigma_q2 = l.tau_m / (3.0 * l.kappa);
     l.psi_tot = l.eta_p / (0.5 * l.H * l.ell * l.ell * l.sigma_q2 * l.lambda_h);
   } else {
     l.lambda_h = 0;
@@ -153,7 +168,7 @@ size_t layout(const Lattice& L, Workspace* w) {
   o = align_up(o + (size_t)diag_blocks_for(L) * TFKT_NDIAG * sizeof(double), A);
   w->off_diag = o;
   o = align_up(o + TFKT_NDIAG * sizeof(double), A);
-  if (fused_supported(L.nx, L.ny, L.nq, sz)) {
+  if (L.qe_model == TFKT_QE_MOMENTUM && fused_supported(L.nx, L.ny, L.nq, sz)) {
     w->off_M2 = o;
     o = align_up(o + (size_t)L.nm * L.plane * sz, A);
     w->off_exp = o;
@@ -261,6 +276,8 @@ KernelArgs<real> make_args(const Ctx* c, const HostTables* ht = nullptr) {
   a.omr = (real)(1.0 - L.tau1 / L.tau2);
   a.kappa = (real)L.kappa;
   a.hl2h = (real)(0.5 * L.H * L.ell * L.ell);
+  a.tau_m = (real)L.tau_m;
+  a.qe = L.qe_model;
   a.rho0 = (real)(1.0 + L.psi_tot);
   a.psi_tot0 = (real)L.psi_tot;
   a.l2 = (real)(L.ell * L.ell);
@@ -596,7 +613,7 @@ tfkt_status tfkt_create(const tfkt_params* p, const double* perturb, void* dev_w
   if (!c) return fail(TFKT_ENOMEM, "host allocation failed");
   c->L = L;
   c->stream = (cudaStream_t)stream;
-  c->fused = fused_supported(L.nx, L.ny, L.nq, real_size(L));
+  c->fused = L.qe_model == TFKT_QE_MOMENTUM && fused_supported(L.nx, L.ny, L.nq, real_size(L));
   const size_t need = layout(L, &c->ws);
   c->diag_blocks = diag_blocks_for(L);
   if (dev_workspace) {
@@ -703,6 +720,7 @@ tfkt_status tfkt_get_info(const tfkt_ctx* c, tfkt_info* info) {
   i.eta_p = L.eta_p;
   i.lambda_h = L.lambda_h;
   i.fene_b = L.fene_b;
+  i.qe_model = L.qe_model;
   i.step = c->step;
   i.workspace_bytes = c->ws.bytes;
   i.pitch = L.pitch;

@@ -34,6 +34,8 @@ tfkt_status check_runs(const tfkt_params* runs, int32_t n, std::vector<Lattice>&
     tfkt_status s = map_params(&runs[i], &L[i]);
     if (s != TFKT_OK) return s;
     if (runs[i].precision != TFKT_FP32) return fail(TFKT_EINVAL, "batched runs must use TFKT_FP32");
+    if (runs[i].qe_model != TFKT_QE_MOMENTUM)
+      return fail(TFKT_EINVAL, "batched runs use the momentum quasi-equilibrium");
     if (!fused_supported(L[i].nx, L[i].ny, L[i].nq, 4))
       return fail(TFKT_EINVAL, "batched runs need nx % 32 == 0 and ny % 8 == 0 (run " +
                                    std::to_string(i) + ")");

@@ -64,6 +64,8 @@ struct Lattice {
   double a0 = 0, kf = 0, u0 = 0, nu = 0, nu_s = 0, eta_p = 0, lambda_h = 0;
   int ic_mode = 0, precision = 0;
   double fene_b = 0;  // 0: Hookean springs; > 0: FENE extensibility b
+  int qe_model = 0;   // tfkt_qe_model
+  double tau_m = 0;   // momentum relaxation time (drag, Q-drift, bead diffusion)
   size_t pitch = 0;   // elements per stored row
   size_t plane = 0;   // elements per plane (ny * pitch)
   int npl = 0;        // population planes: 9 + 25 nq
@@ -115,6 +117,8 @@ struct KernelArgs {
   real om2b, tb, omb;            // 1 - 2 beta, 2 beta, 1 - beta
   real r, omr;                   // tau1 / tau2, 1 - tau1 / tau2
   real kappa, hl2h;              // kappa, H ell^2 / 2
+  real tau_m;                    // momentum relaxation time (tau2, or tau1 in the stress model)
+  int qe;                        // tfkt_qe_model
   real rho0;                     // 1 + psi_tot: total density of the rest state
   real psi_tot0;
   real l2, H;

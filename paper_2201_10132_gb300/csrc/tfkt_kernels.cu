@@ -291,6 +291,139 @@ __global__ void __launch_bounds__(256) step_kernel(KernelArgs<real> a) {
   }
 }
 
+// The same step with the component stresses quasi-conserved (Sec. V, Eq.
+// quasieq2; f*_S and f**_P of Sec. VI): the targets carry the equilibrium
+// momenta (rho_S U; J^r_eq = psi U + tau1 D, J^Q_eq) and the current stresses
+// of f, P(f) = (2 tau2 P(g) + P_eq [+ tau2 (F U + U F) for the solvent]) /
+// (2 tau2 + 1), entered through the second-order Hermite terms normalised so
+// that <f**, vv> = P; momenta relax at tau1, stresses at tau2.
+template <typename real, typename S>
+__global__ void __launch_bounds__(256) step_stress_kernel(KernelArgs<real> a) {
+  __shared__ real sUx[TY + 2][TX + 2];
+  __shared__ real sUy[TY + 2][TX + 2];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  for (int k = tid; k < (TX + 2) * (TY + 2); k += TX * TY) {
+    const int hx = k % (TX + 2), hy = k / (TX + 2);
+    const int gx = wrapi(x0 - 1 + hx, a.nx), gy = wrapi(y0 - 1 + hy, a.ny);
+    real ux, uy, rho;
+    mixture_velocity(a, gx, gy, ux, uy, rho);
+    sUx[hy][hx] = ux;
+    sUy[hy][hx] = uy;
+  }
+  __syncthreads();
+  const int x = x0 + tx, y = y0 + ty;
+  if (x >= a.nx || y >= a.ny) return;
+  const real Ux = sUx[ty + 1][tx + 1], Uy = sUy[ty + 1][tx + 1];
+  const real G00 = real(0.5) * (sUx[ty + 1][tx + 2] - sUx[ty + 1][tx]);
+  const real G01 = real(0.5) * (sUy[ty + 1][tx + 2] - sUy[ty + 1][tx]);
+  const real G10 = real(0.5) * (sUx[ty + 2][tx + 1] - sUx[ty][tx + 1]);
+  const real G11 = real(0.5) * (sUy[ty + 2][tx + 1] - sUy[ty][tx + 1]);
+  const Offsets off = node_offsets(x, y, a.nx, a.ny, a.pitch);
+  const size_t P = a.plane;
+  const size_t n = off.o[4];
+  const int nq = a.nq;
+  const real rho = a.rho0 + a.M[(size_t)(nq + M_DRHO) * P + n];
+  const real force = rho * a.tab.arow[y];
+  const S* __restrict__ src = (const S*)a.src;
+  S* __restrict__ dst = (S*)a.dst;
+  const real cs2 = real(1) / real(3);
+  const real rmix = a.r, omr = a.omr;
+
+  // ---- solvent
+  {
+    real h[9];
+    real drs = 0, pxx = 0, pxy = 0, pyy = 0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      h[i] = from_store<real>(src[(size_t)i * P + off.o[shift_index(-c9x(i), -c9y(i))]]);
+      drs += h[i];
+      pxx += real(c9x(i) * c9x(i)) * h[i];
+      pxy += real(c9x(i) * c9y(i)) * h[i];
+      pyy += real(c9y(i) * c9y(i)) * h[i];
+    }
+    const real rs = real(1) + drs;
+    // P(g) = c_s^2 I + sum h c c (the rest state's stress is c_s^2 I)
+    pxx += cs2;
+    pyy += cs2;
+    const real fxx = (a.c2 * pxx + rs * (cs2 + Ux * Ux) + a.tau2 * real(2) * force * Ux) * a.inv_c2p1;
+    const real fxy = (a.c2 * pxy + rs * Ux * Uy + a.tau2 * force * Uy) * a.inv_c2p1;
+    const real fyy = (a.c2 * pyy + rs * (cs2 + Uy * Uy)) * a.inv_c2p1;
+    const real usq = Ux * Ux + Uy * Uy;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const real cx = real(c9x(i)), cy = real(c9y(i));
+      const real cu = cx * Ux + cy * Uy;
+      const real pneq = (fxx - rs * cs2) * (cx * cx - cs2) + real(2) * fxy * cx * cy +
+                        (fyy - rs * cs2) * (cy * cy - cs2);
+      const real fss_dev = real(w9(i)) * (drs + real(3) * rs * cu + real(4.5) * pneq);
+      const real feq_dev = real(w9(i)) * (drs + rs * (real(3) * cu + real(4.5) * cu * cu - real(1.5) * usq));
+      const real srcterm = real(w9(i)) * (real(3) * (cx - Ux) + real(9) * cu * cx) * force;
+      dst[(size_t)i * P + n] =
+          to_store<S>(a.om2b * h[i] + a.tb * (omr * fss_dev + rmix * feq_dev) + a.omb * srcterm);
+    }
+  }
+
+  // ---- polymer, one Q-node at a time
+  const size_t nxm = off.o[3], nxp = off.o[5], nym = off.o[1], nyp = off.o[7];
+  for (int q = 0; q < nq; ++q) {
+    const real* Mq = a.M + (size_t)q * P;
+    const real dpx = real(0.5) * (Mq[nxp] - Mq[nxm]);
+    const real dpy = real(0.5) * (Mq[nyp] - Mq[nym]);
+    real h[25];
+    real dpsi = 0;
+    // second moments of the deviations: vv (3), v Qdot (4), Qdot Qdot (3)
+    real rxx = 0, rxy = 0, ryy = 0, cxx = 0, cxy = 0, cyx = 0, cyy = 0, qxx = 0, qxy = 0, qyy = 0;
+#pragma unroll
+    for (int i = 0; i < 25; ++i) {
+      const V4 c = c25(i);
+      const int e = a.tab.pull[q * 25 + i];
+      const size_t o = e >= 0 ? off.o[shift_index(-c.rx, -c.ry)] : off.o[4];
+      const int p = e >= 0 ? e : ~e;
+      h[i] = from_store<real>(src[(size_t)p * P + o]) * a.pinv + a.tab.delta[q * 25 + i];
+      dpsi += h[i];
+      rxx += real(c.rx * c.rx) * h[i];
+      rxy += real(c.rx * c.ry) * h[i];
+      ryy += real(c.ry * c.ry) * h[i];
+      cxx += real(c.rx * c.qx) * h[i];
+      cxy += real(c.rx * c.qy) * h[i];
+      cyx += real(c.ry * c.qx) * h[i];
+      cyy += real(c.ry * c.qy) * h[i];
+      qxx += real(c.qx * c.qx) * h[i];
+      qxy += real(c.qx * c.qy) * h[i];
+      qyy += real(c.qy * c.qy) * h[i];
+    }
+    const real Qx = a.tab.qx[q], Qy = a.tab.qy[q], Fx = a.tab.fx[q], Fy = a.tab.fy[q];
+    const real psi0 = a.tab.psi0[q];
+    const real psi = psi0 + dpsi;
+    const real qg = Qx * dpx + Qy * dpy;
+    const real jrex = psi * Ux + a.tau_m * a.hl2h * Fx * qg;
+    const real jrey = psi * Uy + a.tau_m * a.hl2h * Fy * qg;
+    const real jqex = psi * (Qx * G00 + Qy * G10 - a.kappa * Fx);
+    const real jqey = psi * (Qx * G01 + Qy * G11 - a.kappa * Fy);
+    // P(g) = psi0 c_s^2 I + the deviations' moments; P(f) - psi c_s^2 I for the diagonal
+    // blocks, P(f) for the r-Q block, with P_eq = psi c_s^2 I
+    auto dg = [&](real m) { return (a.c2 * (psi0 * cs2 + m) + psi * cs2) * a.inv_c2p1 - psi * cs2; };
+    auto od = [&](real m) { return a.c2 * m * a.inv_c2p1; };
+    const real Rxx = dg(rxx), Rxy = od(rxy), Ryy = dg(ryy);
+    const real Qxx = dg(qxx), Qxy = od(qxy), Qyy = dg(qyy);
+    const real Cxx = od(cxx), Cxy = od(cxy), Cyx = od(cyx), Cyy = od(cyy);
+    S* dq = dst + (size_t)(9 + 25 * q) * P + n;
+#pragma unroll
+    for (int i = 0; i < 25; ++i) {
+      const V4 c = c25(i);
+      const real vx = real(c.rx), vy = real(c.ry), wx = real(c.qx), wy = real(c.qy);
+      const real lin = dpsi + real(3) * (jrex * vx + jrey * vy + jqex * wx + jqey * wy);
+      const real sdiag = Rxx * (vx * vx - cs2) + real(2) * Rxy * vx * vy + Ryy * (vy * vy - cs2) +
+                         Qxx * (wx * wx - cs2) + real(2) * Qxy * wx * wy + Qyy * (wy * wy - cs2);
+      const real scross = Cxx * vx * wx + Cxy * vx * wy + Cyx * vy * wx + Cyy * vy * wy;
+      const real fss_dev = real(w25(i)) * (lin + real(4.5) * sdiag + real(9) * scross);
+      const real feq_dev = real(w25(i)) * lin;
+      dq[(size_t)i * P] = to_store<S>((a.om2b * h[i] + a.tb * (omr * fss_dev + rmix * feq_dev)) * a.pscale);
+    }
+  }
+}
+
 // ------------------------------------------------------------- observers
 template <typename real>
 __global__ void __launch_bounds__(256) velocity_kernel(KernelArgs<real> a) {
@@ -454,7 +587,10 @@ cudaError_t launch_moments(const KernelArgs<real>& a, cudaStream_t s) {
 }
 template <typename real, typename S>
 cudaError_t launch_step(const KernelArgs<real>& a, cudaStream_t s) {
-  step_kernel<real, S><<<node_grid(a.nx, a.ny), dim3(TX, TY), 0, s>>>(a);
+  if (a.qe == TFKT_QE_STRESS)
+    step_stress_kernel<real, S><<<node_grid(a.nx, a.ny), dim3(TX, TY), 0, s>>>(a);
+  else
+    step_kernel<real, S><<<node_grid(a.nx, a.ny), dim3(TX, TY), 0, s>>>(a);
   return cudaGetLastError();
 }
 template <typename real>

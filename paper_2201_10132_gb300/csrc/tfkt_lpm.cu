@@ -400,6 +400,8 @@ tfkt_status check(Ctx* c, int K) {
   if (!c->fused) return fail(TFKT_EINVAL, "the learned block needs nx % 32 == 0 and ny % 8 == 0");
   if (!(L.psi_tot > 0)) return fail(TFKT_EINVAL, "the learned block needs a polymer (beta < 1)");
   if (L.fene_b != 0) return fail(TFKT_EINVAL, "the learned block is for Hookean springs");
+  if (L.qe_model != TFKT_QE_MOMENTUM)
+    return fail(TFKT_EINVAL, "the learned block uses the momentum quasi-equilibrium");
   if (L.nq < 4) return fail(TFKT_EINVAL, "the learned block needs at least 4 Q-nodes");
   if (K < 2 || K > 64 || (K & 1)) return fail(TFKT_EINVAL, "K must be even, 2 <= K <= 64");
   if (c->poisoned) return fail(TFKT_ESTATE, "context is poisoned by an earlier CUDA error");

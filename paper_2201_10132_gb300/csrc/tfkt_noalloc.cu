@@ -101,6 +101,8 @@ tfkt_status moments_noalloc(const Lattice& L, const void* pops, uint32_t mask, d
   a.tau2 = (real)L.tau2;
   a.kappa = (real)L.kappa;
   a.hl2h = (real)(0.5 * L.H * L.ell * L.ell);
+  a.tau_m = (real)L.tau_m;
+  a.qe = L.qe_model;
   a.rho0 = (real)(1.0 + L.psi_tot);
   a.psi_tot0 = (real)L.psi_tot;
   a.l2 = (real)(L.ell * L.ell);

@@ -36,7 +36,8 @@ class _Params(ctypes.Structure):
                 ("beta", ctypes.c_double), ("u0", ctypes.c_double),
                 ("k_periods", ctypes.c_int32), ("tau2", ctypes.c_double),
                 ("ell", ctypes.c_double), ("ic_mode", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("fene_b", ctypes.c_double)]
+                ("precision", ctypes.c_int32), ("fene_b", ctypes.c_double),
+                ("qe_model", ctypes.c_int32)]
 
 
 class _Info(ctypes.Structure):
@@ -48,7 +49,8 @@ class _Info(ctypes.Structure):
                 ("nu", ctypes.c_double), ("nu_s", ctypes.c_double), ("eta_p", ctypes.c_double),
                 ("lambda_h", ctypes.c_double), ("step", ctypes.c_int64),
                 ("workspace_bytes", ctypes.c_size_t), ("pitch", ctypes.c_size_t),
-                ("bytes_per_node_step", ctypes.c_size_t), ("fene_b", ctypes.c_double)]
+                ("bytes_per_node_step", ctypes.c_size_t), ("fene_b", ctypes.c_double),
+                ("qe_model", ctypes.c_int32)]
 
 
 class LpmOpts(ctypes.Structure):
@@ -58,6 +60,7 @@ class LpmOpts(ctypes.Structure):
 
 
 LPM_NET, LPM_FROZEN = 0, 1
+QE_MOMENTUM, QE_STRESS = 0, 1
 MLP_IN, MLP_HID, MLP_OUT = 40, 64, 3
 MLP_NWEIGHTS = MLP_HID * MLP_IN + MLP_HID + MLP_HID * MLP_HID + MLP_HID + MLP_OUT * MLP_HID + MLP_OUT
 MLP_NPARAM = MLP_NWEIGHTS + 2 * MLP_IN + 2 * MLP_OUT
@@ -80,6 +83,7 @@ class Params:
     ic_mode: int = 0
     precision: int = FP64
     fene_b: float = 0.0     # 0: Hookean springs; > 0: FENE extensibility b
+    qe_model: int = 0       # QE_MOMENTUM or QE_STRESS
 
     def _c(self) -> _Params:
         return _Params(*(getattr(self, f.name) for f in dc_fields(self)))

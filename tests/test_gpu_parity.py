@@ -31,8 +31,8 @@ def T():
     return tfkt
 
 
-def _oracle_run(O, nx, ny, S, R, re, wi, beta, kp, tau2, pert, ic, steps, fene_b=0.0):
-    lat = O.map_params(nx, ny, S, R, re, wi, beta, 0.05, kp, tau2, 0.0, fene_b)
+def _oracle_run(O, nx, ny, S, R, re, wi, beta, kp, tau2, pert, ic, steps, fene_b=0.0, qe=0):
+    lat = O.map_params(nx, ny, S, R, re, wi, beta, 0.05, kp, tau2, 0.0, fene_b, qe)
     o = O.Oracle(lat)
     o.init(pert, ic)
     o.step(steps)
@@ -65,22 +65,28 @@ CASES = [
     (70, 19, 8, 4.0, 5.0, 4.0, 0.2, 1, 0.0, 0, 12, 7.5),     # two-pass path, ragged
     (64, 32, 6, 3.0, 5.0, 2.0, 0.2, 1, 0.0, 1, 12, 3.1),     # fused path
     (64, 32, 6, 3.0, 5.0, 2.0, 0.5, 1, 0.3, 1, 12, 3.1),     # fused, tau2 > tau1
+    # stress quasi-equilibrium (last entry 1; tau2 is then the faster momentum time):
+    # always the two-pass kernels
+    (24, 16, 6, 3.0, 5.0, 0.5, 0.2, 1, 0.01, 1, 15, 0.0, 1),
+    (64, 32, 6, 3.0, 5.0, 2.0, 0.5, 1, 0.03, 1, 12, 0.0, 1),   # a grid the fused path would take
+    (33, 9, 4, 2.0, 3.0, 0.0, 1.0, 1, 0.05, 1, 10, 0.0, 1),    # Newtonian
 ]
-FUSED = [c for c in CASES if c[0] % 32 == 0 and c[1] % 8 == 0]
-FENE = [c for c in CASES if len(c) > 11]
+FUSED = [c for c in CASES if c[0] % 32 == 0 and c[1] % 8 == 0 and (len(c) < 13 or c[12] == 0)]
+FENE = [c for c in CASES if len(c) > 11 and c[11] > 0]
+STRESS = [c for c in CASES if len(c) > 12 and c[12] == 1]
 
 
 def _case(case):
-    """(nx, ny, S, R, re, wi, beta, kp, tau2, ic, steps, fene_b)."""
-    return tuple(case) + (0.0,) * (12 - len(case))
+    """(nx, ny, S, R, re, wi, beta, kp, tau2, ic, steps, fene_b, qe_model)."""
+    return tuple(case) + (0.0, 0)[len(case) - 11:] if len(case) < 13 else tuple(case)
 
 
-@pytest.mark.parametrize("case", [CASES[2], CASES[7], FENE[0], FENE[1]])
+@pytest.mark.parametrize("case", [CASES[2], CASES[7], FENE[0], FENE[1], STRESS[1]])
 def test_path_dispatch(T, case):
     """Tile-multiple grids run the fused kernel plus its border fix-up; others the
     moments + step pair."""
-    nx, ny, S, R, re, wi, beta, kp, tau2, ic, steps, fb = _case(case)
-    p = T.Params(nx, ny, S, R, re, wi, beta, 0.05, kp, tau2, 0.0, ic, T.FP64, fb)
+    nx, ny, S, R, re, wi, beta, kp, tau2, ic, steps, fb, qe = _case(case)
+    p = T.Params(nx, ny, S, R, re, wi, beta, 0.05, kp, tau2, 0.0, ic, T.FP64, fb, qe)
     ms = np.zeros(len(T.KERNELS))
     n = np.zeros(len(T.KERNELS), np.int64)
     with T.Solver(p) as s:
@@ -96,10 +102,10 @@ def test_path_dispatch(T, case):
 @pytest.mark.parametrize("case", CASES)
 def test_fp64_matches_oracle(T, oracle_mod, case):
     from paper_2201_10132_gb300.inputs import perturbation
-    nx, ny, S, R, re, wi, beta, kp, tau2, ic, steps, fb = _case(case)
+    nx, ny, S, R, re, wi, beta, kp, tau2, ic, steps, fb, qe = _case(case)
     pert = perturbation(nx, ny, 7, 0.05, 0.05) if nx * ny > 1 else None
-    p = T.Params(nx, ny, S, R, re, wi, beta, 0.05, kp, tau2, 0.0, ic, T.FP64, fb)
-    o = _oracle_run(oracle_mod, nx, ny, S, R, re, wi, beta, kp, tau2, pert, ic, steps, fb)
+    p = T.Params(nx, ny, S, R, re, wi, beta, 0.05, kp, tau2, 0.0, ic, T.FP64, fb, qe)
+    o = _oracle_run(oracle_mod, nx, ny, S, R, re, wi, beta, kp, tau2, pert, ic, steps, fb, qe)
     with T.Solver(p, pert) as s:
         assert s.info["nq"] == o.nq
         s.step(steps)
@@ -130,13 +136,14 @@ def test_fp64_matches_oracle(T, oracle_mod, case):
         assert diag[k] == pytest.approx(od[k], rel=1e-9, abs=1e-13 * max(1.0, od["mass_s"])), k
 
 
-@pytest.mark.parametrize("case", [CASES[1], CASES[2], CASES[3], CASES[7], CASES[9], FENE[1]])
+@pytest.mark.parametrize("case", [CASES[1], CASES[2], CASES[3], CASES[7], CASES[9], FENE[1],
+                                  STRESS[0], STRESS[1]])
 def test_fp32_within_tolerance(T, oracle_mod, case):
     from paper_2201_10132_gb300.inputs import perturbation
-    nx, ny, S, R, re, wi, beta, kp, tau2, ic, steps, fb = _case(case)
+    nx, ny, S, R, re, wi, beta, kp, tau2, ic, steps, fb, qe = _case(case)
     pert = perturbation(nx, ny, 7, 0.05, 0.05)
-    p = T.Params(nx, ny, S, R, re, wi, beta, 0.05, kp, tau2, 0.0, ic, T.FP32, fb)
-    o = _oracle_run(oracle_mod, nx, ny, S, R, re, wi, beta, kp, tau2, pert, ic, steps, fb)
+    p = T.Params(nx, ny, S, R, re, wi, beta, 0.05, kp, tau2, 0.0, ic, T.FP32, fb, qe)
+    o = _oracle_run(oracle_mod, nx, ny, S, R, re, wi, beta, kp, tau2, pert, ic, steps, fb, qe)
     with T.Solver(p, pert) as s:
         s.step(steps)
         g = s.moments()
@@ -157,10 +164,10 @@ def test_fp16_storage_within_tolerance(T, oracle_mod, case):
     (~0.15 w_i) summed over ~25 nq + 9 terms; allowed: 3e-3 of the velocity
     scale and 3e-3 of each other field's largest magnitude for n <= 25."""
     from paper_2201_10132_gb300.inputs import perturbation
-    nx, ny, S, R, re, wi, beta, kp, tau2, ic, steps, fb = _case(case)
+    nx, ny, S, R, re, wi, beta, kp, tau2, ic, steps, fb, qe = _case(case)
     pert = perturbation(nx, ny, 7, 0.05, 0.05)
-    p = T.Params(nx, ny, S, R, re, wi, beta, 0.05, kp, tau2, 0.0, ic, T.FP16, fb)
-    o = _oracle_run(oracle_mod, nx, ny, S, R, re, wi, beta, kp, tau2, pert, ic, steps, fb)
+    p = T.Params(nx, ny, S, R, re, wi, beta, 0.05, kp, tau2, 0.0, ic, T.FP16, fb, qe)
+    o = _oracle_run(oracle_mod, nx, ny, S, R, re, wi, beta, kp, tau2, pert, ic, steps, fb, qe)
     with T.Solver(p, pert) as s:
         s.step(steps)
         g = s.moments()
