@@ -343,19 +343,19 @@ __global__ void __launch_bounds__(256) step_stress_kernel(KernelArgs<real> a) {
       pyy += real(c9y(i) * c9y(i)) * h[i];
     }
     const real rs = real(1) + drs;
-    // P(g) = c_s^2 I + sum h c c (the rest state's stress is c_s^2 I)
-    pxx += cs2;
-    pyy += cs2;
-    const real fxx = (a.c2 * pxx + rs * (cs2 + Ux * Ux) + a.tau2 * real(2) * force * Ux) * a.inv_c2p1;
-    const real fxy = (a.c2 * pxy + rs * Ux * Uy + a.tau2 * force * Uy) * a.inv_c2p1;
-    const real fyy = (a.c2 * pyy + rs * (cs2 + Uy * Uy)) * a.inv_c2p1;
+    // P(g) - P_eq from the deviations (P(g) = c_s^2 I + sum h c c, P_eq = rho_S (c_s^2 I + U U)),
+    // then P(f) - rho_S c_s^2 I = [2 tau2 (P(g) - P_eq) + tau2 (F U + U F)] / (2 tau2 + 1) + rho_S U U
+    const real dxx = pxx - drs * cs2 - rs * Ux * Ux, dxy = pxy - rs * Ux * Uy;
+    const real dyy = pyy - drs * cs2 - rs * Uy * Uy;
+    const real fxx = (a.c2 * dxx + a.tau2 * real(2) * force * Ux) * a.inv_c2p1 + rs * Ux * Ux;
+    const real fxy = (a.c2 * dxy + a.tau2 * force * Uy) * a.inv_c2p1 + rs * Ux * Uy;
+    const real fyy = a.c2 * dyy * a.inv_c2p1 + rs * Uy * Uy;
     const real usq = Ux * Ux + Uy * Uy;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       const real cx = real(c9x(i)), cy = real(c9y(i));
       const real cu = cx * Ux + cy * Uy;
-      const real pneq = (fxx - rs * cs2) * (cx * cx - cs2) + real(2) * fxy * cx * cy +
-                        (fyy - rs * cs2) * (cy * cy - cs2);
+      const real pneq = fxx * (cx * cx - cs2) + real(2) * fxy * cx * cy + fyy * (cy * cy - cs2);
       const real fss_dev = real(w9(i)) * (drs + real(3) * rs * cu + real(4.5) * pneq);
       const real feq_dev = real(w9(i)) * (drs + rs * (real(3) * cu + real(4.5) * cu * cu - real(1.5) * usq));
       const real srcterm = real(w9(i)) * (real(3) * (cx - Ux) + real(9) * cu * cx) * force;
@@ -394,16 +394,15 @@ __global__ void __launch_bounds__(256) step_stress_kernel(KernelArgs<real> a) {
       qyy += real(c.qy * c.qy) * h[i];
     }
     const real Qx = a.tab.qx[q], Qy = a.tab.qy[q], Fx = a.tab.fx[q], Fy = a.tab.fy[q];
-    const real psi0 = a.tab.psi0[q];
-    const real psi = psi0 + dpsi;
+    const real psi = a.tab.psi0[q] + dpsi;
     const real qg = Qx * dpx + Qy * dpy;
     const real jrex = psi * Ux + a.tau_m * a.hl2h * Fx * qg;
     const real jrey = psi * Uy + a.tau_m * a.hl2h * Fy * qg;
     const real jqex = psi * (Qx * G00 + Qy * G10 - a.kappa * Fx);
     const real jqey = psi * (Qx * G01 + Qy * G11 - a.kappa * Fy);
-    // P(g) = psi0 c_s^2 I + the deviations' moments; P(f) - psi c_s^2 I for the diagonal
-    // blocks, P(f) for the r-Q block, with P_eq = psi c_s^2 I
-    auto dg = [&](real m) { return (a.c2 * (psi0 * cs2 + m) + psi * cs2) * a.inv_c2p1 - psi * cs2; };
+    // P(g) - P_eq = (the deviations' moments) - dpsi c_s^2 I on the diagonal blocks (P_eq =
+    // psi c_s^2 I), so P(f) - P_eq = 2 tau2 (P(g) - P_eq) / (2 tau2 + 1)
+    auto dg = [&](real m) { return a.c2 * (m - dpsi * cs2) * a.inv_c2p1; };
     auto od = [&](real m) { return a.c2 * m * a.inv_c2p1; };
     const real Rxx = dg(rxx), Rxy = od(rxy), Ryy = dg(ryy);
     const real Qxx = dg(qxx), Qxy = od(qxy), Qyy = dg(qyy);

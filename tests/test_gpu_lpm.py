@@ -269,3 +269,15 @@ def test_pending_increment_flush_equals_fused_pull(T, L, oracle_mod):
         scale = np.abs(out[0][k]).max()
         assert np.abs(out[0][k] - out[1][k]).max() <= 1e-5 * scale, k
     m.close()
+
+
+def test_paper_run_low_weissenberg(T):
+    """The paper's 72^2 run at Wi = 0.1 (Sec. VII): the inflectional instability lowers
+    the enstrophy from its laminar plateau early on, and the polymer stays at its
+    equilibrium extension, Q_rms ~ 0.2 of the maximum extension sqrt(b)."""
+    from paper_2201_10132_gb300 import paper_run
+    r = paper_run.run(0.1, 150.0, 5.0)
+    s = paper_run.summarise(r)
+    assert r["blowup_time"] is None
+    assert s["onset_time"] is not None and 20 < s["onset_time"] < 120, s
+    assert 0.15 < s["qrms_over_q0_late"] < 0.25, s
