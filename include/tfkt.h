@@ -249,7 +249,11 @@ tfkt_status tfkt_batch_required_bytes(const tfkt_params* runs, int32_t n, size_t
 /* Create n runs. perturbs: n host pointers to [2][ny][nx] perturbations (or
    NULL entries, or perturbs NULL). dev_workspace/bytes as in tfkt_create. The
    batch uses the caller's stream if it is not NULL, else one it creates (a CUDA
-   graph cannot capture the legacy default stream). */
+   graph cannot capture the legacy default stream). Before the runs are
+   initialised, the batch times a few steps of its launch at each tile height
+   (4, 8 and 16 rows of 32 nodes) that every run supports and keeps the fastest;
+   the environment variable TFKT_BATCH_TILE_HEIGHT (4, 8 or 16) fixes the height
+   instead (EINVAL if a run does not support it). */
 tfkt_status tfkt_batch_create(const tfkt_params* runs, int32_t n, const double* const* perturbs,
                               void* dev_workspace, size_t workspace_bytes, void* stream,
                               tfkt_batch** out);
@@ -261,6 +265,10 @@ tfkt_status tfkt_batch_step(tfkt_batch* b, int64_t n);
    tfkt_psi, tfkt_populations and tfkt_get_info; owned by the batch: do not
    call tfkt_step or tfkt_destroy on it. */
 tfkt_status tfkt_batch_run(tfkt_batch* b, int32_t i, tfkt_ctx** run);
+
+/* The batch's tile height, and (ms: float[3] or NULL) the timed milliseconds per
+   step at heights 4, 8 and 16 (NaN where not timed). */
+tfkt_status tfkt_batch_tile_height(const tfkt_batch* b, int32_t* ty, float* ms);
 
 tfkt_status tfkt_batch_destroy(tfkt_batch* b);
 

@@ -172,7 +172,7 @@ size_t layout(const Lattice& L, Workspace* w) {
     w->off_M2 = o;
     o = align_up(o + (size_t)L.nm * L.plane * sz, A);
     w->off_exp = o;
-    o = align_up(o + fused_export_elems(L.nx, L.ny, L.nq) * sz, A);
+    o = align_up(o + fused_export_capacity(L.nx, L.ny, L.nq) * sz, A);
     w->off_ftab = o;
     o = align_up(o + (size_t)L.nq * (9 * sizeof(int) + sz + 25 * sizeof(long long)) + 2 * A, A);
   }
@@ -584,6 +584,14 @@ FusedArgs<real> ctx_fused(const Ctx* c) {
 }
 template KernelArgs<float> ctx_args<float>(const Ctx*);
 template FusedArgs<float> ctx_fused<float>(const Ctx*);
+tfkt_status ctx_reinit(Ctx* c, const double* perturb) {
+  c->cur = 0;
+  c->mcur = 0;
+  c->step = 0;
+  c->lpm_pending = false;
+  c->lpm_step = -1;
+  return DISPATCH(c, init_state, c, perturb);
+}
 tfkt_status ctx_ensure_moments_f32(Ctx* c) {
   if (c->L.precision != TFKT_FP32) return fail(TFKT_EINVAL, "FP32 context expected");
   return ensure_moments<float, float>(c);

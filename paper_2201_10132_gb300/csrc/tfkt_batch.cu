@@ -1,7 +1,12 @@
 // Batched ensembles: independent runs sharing one launch of the fused kernel
-// (and one of its border fix-up) per step, replayed from a CUDA graph.
+// (and one of its border fix-up) per step, replayed from a CUDA graph. The
+// tile height of that launch (4, 8 or 16 rows of 32 nodes) is chosen by
+// timing each candidate on the batch itself before the runs are initialised.
 #include <cuda_runtime.h>
 
+#include <cmath>
+#include <cstdlib>
+#include <limits>
 #include <new>
 #include <string>
 #include <vector>
@@ -20,6 +25,9 @@ struct tfkt_batch {
   int parity = 0;                          // buffer parity shared by all runs
   cudaGraphExec_t graph = nullptr;         // two steps: parity 0 then 1
   int64_t step = 0;
+  int ty = tfkt::TY;                       // tile height of the launch
+  float tune_ms[3] = {NAN, NAN, NAN};      // timed ms per step for heights 4, 8, 16
+  std::vector<tfkt::BatchRun<float>> host; // launch tables of the chosen height
 };
 
 namespace tfkt {
@@ -36,7 +44,10 @@ tfkt_status check_runs(const tfkt_params* runs, int32_t n, std::vector<Lattice>&
     if (runs[i].precision != TFKT_FP32) return fail(TFKT_EINVAL, "batched runs must use TFKT_FP32");
     if (runs[i].qe_model != TFKT_QE_MOMENTUM)
       return fail(TFKT_EINVAL, "batched runs use the momentum quasi-equilibrium");
-    if (!fused_supported(L[i].nx, L[i].ny, L[i].nq, 4))
+    // Every run must take the single-run fused path (8-row tiles): its context
+    // then holds the export ring, the second moment buffer and the fused tables
+    // that the batch kernels use at any tile height.
+    if (!fused_supported(L[i].nx, L[i].ny, L[i].nq, 4, 8))
       return fail(TFKT_EINVAL, "batched runs need nx % 32 == 0 and ny % 8 == 0 (run " +
                                    std::to_string(i) + ")");
   }
@@ -68,9 +79,94 @@ void release(tfkt_batch* b) {
 
 tfkt_status plain_step(tfkt_batch* b) {
   cudaError_t e = launch_batch_step(b->d_runs, b->d_tile_start, (int)b->runs.size(),
-                                    b->total_tiles, b->max_nq, b->parity, b->stream);
+                                    b->total_tiles, b->max_nq, b->parity, b->stream, b->ty);
   if (e != cudaSuccess) return fail(TFKT_ECUDA, std::string("batch step: ") + cudaGetErrorString(e));
   b->parity ^= 1;
+  return TFKT_OK;
+}
+
+// Launch tables (ntx, nty per run, prefix sums of the tile counts) for tile height ty.
+cudaError_t set_tables(tfkt_batch* b, const std::vector<Lattice>& L, int ty) {
+  const int n = (int)b->runs.size();
+  std::vector<int> tile_start(n + 1, 0);
+  for (int i = 0; i < n; ++i) {
+    b->host[i].ntx = L[i].nx / TX;
+    b->host[i].nty = L[i].ny / ty;
+    tile_start[i + 1] = tile_start[i] + b->host[i].ntx * b->host[i].nty;
+  }
+  b->total_tiles = tile_start[n];
+  b->ty = ty;
+  cudaError_t e = cudaMemcpyAsync(b->d_runs, b->host.data(), n * sizeof(BatchRun<float>),
+                                  cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_tile_start, tile_start.data(), (n + 1) * sizeof(int),
+                        cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = prepare_batch(b->max_nq, ty);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);   // host tables are pageable
+  return e;
+}
+
+// Tile heights every run supports (the grid divides, the tile's shared memory fits).
+std::vector<int> candidates(const std::vector<Lattice>& L) {
+  std::vector<int> out;
+  for (int ty : {4, 8, 16}) {
+    bool ok = true;
+    for (const Lattice& l : L) ok = ok && fused_supported(l.nx, l.ny, l.nq, 4, ty);
+    if (ok) out.push_back(ty);
+  }
+  return out;
+}
+
+// Time `steps` batch steps at each candidate height on the current states (the
+// runs are initialised afterwards, so the states timed here are thrown away);
+// keep the fastest. TFKT_BATCH_TILE_HEIGHT (4, 8 or 16) skips the timing.
+tfkt_status autotune(tfkt_batch* b, const std::vector<Lattice>& L) {
+  const std::vector<int> cand = candidates(L);
+  const char* env = std::getenv("TFKT_BATCH_TILE_HEIGHT");
+  const int forced = env ? std::atoi(env) : 0;
+  if (forced) {
+    for (int ty : cand)
+      if (ty == forced) {
+        cudaError_t e = set_tables(b, L, ty);
+        if (e != cudaSuccess) return fail(TFKT_ECUDA, std::string("batch tables: ") + cudaGetErrorString(e));
+        return TFKT_OK;
+      }
+    return fail(TFKT_EINVAL, "TFKT_BATCH_TILE_HEIGHT names a height these runs do not support");
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(TFKT_ECUDA, "cudaEventCreate");
+  int best = -1;
+  float best_ms = std::numeric_limits<float>::infinity();
+  cudaError_t e = cudaSuccess;
+  for (int ty : cand) {
+    e = set_tables(b, L, ty);
+    if (e != cudaSuccess) break;
+    const int warm = 1, steps = 4;
+    for (int k = 0; k < warm + steps && e == cudaSuccess; ++k) {
+      if (k == warm) e = cudaEventRecord(e0, b->stream);
+      if (e == cudaSuccess)
+        e = launch_batch_step(b->d_runs, b->d_tile_start, (int)b->runs.size(), b->total_tiles,
+                              b->max_nq, b->parity, b->stream, ty);
+      b->parity ^= 1;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) break;
+    ms /= steps;
+    b->tune_ms[ty == 4 ? 0 : (ty == 8 ? 1 : 2)] = ms;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = ty;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e == cudaSuccess && best > 0) e = set_tables(b, L, best);
+  if (e != cudaSuccess) return fail(TFKT_ECUDA, std::string("batch tuning: ") + cudaGetErrorString(e));
+  b->parity = 0;
   return TFKT_OK;
 }
 
@@ -131,12 +227,11 @@ tfkt_status tfkt_batch_create(const tfkt_params* runs, int32_t n, const double* 
     }
     b->own_stream = true;
   }
-  std::vector<BatchRun<float>> host(n);
-  std::vector<int> tile_start(n + 1, 0);
+  b->host.resize(n);
   for (int32_t i = 0; i < n; ++i) {
     tfkt_ctx* c = nullptr;
-    s = tfkt_create(&runs[i], perturbs ? perturbs[i] : nullptr, (char*)b->ws + off[i],
-                    ctx_layout(L[i]), b->stream, &c);
+    // rest state first: the tile-height timing below runs on it
+    s = tfkt_create(&runs[i], nullptr, (char*)b->ws + off[i], ctx_layout(L[i]), b->stream, &c);
     if (s != TFKT_OK) {
       release(b);
       return s;
@@ -145,27 +240,24 @@ tfkt_status tfkt_batch_create(const tfkt_params* runs, int32_t n, const double* 
     Ctx* x = ctx_of(c);
     for (int p = 0; p < 2; ++p) {
       x->cur = x->mcur = p;
-      host[i].a[p] = ctx_args<float>(x);
-      host[i].f[p] = ctx_fused<float>(x);
+      b->host[i].a[p] = ctx_args<float>(x);
+      b->host[i].f[p] = ctx_fused<float>(x);
     }
     x->cur = x->mcur = 0;
-    host[i].ntx = L[i].nx / TX;
-    host[i].nty = L[i].ny / TY;
-    tile_start[i + 1] = tile_start[i] + host[i].ntx * host[i].nty;
     if (L[i].nq > b->max_nq) b->max_nq = L[i].nq;
   }
-  b->total_tiles = tile_start[n];
   b->d_runs = (BatchRun<float>*)((char*)b->ws + off_tab);
   b->d_tile_start = (int*)((char*)b->ws + align256(off_tab + n * sizeof(BatchRun<float>)));
-  cudaError_t e = cudaMemcpy(b->d_runs, host.data(), n * sizeof(BatchRun<float>),
-                             cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(b->d_tile_start, tile_start.data(), (n + 1) * sizeof(int),
-                   cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = prepare_batch(b->max_nq);
-  if (e != cudaSuccess) {
+  if ((s = autotune(b, L)) != TFKT_OK) {
     release(b);
-    return fail(TFKT_ECUDA, std::string("batch tables: ") + cudaGetErrorString(e));
+    return s;
+  }
+  // the runs' initial states (Sec. VI-D), now that the timing steps are done
+  for (int32_t i = 0; i < n; ++i) {
+    if ((s = ctx_reinit(ctx_of(b->runs[i]), perturbs ? perturbs[i] : nullptr)) != TFKT_OK) {
+      release(b);
+      return s;
+    }
   }
   *out = b;
   return TFKT_OK;
@@ -186,9 +278,9 @@ tfkt_status tfkt_batch_step(tfkt_batch* b, int64_t n) {
     cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
       cudaError_t e1 = launch_batch_step(b->d_runs, b->d_tile_start, (int)b->runs.size(),
-                                         b->total_tiles, b->max_nq, 0, b->stream);
+                                         b->total_tiles, b->max_nq, 0, b->stream, b->ty);
       cudaError_t e2 = launch_batch_step(b->d_runs, b->d_tile_start, (int)b->runs.size(),
-                                         b->total_tiles, b->max_nq, 1, b->stream);
+                                         b->total_tiles, b->max_nq, 1, b->stream, b->ty);
       e = cudaStreamEndCapture(b->stream, &g);
       if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : e2;
     }
@@ -217,6 +309,14 @@ tfkt_status tfkt_batch_run(tfkt_batch* b, int32_t i, tfkt_ctx** run) {
   if (!b || !run || i < 0 || i >= (int32_t)b->runs.size())
     return fail(TFKT_EINVAL, "bad batch, run index or output pointer");
   *run = b->runs[i];
+  return TFKT_OK;
+}
+
+tfkt_status tfkt_batch_tile_height(const tfkt_batch* b, int32_t* ty, float* ms) {
+  if (!b || !ty) return fail(TFKT_EINVAL, "NULL argument");
+  *ty = b->ty;
+  if (ms)
+    for (int k = 0; k < 3; ++k) ms[k] = b->tune_ms[k];
   return TFKT_OK;
 }
 

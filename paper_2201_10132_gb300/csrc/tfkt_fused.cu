@@ -16,6 +16,7 @@
 // M planes written for step n+1: interior nodes get final values (delta psi,
 // delta rho, J, delta Theta); border nodes get the tile's raw partial sums in
 // the delta psi, delta rho and J planes, completed by the fix-up kernel.
+#include <algorithm>
 #include <type_traits>
 #include <utility>
 
@@ -35,21 +36,32 @@ __device__ __forceinline__ void static_for(F&& f) {
   static_for_impl<B>(f, std::make_integer_sequence<int, N>{});
 }
 
-constexpr int NT = TX * TY;                  // threads / nodes per tile
-constexpr int RING = 2 * (TX + 2) + 2 * TY;  // ring nodes around a tile
+// Tile geometry for a tile height H (the width is one warp, TX): threads /
+// nodes per tile, ring nodes around it, the exchange buffer's rows and plane.
+// The single-run path uses H = TY; batches pick H by timing (tfkt_batch.cu).
+template <int H>
+struct Geo {
+  static constexpr int NT = TX * H;
+  static constexpr int RING = 2 * (TX + 2) + 2 * H;
+  static constexpr int HY = H + 4;
+  static constexpr int HSZ = (TX + 4) * (H + 4);
+  static constexpr int MINB = NT >= 512 ? 1 : 512 / NT;   // blocks per SM at 128 registers
+};
 
-// Ring position of frame coordinates (ex, ey) in [-1, TX] x [-1, TY] \ tile.
+// Ring position of frame coordinates (ex, ey) in [-1, TX] x [-1, H] \ tile.
+template <int H>
 __host__ __device__ constexpr int ring_pos(int ex, int ey) {
   return ey == -1 ? ex + 1
-       : ey == TY ? TX + 3 + ex
+       : ey == H ? TX + 3 + ex
        : ex == -1 ? 2 * TX + 4 + ey
-                  : 2 * TX + 4 + TY + ey;
+                  : 2 * TX + 4 + H + ey;
 }
+template <int H>
 __device__ __forceinline__ void ring_coords(int k, int& ex, int& ey) {
   if (k < TX + 2) { ex = k - 1; ey = -1; }
-  else if (k < 2 * TX + 4) { ex = k - (TX + 3); ey = TY; }
-  else if (k < 2 * TX + 4 + TY) { ex = -1; ey = k - (2 * TX + 4); }
-  else { ex = TX; ey = k - (2 * TX + 4 + TY); }
+  else if (k < 2 * TX + 4) { ex = k - (TX + 3); ey = H; }
+  else if (k < 2 * TX + 4 + H) { ex = -1; ey = k - (2 * TX + 4); }
+  else { ex = TX; ey = k - (2 * TX + 4 + H); }
 }
 
 // Q-displacement group of a velocity: (qy + 1) * 3 + (qx + 1); 4 = no Q motion.
@@ -99,8 +111,6 @@ __device__ __forceinline__ void load_vec(T* out, const T* src) {
 }
 
 constexpr int HX = TX + 4;       // exchange-buffer row: the tile plus a 2-node zero halo
-constexpr int HY = TY + 4;
-constexpr int HSZ = HX * HY;     // one velocity's plane in the exchange buffer
 constexpr int DQ = 28;           // per-Q-node stride of the shift table (vector loads)
 constexpr int GQ = 12;           // per-Q-node stride of the target table (vector loads)
 
@@ -109,23 +119,23 @@ struct Smem {
   real* hb;          // [20][HY][HX] collided values of the r-moving velocities, zero halo
   real* A;           // [nq][NT] own-node arrival sums per Q-node
   real* Ar;          // [nq][RING] ring-node arrival sums per Q-node
-  real* Ux;          // [TY+2][TX+2]
+  real* Ux;          // [H+2][TX+2]
   real* Uy;
   long long* poff;   // [nq*25] element offset of each pull's source plane
   real* delta;       // [nq][DQ] pull shift differences
   int* tgt;          // [nq][GQ] target Q-node of each Q-displacement group, -1: bounce-back
 };
 
-template <typename real>
+template <typename real, int H>
 __host__ __device__ constexpr size_t smem_layout(int nq, size_t* o_A, size_t* o_Ar, size_t* o_U,
                                                  size_t* o_poff, size_t* o_delta, size_t* o_tgt) {
-  size_t o = sizeof(real) * 20 * HSZ;
+  size_t o = sizeof(real) * 20 * Geo<H>::HSZ;
   *o_A = o;
-  o += sizeof(real) * (size_t)nq * NT;
+  o += sizeof(real) * (size_t)nq * Geo<H>::NT;
   *o_Ar = o;
-  o += sizeof(real) * (size_t)nq * RING;
+  o += sizeof(real) * (size_t)nq * Geo<H>::RING;
   *o_U = o;
-  o += sizeof(real) * 2 * (TY + 2) * (TX + 2);
+  o += sizeof(real) * 2 * (H + 2) * (TX + 2);
   o = (o + 15) & ~(size_t)15;
   *o_poff = o;
   o += sizeof(long long) * (size_t)nq * 25;
@@ -138,16 +148,16 @@ __host__ __device__ constexpr size_t smem_layout(int nq, size_t* o_A, size_t* o_
   return o;
 }
 
-template <typename real>
+template <typename real, int H>
 __device__ __forceinline__ Smem<real> carve(unsigned char* base, int nq) {
   size_t oA, oAr, oU, op, od, ot;
-  smem_layout<real>(nq, &oA, &oAr, &oU, &op, &od, &ot);
+  smem_layout<real, H>(nq, &oA, &oAr, &oU, &op, &od, &ot);
   Smem<real> s;
   s.hb = (real*)base;
   s.A = (real*)(base + oA);
   s.Ar = (real*)(base + oAr);
   s.Ux = (real*)(base + oU);
-  s.Uy = s.Ux + (TY + 2) * (TX + 2);
+  s.Uy = s.Ux + (H + 2) * (TX + 2);
   s.poff = (long long*)(base + op);
   s.delta = (real*)(base + od);
   s.tgt = (int*)(base + ot);
@@ -179,12 +189,14 @@ __device__ __forceinline__ void velocity_at(const KernelArgs<real>& a, const rea
 
 // One tile (btx, bty) of an ntx x nty tile grid; shared by the single-run and
 // the batched kernels.
-template <typename real, typename S, bool RESHAPE = false>
+template <typename real, typename S, bool RESHAPE, int H>
 __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const FusedArgs<real>& fa,
                                            int btx, int bty, int ntx, int nty,
                                            unsigned char* smem_raw) {
+  constexpr int NT = Geo<H>::NT, RING = Geo<H>::RING, HSZ = Geo<H>::HSZ;
+  constexpr int TY = H;     // tile height within this body
   const int nq = a.nq;
-  Smem<real> sm = carve<real>(smem_raw, nq);
+  Smem<real> sm = carve<real, H>(smem_raw, nq);
   const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * TX + lx;
   const int x0 = btx * TX, y0 = bty * TY;
   const int x = x0 + lx, y = y0 + ly;
@@ -241,7 +253,7 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
   const int hcell = (ly + 2) * HX + (lx + 2);
   const bool ring_thread = tid < RING;
   int rex = 0, rey = 0;
-  if (ring_thread) ring_coords(tid, rex, rey);
+  if (ring_thread) ring_coords<H>(tid, rex, rey);
   const int rcell = (rey + 2) * HX + (rex + 2);
 
   const real rho = a.rho0 + Min[(size_t)(nq + M_DRHO) * P + n];
@@ -513,20 +525,22 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
 }
 
 template <typename real, typename S, bool RESHAPE>
-__global__ void __launch_bounds__(NT, 2)
+__global__ void __launch_bounds__(Geo<TY>::NT, 2)
 step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  fused_body<real, S, RESHAPE>(a, fa, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y, smem_raw);
+  fused_body<real, S, RESHAPE, TY>(a, fa, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y, smem_raw);
 }
 
 // Completes the border nodes of every tile: own partial sums plus the ring
 // exports of the neighbouring tiles (left, right, down, up, then the four
 // diagonal neighbours at corners), plus the constant shift terms; then
 // delta rho and delta Theta.
-template <typename real>
+template <typename real, int H>
 __device__ __forceinline__ void fixup_body(const KernelArgs<real>& a, const FusedArgs<real>& fa,
                                            int tx, int ty, int ntx, int nty) {
+  constexpr int TY = H, RING = Geo<H>::RING;
   constexpr int NB = 2 * TX + 2 * (TY - 2);
+  static_assert(NB <= 128, "one fix-up block of 128 threads per tile");
   const int k = threadIdx.x;
   if (k >= NB) return;
   int lx, ly;
@@ -545,14 +559,14 @@ __device__ __forceinline__ void fixup_body(const KernelArgs<real>& a, const Fuse
     const int ax = (tx + dx + ntx) % ntx, ay = (ty + dy + nty) % nty;
     return ay * ntx + ax;
   };
-  if (lx == 0) { ctile[nc] = tile_of(-1, 0); cpos[nc++] = ring_pos(TX, ly); }
-  if (lx == TX - 1) { ctile[nc] = tile_of(1, 0); cpos[nc++] = ring_pos(-1, ly); }
-  if (ly == 0) { ctile[nc] = tile_of(0, -1); cpos[nc++] = ring_pos(lx, TY); }
-  if (ly == TY - 1) { ctile[nc] = tile_of(0, 1); cpos[nc++] = ring_pos(lx, -1); }
-  if (lx == 0 && ly == 0) { ctile[nc] = tile_of(-1, -1); cpos[nc++] = ring_pos(TX, TY); }
-  if (lx == TX - 1 && ly == 0) { ctile[nc] = tile_of(1, -1); cpos[nc++] = ring_pos(-1, TY); }
-  if (lx == 0 && ly == TY - 1) { ctile[nc] = tile_of(-1, 1); cpos[nc++] = ring_pos(TX, -1); }
-  if (lx == TX - 1 && ly == TY - 1) { ctile[nc] = tile_of(1, 1); cpos[nc++] = ring_pos(-1, -1); }
+  if (lx == 0) { ctile[nc] = tile_of(-1, 0); cpos[nc++] = ring_pos<H>(TX, ly); }
+  if (lx == TX - 1) { ctile[nc] = tile_of(1, 0); cpos[nc++] = ring_pos<H>(-1, ly); }
+  if (ly == 0) { ctile[nc] = tile_of(0, -1); cpos[nc++] = ring_pos<H>(lx, TY); }
+  if (ly == TY - 1) { ctile[nc] = tile_of(0, 1); cpos[nc++] = ring_pos<H>(lx, -1); }
+  if (lx == 0 && ly == 0) { ctile[nc] = tile_of(-1, -1); cpos[nc++] = ring_pos<H>(TX, TY); }
+  if (lx == TX - 1 && ly == 0) { ctile[nc] = tile_of(1, -1); cpos[nc++] = ring_pos<H>(-1, TY); }
+  if (lx == 0 && ly == TY - 1) { ctile[nc] = tile_of(-1, 1); cpos[nc++] = ring_pos<H>(TX, -1); }
+  if (lx == TX - 1 && ly == TY - 1) { ctile[nc] = tile_of(1, 1); cpos[nc++] = ring_pos<H>(-1, -1); }
   const real* ex = fa.exports;
   size_t eoff[3];
 #pragma unroll
@@ -600,7 +614,7 @@ __device__ __forceinline__ void fixup_body(const KernelArgs<real>& a, const Fuse
 
 template <typename real>
 __global__ void __launch_bounds__(128) fixup_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
-  fixup_body<real>(a, fa, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
+  fixup_body<real, TY>(a, fa, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
 }
 
 // ---------------------------------------------------------------- batches
@@ -626,9 +640,10 @@ __device__ __forceinline__ void copy_words(T* dst, const T* src, int tid, int nt
   for (int k = tid; k < (int)(sizeof(T) / 4); k += nthreads) d[k] = s[k];
 }
 
-template <typename real, typename S>
-__global__ void __launch_bounds__(NT, 2)
+template <typename real, typename S, int H>
+__global__ void __launch_bounds__(Geo<H>::NT, Geo<H>::MINB)
 step_fused_batch_kernel(const BatchRun<real>* runs, const int* tile_start, int nruns, int parity) {
+  constexpr int NT = Geo<H>::NT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ KernelArgs<real> sa;
   __shared__ FusedArgs<real> sf;
@@ -641,10 +656,10 @@ step_fused_batch_kernel(const BatchRun<real>* runs, const int* tile_start, int n
   copy_words(&sf, &br.f[parity], tid, NT);
   __syncthreads();
   const int local = blockIdx.x - tile_start[s_run];
-  fused_body<real, S>(sa, sf, local % br.ntx, local / br.ntx, br.ntx, br.nty, smem_raw);
+  fused_body<real, S, false, H>(sa, sf, local % br.ntx, local / br.ntx, br.ntx, br.nty, smem_raw);
 }
 
-template <typename real>
+template <typename real, int H>
 __global__ void __launch_bounds__(128) fixup_batch_kernel(const BatchRun<real>* runs,
                                                           const int* tile_start, int nruns,
                                                           int parity) {
@@ -658,28 +673,46 @@ __global__ void __launch_bounds__(128) fixup_batch_kernel(const BatchRun<real>* 
   copy_words(&sf, &br.f[parity], threadIdx.x, blockDim.x);
   __syncthreads();
   const int local = blockIdx.x - tile_start[s_run];
-  fixup_body<real>(sa, sf, local % br.ntx, local / br.ntx, br.ntx, br.nty);
+  fixup_body<real, H>(sa, sf, local % br.ntx, local / br.ntx, br.ntx, br.nty);
 }
 
 }  // namespace
 
-size_t fused_smem_bytes(int nq, size_t real_bytes) {
+template <int H>
+size_t smem_bytes_h(int nq, size_t real_bytes) {
   size_t a, b, c, d, e, f;
-  return real_bytes == 8 ? smem_layout<double>(nq, &a, &b, &c, &d, &e, &f)
-                         : smem_layout<float>(nq, &a, &b, &c, &d, &e, &f);
+  return real_bytes == 8 ? smem_layout<double, H>(nq, &a, &b, &c, &d, &e, &f)
+                         : smem_layout<float, H>(nq, &a, &b, &c, &d, &e, &f);
 }
 
-size_t fused_export_elems(int nx, int ny, int nq) {
-  return (size_t)(nx / TX) * (ny / TY) * RING * (size_t)(nq + 3);
+size_t fused_smem_bytes(int nq, size_t real_bytes, int ty) {
+  switch (ty) {
+    case 4: return smem_bytes_h<4>(nq, real_bytes);
+    case 8: return smem_bytes_h<8>(nq, real_bytes);
+    case 16: return smem_bytes_h<16>(nq, real_bytes);
+    default: return ~(size_t)0;
+  }
 }
 
-bool fused_supported(int nx, int ny, int nq, size_t real_bytes) {
-  return nx % TX == 0 && ny % TY == 0 && fused_smem_bytes(nq, real_bytes) <= 227 * 1024;
+size_t fused_export_elems(int nx, int ny, int nq, int ty) {
+  const size_t ring = 2 * (TX + 2) + 2 * (size_t)ty;
+  return (size_t)(nx / TX) * (ny / ty) * ring * (size_t)(nq + 3);
+}
+
+size_t fused_export_capacity(int nx, int ny, int nq) {
+  size_t m = 0;
+  for (int ty : {4, 8, 16})
+    if (ny % ty == 0) m = std::max(m, fused_export_elems(nx, ny, nq, ty));
+  return m;
+}
+
+bool fused_supported(int nx, int ny, int nq, size_t real_bytes, int ty) {
+  return nx % TX == 0 && ny % ty == 0 && fused_smem_bytes(nq, real_bytes, ty) <= 227 * 1024;
 }
 
 template <typename real, typename S>
 cudaError_t launch_step_fused(const KernelArgs<real>& a, const FusedArgs<real>& f, cudaStream_t s) {
-  const size_t smem = fused_smem_bytes(a.nq, sizeof(real));
+  const size_t smem = fused_smem_bytes(a.nq, sizeof(real), TY);
   const dim3 grid(a.nx / TX, a.ny / TY), block(TX, TY);
   if (f.rshp) {
     // a learned block's increment rides on this step's pull (FP32 storage only)
@@ -706,21 +739,43 @@ cudaError_t launch_fixup(const KernelArgs<real>& a, const FusedArgs<real>& f, cu
   return cudaGetLastError();
 }
 
-cudaError_t prepare_batch(int max_nq) {
-  const size_t smem = fused_smem_bytes(max_nq, sizeof(float));
-  return cudaFuncSetAttribute(step_fused_batch_kernel<float, float>,
+template <int H>
+cudaError_t prepare_batch_h(int max_nq) {
+  const size_t smem = fused_smem_bytes(max_nq, sizeof(float), H);
+  return cudaFuncSetAttribute(step_fused_batch_kernel<float, float, H>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-cudaError_t launch_batch_step(const BatchRun<float>* runs, const int* tile_start, int nruns,
-                              int total_tiles, int max_nq, int parity, cudaStream_t s) {
-  const size_t smem = fused_smem_bytes(max_nq, sizeof(float));
-  step_fused_batch_kernel<float, float><<<total_tiles, dim3(TX, TY), smem, s>>>(runs, tile_start,
-                                                                               nruns, parity);
+cudaError_t prepare_batch(int max_nq, int ty) {
+  switch (ty) {
+    case 4: return prepare_batch_h<4>(max_nq);
+    case 8: return prepare_batch_h<8>(max_nq);
+    case 16: return prepare_batch_h<16>(max_nq);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int H>
+cudaError_t launch_batch_step_h(const BatchRun<float>* runs, const int* tile_start, int nruns,
+                                int total_tiles, int max_nq, int parity, cudaStream_t s) {
+  const size_t smem = fused_smem_bytes(max_nq, sizeof(float), H);
+  step_fused_batch_kernel<float, float, H><<<total_tiles, dim3(TX, H), smem, s>>>(
+      runs, tile_start, nruns, parity);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  fixup_batch_kernel<float><<<total_tiles, 128, 0, s>>>(runs, tile_start, nruns, parity);
+  fixup_batch_kernel<float, H><<<total_tiles, 128, 0, s>>>(runs, tile_start, nruns, parity);
   return cudaGetLastError();
+}
+
+cudaError_t launch_batch_step(const BatchRun<float>* runs, const int* tile_start, int nruns,
+                              int total_tiles, int max_nq, int parity, cudaStream_t s, int ty) {
+  switch (ty) {
+    case 4: return launch_batch_step_h<4>(runs, tile_start, nruns, total_tiles, max_nq, parity, s);
+    case 8: return launch_batch_step_h<8>(runs, tile_start, nruns, total_tiles, max_nq, parity, s);
+    case 16:
+      return launch_batch_step_h<16>(runs, tile_start, nruns, total_tiles, max_nq, parity, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 // Host-side tables of the fused kernel: target Q-node of every

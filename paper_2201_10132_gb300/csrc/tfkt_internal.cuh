@@ -55,6 +55,9 @@ __host__ __device__ constexpr double w25(int i) { return i == 0 ? 1.0 / 3.0 : 1.
 // Index of the pull offset for a source displaced by (sx, sy) in {-1,0,1}^2.
 __host__ __device__ constexpr int shift_index(int sx, int sy) { return (sy + 1) * 3 + (sx + 1); }
 
+constexpr int TX = 32;   // tile width (one warp along x)
+constexpr int TY = 8;    // tile height of the single-run path (batches choose 4, 8 or 16)
+
 // --------------------------------------------------------------- contexts
 // Derived lattice parameters (lattice units).
 struct Lattice {
@@ -214,9 +217,11 @@ cudaError_t launch_diag(const KernelArgs<real>& a, double* partials, int nblocks
                         cudaStream_t s);
 
 // Fused single-pass step (tfkt_fused.cu).
-size_t fused_smem_bytes(int nq, size_t real_bytes);
-size_t fused_export_elems(int nx, int ny, int nq);
-bool fused_supported(int nx, int ny, int nq, size_t real_bytes);
+size_t fused_smem_bytes(int nq, size_t real_bytes, int ty = TY);
+size_t fused_export_elems(int nx, int ny, int nq, int ty = TY);
+// ring-export elements enough for every tile height the grid allows (4, 8, 16)
+size_t fused_export_capacity(int nx, int ny, int nq);
+bool fused_supported(int nx, int ny, int nq, size_t real_bytes, int ty = TY);
 void fused_tables(const Lattice& L, const HostTables& t, std::vector<int>& tgt,
                   std::vector<double>& dpsi, double& dvx, double& dvy,
                   std::vector<long long>& poff);
@@ -226,9 +231,9 @@ template <typename real>
 cudaError_t launch_fixup(const KernelArgs<real>& a, const FusedArgs<real>& f, cudaStream_t s);
 
 // Batched fused step (FP32): all tiles of all runs in one launch of each kernel.
-cudaError_t prepare_batch(int max_nq);
+cudaError_t prepare_batch(int max_nq, int ty);
 cudaError_t launch_batch_step(const BatchRun<float>* runs, const int* tile_start, int nruns,
-                              int total_tiles, int max_nq, int parity, cudaStream_t s);
+                              int total_tiles, int max_nq, int parity, cudaStream_t s, int ty);
 // Access to a context's internals and argument builders (tfkt_api.cu).
 Ctx* ctx_of(tfkt_ctx* c);
 size_t ctx_layout(const Lattice& L);
@@ -238,11 +243,11 @@ template <typename real>
 FusedArgs<real> ctx_fused(const Ctx* c);
 // Make the moment planes of an FP32 context current (tfkt_api.cu).
 tfkt_status ctx_ensure_moments_f32(Ctx* c);
+// Write the initial state (Sec. VI-D) again, from this perturbation (tfkt_api.cu).
+tfkt_status ctx_reinit(Ctx* c, const double* perturb);
 // Add a pending learned-block increment to the stored populations (tfkt_lpm.cu).
 tfkt_status ctx_lpm_flush(Ctx* c);
 
-constexpr int TX = 32;   // tile width (one warp along x)
-constexpr int TY = 8;    // tile height
 constexpr int DIAG_THREADS = 256;
 
 }  // namespace tfkt

@@ -130,6 +130,9 @@ def lib() -> ctypes.CDLL:
         L.tfkt_batch_step.argtypes = [P, ctypes.c_int64]
         L.tfkt_batch_run.argtypes = [P, ctypes.c_int32, ctypes.POINTER(P)]
         L.tfkt_batch_destroy.argtypes = [P]
+        L.tfkt_batch_tile_height.argtypes = [P, ctypes.POINTER(ctypes.c_int32),
+                                             ctypes.POINTER(ctypes.c_float)]
+        L.tfkt_batch_tile_height.restype = S
         for n in ("tfkt_batch_required_bytes", "tfkt_batch_create", "tfkt_batch_step",
                   "tfkt_batch_run", "tfkt_batch_destroy"):
             getattr(L, n).restype = S
@@ -349,6 +352,13 @@ class Batch:
 
     def step(self, n: int = 1):
         _check(lib().tfkt_batch_step(self._h, int(n)), "tfkt_batch_step")
+
+    def tile_height(self):
+        """(tile height of the launch, timed ms per step at heights 4, 8, 16)."""
+        ty = ctypes.c_int32()
+        ms = (ctypes.c_float * 3)()
+        _check(lib().tfkt_batch_tile_height(self._h, ctypes.byref(ty), ms), "tfkt_batch_tile_height")
+        return int(ty.value), [float(v) for v in ms]
 
     def run(self, i: int) -> Solver:
         r = ctypes.c_void_p()

@@ -32,16 +32,23 @@ def test_batch_rejects_unsupported_runs(T):
     ragged[0] = 70
     with pytest.raises(T.TfktError):
         T.batch_required_bytes([_params(T, tuple(ragged))])
+    short = list(RUNS[0])
+    short[1] = 12                       # runs must admit the single-run 8-row tile
+    with pytest.raises(T.TfktError):
+        T.batch_required_bytes([_params(T, tuple(short))])
     assert T.batch_required_bytes([_params(T, r) for r in RUNS]) > 0
 
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("steps", [1, 7])
-def test_batch_equals_single_runs(T, steps):
+def test_batch_equals_single_runs(T, steps, monkeypatch):
+    """At the single-run tile height (8 rows) the batch is bit-identical."""
     from paper_2201_10132_gb300.inputs import perturbation
+    monkeypatch.setenv("TFKT_BATCH_TILE_HEIGHT", "8")
     params = [_params(T, r) for r in RUNS]
     perts = [perturbation(r[0], r[1], r[9], 0.05, 0.05) for r in RUNS]
     with T.Batch(params, perts) as b:
+        assert b.tile_height()[0] == 8
         b.step(steps)
         got = [b.run(i).moments() for i in range(len(RUNS))]
         diag = [b.run(i).diagnostics() for i in range(len(RUNS))]
@@ -54,3 +61,65 @@ def test_batch_equals_single_runs(T, steps):
         for k in ref:
             assert np.array_equal(got[i][k], ref[k]), (i, k)
         assert diag[i] == dref
+
+
+def _single(T, p, pert, steps):
+    with T.Solver(p, pert) as s:
+        s.step(steps)
+        return s.moments()
+
+
+def _close(got, ref):
+    """The FP32 tolerance of the oracle parity tests: 2e-5 of the field's largest
+    magnitude, velocity-derived fields against the largest velocity. Another tile
+    split changes only the float rounding (the tile edges are finished by the
+    fix-up kernel instead of the tile body), not the arithmetic of a node."""
+    uscale = max(np.abs(ref["ux"]).max(), np.abs(ref["uy"]).max())
+    for k in ref:
+        scale = uscale if k in ("ux", "uy", "vort") else np.abs(ref[k]).max()
+        err = float(np.abs(got[k] - ref[k]).max()) / max(scale, 1e-30)
+        assert err < 2e-5, (k, err)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("ty", [4, 16])
+def test_batch_tile_heights_match_single_runs(T, ty, monkeypatch):
+    """Other tile heights change only which CTA updates a node; each node's
+    collision is the same, so the fields agree with the single runs."""
+    from paper_2201_10132_gb300.inputs import perturbation
+    runs = RUNS[:2] if ty == 16 else RUNS       # ny = 24 is not a multiple of 16
+    monkeypatch.setenv("TFKT_BATCH_TILE_HEIGHT", str(ty))
+    params = [_params(T, r) for r in runs]
+    perts = [perturbation(r[0], r[1], r[9], 0.05, 0.05) for r in runs]
+    steps = 7
+    with T.Batch(params, perts) as b:
+        assert b.tile_height()[0] == ty
+        b.step(steps)
+        got = [b.run(i).moments() for i in range(len(runs))]
+    for i, (p, pert) in enumerate(zip(params, perts)):
+        _close(got[i], _single(T, p, pert, steps))
+
+
+@pytest.mark.gpu
+def test_batch_autotune_picks_fastest(T, monkeypatch):
+    from paper_2201_10132_gb300.inputs import perturbation
+    monkeypatch.delenv("TFKT_BATCH_TILE_HEIGHT", raising=False)
+    runs = RUNS[:2]
+    params = [_params(T, r) for r in runs]
+    perts = [perturbation(r[0], r[1], r[9], 0.05, 0.05) for r in runs]
+    with T.Batch(params, perts) as b:
+        ty, ms = b.tile_height()
+        assert all(np.isfinite(m) and m > 0 for m in ms)
+        assert ms[(4, 8, 16).index(ty)] == min(ms)
+        assert all(b.run(i).get_info()["step"] == 0 for i in range(len(runs)))
+        b.step(3)
+        got = [b.run(i).moments() for i in range(len(runs))]
+    for i, (p, pert) in enumerate(zip(params, perts)):
+        _close(got[i], _single(T, p, pert, 3))
+
+
+@pytest.mark.gpu
+def test_batch_forced_height_must_fit(T, monkeypatch):
+    monkeypatch.setenv("TFKT_BATCH_TILE_HEIGHT", "16")
+    with pytest.raises(T.TfktError):
+        T.Batch([_params(T, RUNS[2])], None)         # ny = 24
