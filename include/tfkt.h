@@ -240,7 +240,9 @@ tfkt_status tfkt_destroy(tfkt_ctx* ctx);
    replayed from a CUDA graph two steps at a time. The paper runs one case at
    a time; batching is this library's addition. Requirements: every run uses
    TFKT_FP32 and has nx a multiple of 32 and ny a multiple of 8 (the fused
-   path); otherwise TFKT_EINVAL. */
+   path); otherwise TFKT_EINVAL. A run of the batch matches the same run
+   stepped alone up to float rounding (the batched kernel sums some moments in
+   another order), not bit for bit. */
 typedef struct tfkt_batch tfkt_batch;
 
 /* Device bytes for the batch (the runs' workspaces and the launch tables). */

@@ -83,6 +83,24 @@ __device__ __forceinline__ void acc(real& sum, real v) {
   else if constexpr (S == -1) sum -= v;
 }
 
+// Component k (0..3 = rx, ry, qx, qy) of a velocity, and the index of the
+// D4Q25 velocity with components ca = sa, cb = sb and zero elsewhere (every
+// moving velocity is +-1 on exactly one pair of components).
+__host__ __device__ constexpr int comp_of(const V4 c, int k) {
+  return k == 0 ? c.rx : (k == 1 ? c.ry : (k == 2 ? c.qx : c.qy));
+}
+__host__ __device__ constexpr int pair_vel(int ca, int cb, int sa, int sb) {
+  for (int i = 1; i < 25; ++i) {
+    bool ok = true;
+    for (int k = 0; k < 4; ++k) {
+      const int want = k == ca ? sa : (k == cb ? sb : 0);
+      ok = ok && comp_of(c25(i), k) == want;
+    }
+    if (ok) return i;
+  }
+  return -1;
+}
+
 // Velocities 1..20 move in r (they reach other r-nodes); 0 and 21..24 do not.
 __host__ __device__ constexpr bool moves_r(int i) { return i >= 1 && i <= 20; }
 
@@ -121,7 +139,8 @@ struct Smem {
   real* Ar;          // [nq][RING] ring-node arrival sums per Q-node
   real* Ux;          // [H+2][TX+2]
   real* Uy;
-  long long* poff;   // [nq*25] element offset of each pull's source plane
+  const void** pptr; // [nq*25] source plane of each pull in the current source buffer,
+                     // or (lean variant) its element offset as a long long
   real* delta;       // [nq][DQ] pull shift differences
   int* tgt;          // [nq][GQ] target Q-node of each Q-displacement group, -1: bounce-back
 };
@@ -158,7 +177,7 @@ __device__ __forceinline__ Smem<real> carve(unsigned char* base, int nq) {
   s.Ar = (real*)(base + oAr);
   s.Ux = (real*)(base + oU);
   s.Uy = s.Ux + (H + 2) * (TX + 2);
-  s.poff = (long long*)(base + op);
+  s.pptr = (const void**)(base + op);
   s.delta = (real*)(base + od);
   s.tgt = (int*)(base + ot);
   return s;
@@ -188,8 +207,13 @@ __device__ __forceinline__ void velocity_at(const KernelArgs<real>& a, const rea
 }
 
 // One tile (btx, bty) of an ntx x nty tile grid; shared by the single-run and
-// the batched kernels.
-template <typename real, typename S, bool RESHAPE, int H>
+// the batched kernels. LEAN (the batched kernel, whose arguments sit in shared
+// memory and which already runs at its register limit) addresses the pulls by
+// offsets and sums the moments velocity by velocity; the single-run kernel
+// uses a table of source-plane pointers and pairwise moment sums, which cost
+// registers but fewer instructions (measured: each is faster in one kernel and
+// slower in the other).
+template <typename real, typename S, bool RESHAPE, int H, bool LEAN>
 __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const FusedArgs<real>& fa,
                                            int btx, int bty, int ntx, int nty,
                                            unsigned char* smem_raw) {
@@ -221,7 +245,10 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
     const int q = k / GQ, g = k % GQ;
     sm.tgt[k] = g < 9 ? fa.tgt[q * 9 + g] : -1;
   }
-  for (int k = tid; k < nq * 25; k += NT) sm.poff[k] = fa.poff[k];
+  for (int k = tid; k < nq * 25; k += NT) {
+    if constexpr (LEAN) reinterpret_cast<long long*>(sm.pptr)[k] = fa.poff[k];
+    else sm.pptr[k] = src + fa.poff[k];
+  }
   for (int k = tid; k < nq * DQ; k += NT) {
     const int q = k / DQ, i = k % DQ;
     sm.delta[k] = i < 25 ? a.tab.delta[q * 25 + i] : real(0);
@@ -271,8 +298,8 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
       if (tv[g] < 0) m |= 1u << g;
     return m;
   };
-  // Source offset of the pull of velocity i at Q-node q (bm: that Q-node's mask);
-  // the pull bounces when q - Qdot_i leaves the disk, the opposite group 8 - g.
+  // Source address of the pull of velocity i at Q-node q (bm: that Q-node's
+  // mask); the pull bounces when q - Qdot_i leaves the disk, the opposite group 8 - g.
   auto pull_offset = [&](auto I, int q, uint32_t bm) {
     constexpr int i = decltype(I)::value;
     constexpr V4 cv = c25(i);
@@ -280,7 +307,8 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
     if constexpr (moves_r(i)) {
       if ((bm >> (8 - qgroup(cv))) & 1u) o = off[4];
     }
-    return sm.poff[q * 25 + i] + o;
+    if constexpr (LEAN) return src + (reinterpret_cast<const long long*>(sm.pptr)[q * 25 + i] + o);
+    else return (const S*)sm.pptr[q * 25 + i] + o;
   };
   // The populations of a Q-node are loaded one Q-node ahead: register h[i] is
   // refilled for Q-node q + 1 as soon as the collision of Q-node q has used it,
@@ -289,7 +317,7 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
   if (nq > 0) {
     const uint32_t bm0 = bounce_mask(0);
     static_for<0, 25>([&](auto I) {
-      h[decltype(I)::value] = from_store<real>(src[pull_offset(I, 0, bm0)]);
+      h[decltype(I)::value] = from_store<real>(*pull_offset(I, 0, bm0));
     });
     mn[0] = Min[off[5]];
     mn[1] = Min[off[3]];
@@ -368,7 +396,10 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
       real dl[DQ];
       load_vec<DQ>(dl, sm.delta + q * DQ);
 #pragma unroll
-      for (int i = 0; i < 25; ++i) h[i] = h[i] * a.pinv + dl[i];   // unscale, shift to this Q-node
+      for (int i = 0; i < 25; ++i) {   // unscale (FP16 storage), shift to this Q-node
+        if constexpr (std::is_same<S, real>::value) h[i] += dl[i];
+        else h[i] = h[i] * a.pinv + dl[i];
+      }
     }
     if constexpr (RESHAPE) {
       // added as the linear quasi-equilibrium w_i [dpsi + 3 (v_i . dpsi U + Qdot_i . dpsi
@@ -400,14 +431,40 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
       mn[3] = Mq[off[1]];
     }
     real dpsi = 0, rx = 0, ry = 0, qx = 0, qy = 0;
-    static_for<0, 25>([&](auto I) {
-      constexpr int i = I;
-      dpsi += h[i];
-      acc<c25(i).rx>(rx, h[i]);
-      acc<c25(i).ry>(ry, h[i]);
-      acc<c25(i).qx>(qx, h[i]);
-      acc<c25(i).qy>(qy, h[i]);
-    });
+    if constexpr (LEAN) {
+      static_for<0, 25>([&](auto I) {
+        constexpr int i = I;
+        dpsi += h[i];
+        acc<c25(i).rx>(rx, h[i]);
+        acc<c25(i).ry>(ry, h[i]);
+        acc<c25(i).qx>(qx, h[i]);
+        acc<c25(i).qy>(qy, h[i]);
+      });
+    } else {
+      // the four velocities (+-1, +-1) on a component pair (a, b) give their
+      // sum and the a- and b-momenta from two differences
+      dpsi = h[0];
+      static_for<0, 6>([&](auto PR) {
+        constexpr int pr = PR;   // pairs (rx,ry) (rx,qx) (rx,qy) (ry,qx) (ry,qy) (qx,qy)
+        constexpr int ca = pr < 3 ? 0 : (pr < 5 ? 1 : 2);
+        constexpr int cb = pr == 0 ? 1 : (pr == 1 ? 2 : (pr == 2 ? 3 : (pr == 3 ? 2 : 3)));
+        constexpr int ipp = pair_vel(ca, cb, 1, 1), ipm = pair_vel(ca, cb, 1, -1);
+        constexpr int imp = pair_vel(ca, cb, -1, 1), imm = pair_vel(ca, cb, -1, -1);
+        static_assert(ipp > 0 && ipm > 0 && imp > 0 && imm > 0, "D4Q25 pair velocities");
+        const real d1 = h[ipp] - h[imm], d2 = h[ipm] - h[imp];
+        dpsi += (h[ipp] + h[imm]) + (h[ipm] + h[imp]);
+        const real ma = d1 + d2, mb = d1 - d2;
+        auto addc = [&](auto K, real v) {
+          constexpr int k = decltype(K)::value;
+          if constexpr (k == 0) rx += v;
+          else if constexpr (k == 1) ry += v;
+          else if constexpr (k == 2) qx += v;
+          else qy += v;
+        };
+        addc(std::integral_constant<int, ca>(), ma);
+        addc(std::integral_constant<int, cb>(), mb);
+      });
+    }
     const real Qx = a.tab.qx[q], Qy = a.tab.qy[q], Fx = a.tab.fx[q], Fy = a.tab.fy[q];
     const real psi = a.tab.psi0[q] + dpsi;
     const real qg = Qx * dpx + Qy * dpy;
@@ -415,24 +472,30 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
     const real jrey = psi * Uy + a.tau2 * a.hl2h * Fy * qg;
     const real jqex = psi * (Qx * G00 + Qy * G10 - a.kappa * Fx);
     const real jqey = psi * (Qx * G01 + Qy * G11 - a.kappa * Fy);
-    // 3 x the momenta of the mixed equilibrium (1 - r) f* + r f^eq
-    const real mrx = real(3) * (a.omr * (a.c2 * rx + jrex) * a.inv_c2p1 + a.r * jrex);
-    const real mry = real(3) * (a.omr * (a.c2 * ry + jrey) * a.inv_c2p1 + a.r * jrey);
-    const real mqx = real(3) * (a.omr * (a.c2 * qx + jqex) * a.inv_c2p1 + a.r * jqex);
-    const real mqy = real(3) * (a.omr * (a.c2 * qy + jqey) * a.inv_c2p1 + a.r * jqey);
+    // 3 x the momenta of the mixed equilibrium (1 - r) f* + r f^eq, times the
+    // relaxation weight 2 beta w_i of the moving velocities (w_i = 1/36): a
+    // moving population then takes an add per nonzero component and one FMA
+    const real tw = a.tb * real(1.0 / 36.0), tw3 = real(3) * tw;
+    const real mrx = tw3 * (a.omr * (a.c2 * rx + jrex) * a.inv_c2p1 + a.r * jrex);
+    const real mry = tw3 * (a.omr * (a.c2 * ry + jrey) * a.inv_c2p1 + a.r * jrey);
+    const real mqx = tw3 * (a.omr * (a.c2 * qx + jqex) * a.inv_c2p1 + a.r * jqex);
+    const real mqy = tw3 * (a.omr * (a.c2 * qy + jqey) * a.inv_c2p1 + a.r * jqey);
+    const real wdpsi = tw * dpsi;
     S* dq = dst + (size_t)(9 + 25 * q) * P + n;
     real grp[9];
 #pragma unroll
     for (int g = 0; g < 9; ++g) grp[g] = real(0);
     static_for<0, 25>([&](auto I) {
       constexpr int i = I;
-      real d = dpsi;
+      static_assert(i == 0 || w25(i) == 1.0 / 36.0, "moving weights");
+      real d = i == 0 ? a.tb * real(w25(0)) * dpsi : wdpsi;
       acc<c25(i).rx>(d, mrx);
       acc<c25(i).ry>(d, mry);
       acc<c25(i).qx>(d, mqx);
       acc<c25(i).qy>(d, mqy);
-      const real hp = a.om2b * h[i] + a.tb * real(w25(i)) * d;
-      dq[(size_t)i * P] = to_store<S>(hp * a.pscale);
+      const real hp = a.om2b * h[i] + d;
+      if constexpr (std::is_same<S, real>::value) dq[(size_t)i * P] = hp;
+      else dq[(size_t)i * P] = to_store<S>(hp * a.pscale);
       constexpr int g = qgroup(c25(i));
       const bool b = (bm >> g) & 1u;
       if constexpr (!moves_r(i)) {
@@ -450,7 +513,7 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
         acc<-c25(i).rx>(jx_arr, back);
         acc<-c25(i).ry>(jy_arr, back);
       }
-      if (more) h[i] = from_store<real>(src[pull_offset(I, q + 1, bmn)]);
+      if (more) h[i] = from_store<real>(*pull_offset(I, q + 1, bmn));
     });
     __syncthreads();
     // arrivals from the other r-nodes of the tile
@@ -462,9 +525,11 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
       acc<cv.rx>(jx_arr, v);
       acc<cv.ry>(jy_arr, v);
     });
+    int tq[GQ];
+    load_vec<GQ>(tq, sm.tgt + q * GQ);
 #pragma unroll
     for (int g = 0; g < 9; ++g) {
-      const int t = g == 4 ? q : sm.tgt[q * GQ + g];
+      const int t = g == 4 ? q : tq[g];
       if (t >= 0) sm.A[t * NT + tid] += grp[g];
     }
     if (ring_thread) {
@@ -528,7 +593,8 @@ template <typename real, typename S, bool RESHAPE>
 __global__ void __launch_bounds__(Geo<TY>::NT, 2)
 step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  fused_body<real, S, RESHAPE, TY>(a, fa, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y, smem_raw);
+  fused_body<real, S, RESHAPE, TY, false>(a, fa, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y,
+                                          smem_raw);
 }
 
 // Completes the border nodes of every tile: own partial sums plus the ring
@@ -656,7 +722,8 @@ step_fused_batch_kernel(const BatchRun<real>* runs, const int* tile_start, int n
   copy_words(&sf, &br.f[parity], tid, NT);
   __syncthreads();
   const int local = blockIdx.x - tile_start[s_run];
-  fused_body<real, S, false, H>(sa, sf, local % br.ntx, local / br.ntx, br.ntx, br.nty, smem_raw);
+  fused_body<real, S, false, H, true>(sa, sf, local % br.ntx, local / br.ntx, br.ntx, br.nty,
+                                       smem_raw);
 }
 
 template <typename real, int H>

@@ -1,6 +1,8 @@
 """Batched ensembles (tfkt_batch_*): independent runs advanced by one launch of
-each kernel per step must give exactly the results of the same runs stepped
-one by one (the kernels share one tile routine and sum in a fixed order)."""
+each kernel per step must give the results of the same runs stepped one by one
+up to float rounding: the kernels share one tile routine, but the batched one
+sums a Q-node's moments velocity by velocity and the single-run one by velocity
+pairs, and other tile heights move the tile borders (finished by the fix-up)."""
 import numpy as np
 import pytest
 
@@ -41,8 +43,8 @@ def test_batch_rejects_unsupported_runs(T):
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("steps", [1, 7])
-def test_batch_equals_single_runs(T, steps, monkeypatch):
-    """At the single-run tile height (8 rows) the batch is bit-identical."""
+def test_batch_matches_single_runs(T, steps, monkeypatch):
+    """At the single-run tile height (8 rows): fields and diagnostics."""
     from paper_2201_10132_gb300.inputs import perturbation
     monkeypatch.setenv("TFKT_BATCH_TILE_HEIGHT", "8")
     params = [_params(T, r) for r in RUNS]
@@ -58,9 +60,9 @@ def test_batch_equals_single_runs(T, steps, monkeypatch):
             s.step(steps)
             ref = s.moments()
             dref = s.diagnostics()
-        for k in ref:
-            assert np.array_equal(got[i][k], ref[k]), (i, k)
-        assert diag[i] == dref
+        _close(got[i], ref)
+        for k, v in dref.items():
+            assert diag[i][k] == pytest.approx(v, rel=1e-5, abs=1e-8 * dref["mass_s"]), (i, k)
 
 
 def _single(T, p, pert, steps):
@@ -71,9 +73,7 @@ def _single(T, p, pert, steps):
 
 def _close(got, ref):
     """The FP32 tolerance of the oracle parity tests: 2e-5 of the field's largest
-    magnitude, velocity-derived fields against the largest velocity. Another tile
-    split changes only the float rounding (the tile edges are finished by the
-    fix-up kernel instead of the tile body), not the arithmetic of a node."""
+    magnitude, velocity-derived fields against the largest velocity."""
     uscale = max(np.abs(ref["ux"]).max(), np.abs(ref["uy"]).max())
     for k in ref:
         scale = uscale if k in ("ux", "uy", "vort") else np.abs(ref[k]).max()
