@@ -43,7 +43,8 @@ typedef enum {
   TFKT_ENOMEM = 2,  /* device allocation failed, or the workspace is too small */
   TFKT_ECUDA = 3,   /* a CUDA call failed; the context is now poisoned */
   TFKT_ENAN = 4,    /* diagnostics found a non-finite value; state kept */
-  TFKT_ESTATE = 5   /* the context was poisoned by an earlier CUDA error */
+  TFKT_ESTATE = 5,  /* the context was poisoned by an earlier CUDA error */
+  TFKT_EIO = 6      /* a checkpoint file could not be written or read, or is corrupt */
 } tfkt_status;
 
 typedef enum {
@@ -228,6 +229,23 @@ tfkt_status tfkt_lattice(int32_t* c9, int32_t* c25);
 
 /* Wait for all work of the context. */
 tfkt_status tfkt_sync(tfkt_ctx* ctx);
+
+/* Checkpoint and restart. tfkt_save writes the current state to the file
+   `path` (through `path`.part, renamed when complete): a header (the lattice
+   parameters the state belongs to, the step count, sizes, a 64-bit checksum)
+   and the raw current populations plus, where valid, the current moment
+   planes. A pending learned-block increment is applied first. The file is
+   about the size of one population buffer (54 GB at 4096^2, N_Q = 32, FP32).
+   Synchronises. Allowed on a run of a batch.
+   tfkt_load reads such a file into a context created with the same
+   parameters (TFKT_EINVAL otherwise, nothing changed) and sets its step count;
+   stepping on gives the trajectory of the run that was saved, bit for bit.
+   TFKT_EIO: unreadable, not a checkpoint, truncated, trailing bytes or a
+   checksum mismatch; if the payload was already being copied, the context is
+   reset to its initial state (without perturbation). Not allowed on a run of
+   a batch (TFKT_EINVAL). Synchronises. */
+tfkt_status tfkt_save(tfkt_ctx* ctx, const char* path);
+tfkt_status tfkt_load(tfkt_ctx* ctx, const char* path);
 
 /* Release the context (and the workspace if the library allocated it).
    Synchronises first. NULL is accepted. */

@@ -786,6 +786,7 @@ const char* tfkt_status_string(tfkt_status s) {
     case TFKT_ECUDA: return "CUDA error";
     case TFKT_ENAN: return "non-finite value";
     case TFKT_ESTATE: return "context poisoned";
+    case TFKT_EIO: return "checkpoint file error";
   }
   return "unknown status";
 }

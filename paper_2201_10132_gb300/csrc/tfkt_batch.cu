@@ -238,6 +238,7 @@ tfkt_status tfkt_batch_create(const tfkt_params* runs, int32_t n, const double* 
     }
     b->runs.push_back(c);
     Ctx* x = ctx_of(c);
+    x->in_batch = true;
     for (int p = 0; p < 2; ++p) {
       x->cur = x->mcur = p;
       b->host[i].a[p] = ctx_args<float>(x);

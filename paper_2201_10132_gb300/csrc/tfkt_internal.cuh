@@ -179,6 +179,7 @@ struct Ctx {
   int64_t lpm_step = -1;  // step whose conformation the learned block's scratch holds
   bool lpm_pending = false;        // an increment waits to be added at the next pull
   const float* lpm_rshp = nullptr; // its coefficient planes
+  bool in_batch = false;  // a run of a tfkt_batch (its buffer parity belongs to the batch)
 };
 
 // Host helpers (tfkt_api.cu).

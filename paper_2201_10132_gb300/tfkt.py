@@ -21,7 +21,8 @@ FIELDS = ["rho_s", "psi_tot", "ux", "uy", "cxx", "cxy", "cyy", "thxx", "thxy", "
 KERNELS = ["moments", "step", "fused", "fixup"]
 DIAGS = ["mass_s", "mass_p", "px", "py", "ke", "enstrophy", "qrms_mean", "ey2"]
 STATUS = {0: "TFKT_OK", 1: "TFKT_EINVAL", 2: "TFKT_ENOMEM", 3: "TFKT_ECUDA", 4: "TFKT_ENAN",
-          5: "TFKT_ESTATE"}
+          5: "TFKT_ESTATE", 6: "TFKT_EIO"}
+EINVAL, EIO = 1, 6
 
 
 class TfktError(RuntimeError):
@@ -122,6 +123,8 @@ def lib() -> ctypes.CDLL:
         L.tfkt_lattice.argtypes = [ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
         L.tfkt_sync.argtypes = [P]
         L.tfkt_destroy.argtypes = [P]
+        L.tfkt_save.argtypes = [P, ctypes.c_char_p]
+        L.tfkt_load.argtypes = [P, ctypes.c_char_p]
         L.tfkt_batch_required_bytes.argtypes = [ctypes.POINTER(_Params), ctypes.c_int32,
                                                  ctypes.POINTER(ctypes.c_size_t)]
         L.tfkt_batch_create.argtypes = [ctypes.POINTER(_Params), ctypes.c_int32,
@@ -159,7 +162,7 @@ def lib() -> ctypes.CDLL:
         for n in ("tfkt_required_bytes", "tfkt_create", "tfkt_step", "tfkt_step_profiled",
                   "tfkt_moments", "tfkt_psi",
                   "tfkt_diagnostics", "tfkt_populations", "tfkt_get_info", "tfkt_lattice",
-                  "tfkt_sync", "tfkt_destroy"):
+                  "tfkt_sync", "tfkt_destroy", "tfkt_save", "tfkt_load"):
             getattr(L, n).restype = S
         _lib = L
     return _lib
@@ -257,6 +260,14 @@ class Solver:
 
     def sync(self):
         _check(lib().tfkt_sync(self._h), "tfkt_sync")
+
+    def save(self, path: str):
+        """Checkpoint the current state to `path` (tfkt_save)."""
+        _check(lib().tfkt_save(self._h, os.fsencode(path)), "tfkt_save")
+
+    def load(self, path: str):
+        """Restore a checkpoint written for the same parameters (tfkt_load)."""
+        _check(lib().tfkt_load(self._h, os.fsencode(path)), "tfkt_load")
 
     def get_info(self) -> dict:
         i = _Info()
