@@ -600,87 +600,120 @@ step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
 // Completes the border nodes of every tile: own partial sums plus the ring
 // exports of the neighbouring tiles (left, right, down, up, then the four
 // diagonal neighbours at corners), plus the constant shift terms; then
-// delta rho and delta Theta.
+// delta rho and delta Theta. One block per tile. Pass A takes one (plane,
+// border node) item per thread at a time, FIX_BATCH items with all their loads
+// issued first, so that many loads are in flight; it writes the final delta
+// psi planes and J and keeps delta psi and the raw delta rho in shared memory.
+// Pass B sums delta rho and Theta over the Q-nodes of each border node in the
+// same order as the tile body.
+constexpr int FIX_T = 256;       // threads of a fix-up block
+constexpr int FIX_BATCH = 4;     // items per thread whose loads are issued together
+
+template <int H>
+constexpr int fix_nodes() { return 2 * TX + 2 * (H - 2); }
+
+template <typename real, int H>
+size_t fix_smem_bytes(int nq) { return (size_t)(nq + 1) * fix_nodes<H>() * sizeof(real); }
+
 template <typename real, int H>
 __device__ __forceinline__ void fixup_body(const KernelArgs<real>& a, const FusedArgs<real>& fa,
-                                           int tx, int ty, int ntx, int nty) {
+                                           int tx, int ty, int ntx, int nty, real* s_d) {
   constexpr int TY = H, RING = Geo<H>::RING;
-  constexpr int NB = 2 * TX + 2 * (TY - 2);
-  static_assert(NB <= 128, "one fix-up block of 128 threads per tile");
-  const int k = threadIdx.x;
-  if (k >= NB) return;
-  int lx, ly;
-  if (k < TX) { lx = k; ly = 0; }
-  else if (k < 2 * TX) { lx = k - TX; ly = TY - 1; }
-  else if (k < 2 * TX + TY - 2) { lx = 0; ly = 1 + (k - 2 * TX); }
-  else { lx = TX - 1; ly = 1 + (k - 2 * TX - (TY - 2)); }
+  constexpr int NB = fix_nodes<H>();
+  __shared__ uint32_t s_n[NB];        // node offset within a plane
+  __shared__ uint32_t s_nc[NB];       // contributing neighbour tiles (1 to 3)
+  __shared__ size_t s_e[3][NB];       // their export positions (tile * RING + ring position)
+  const int tid = threadIdx.x;
   const size_t ntiles = (size_t)ntx * nty;
   const int nq = a.nq;
   const size_t P = a.plane;
-  const size_t n = (size_t)(ty * TY + ly) * a.pitch + (tx * TX + lx);
-  // contributing neighbour tiles (at most 3: two edges and a corner) and the
-  // ring position of this node in each
-  int ctile[3] = {0, 0, 0}, cpos[3] = {0, 0, 0}, nc = 0;
-  auto tile_of = [&](int dx, int dy) {
-    const int ax = (tx + dx + ntx) % ntx, ay = (ty + dy + nty) % nty;
-    return ay * ntx + ax;
-  };
-  if (lx == 0) { ctile[nc] = tile_of(-1, 0); cpos[nc++] = ring_pos<H>(TX, ly); }
-  if (lx == TX - 1) { ctile[nc] = tile_of(1, 0); cpos[nc++] = ring_pos<H>(-1, ly); }
-  if (ly == 0) { ctile[nc] = tile_of(0, -1); cpos[nc++] = ring_pos<H>(lx, TY); }
-  if (ly == TY - 1) { ctile[nc] = tile_of(0, 1); cpos[nc++] = ring_pos<H>(lx, -1); }
-  if (lx == 0 && ly == 0) { ctile[nc] = tile_of(-1, -1); cpos[nc++] = ring_pos<H>(TX, TY); }
-  if (lx == TX - 1 && ly == 0) { ctile[nc] = tile_of(1, -1); cpos[nc++] = ring_pos<H>(-1, TY); }
-  if (lx == 0 && ly == TY - 1) { ctile[nc] = tile_of(-1, 1); cpos[nc++] = ring_pos<H>(TX, -1); }
-  if (lx == TX - 1 && ly == TY - 1) { ctile[nc] = tile_of(1, 1); cpos[nc++] = ring_pos<H>(-1, -1); }
-  const real* ex = fa.exports;
-  size_t eoff[3];
+  if (tid < NB) {
+    const int k = tid;
+    int lx, ly;
+    if (k < TX) { lx = k; ly = 0; }
+    else if (k < 2 * TX) { lx = k - TX; ly = TY - 1; }
+    else if (k < 2 * TX + TY - 2) { lx = 0; ly = 1 + (k - 2 * TX); }
+    else { lx = TX - 1; ly = 1 + (k - 2 * TX - (TY - 2)); }
+    s_n[k] = (uint32_t)((size_t)(ty * TY + ly) * a.pitch + (tx * TX + lx));
+    int ctile[3] = {0, 0, 0}, cpos[3] = {0, 0, 0}, nc = 0;
+    auto tile_of = [&](int dx, int dy) {
+      const int ax = (tx + dx + ntx) % ntx, ay = (ty + dy + nty) % nty;
+      return ay * ntx + ax;
+    };
+    if (lx == 0) { ctile[nc] = tile_of(-1, 0); cpos[nc++] = ring_pos<H>(TX, ly); }
+    if (lx == TX - 1) { ctile[nc] = tile_of(1, 0); cpos[nc++] = ring_pos<H>(-1, ly); }
+    if (ly == 0) { ctile[nc] = tile_of(0, -1); cpos[nc++] = ring_pos<H>(lx, TY); }
+    if (ly == TY - 1) { ctile[nc] = tile_of(0, 1); cpos[nc++] = ring_pos<H>(lx, -1); }
+    if (lx == 0 && ly == 0) { ctile[nc] = tile_of(-1, -1); cpos[nc++] = ring_pos<H>(TX, TY); }
+    if (lx == TX - 1 && ly == 0) { ctile[nc] = tile_of(1, -1); cpos[nc++] = ring_pos<H>(-1, TY); }
+    if (lx == 0 && ly == TY - 1) { ctile[nc] = tile_of(-1, 1); cpos[nc++] = ring_pos<H>(TX, -1); }
+    if (lx == TX - 1 && ly == TY - 1) { ctile[nc] = tile_of(1, 1); cpos[nc++] = ring_pos<H>(-1, -1); }
+    s_nc[k] = nc;
 #pragma unroll
-  for (int c = 0; c < 3; ++c) eoff[c] = (size_t)ctile[c] * RING + cpos[c];
-  const size_t estride = ntiles * RING;
-  auto gather = [&](int j, real v) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-      if (c < nc) v += ex[(size_t)j * estride + eoff[c]];
-    return v;
-  };
+    for (int c = 0; c < 3; ++c) s_e[c][k] = (size_t)ctile[c] * RING + cpos[c];
+  }
+  __syncthreads();
   real* M = fa.Mout;
-  real drho = gather(nq + 0, M[(size_t)(nq + M_DRHO) * P + n]);
-  const real jx = gather(nq + 1, M[(size_t)(nq + M_JX) * P + n]) + fa.dvx;
-  const real jy = gather(nq + 2, M[(size_t)(nq + M_JY) * P + n]) + fa.dvy;
-  real txx = 0, txy = 0, tyy = 0;
-  // four Q-nodes at a time: all their loads are issued before any store
-  for (int p0 = 0; p0 < nq; p0 += 4) {
-    real d[4];
+  const real* ex = fa.exports;
+  const size_t estride = ntiles * RING;
+  // planes j < nq: delta psi(q = j); j = nq, nq + 1, nq + 2: delta rho, J_x, J_y
+  // (the moment planes and the export planes use the same index)
+  const int nitems = (nq + 3) * NB;
+  for (int b0 = 0; b0 < nitems; b0 += FIX_T * FIX_BATCH) {
+    real v[FIX_BATCH];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) d[u] = p0 + u < nq ? M[(size_t)(p0 + u) * P + n] : real(0);
+    for (int u = 0; u < FIX_BATCH; ++u) {
+      const int it = b0 + u * FIX_T + tid;
+      if (it < nitems) {
+        const int j = it / NB, k = it - j * NB;
+        real w = M[(size_t)j * P + s_n[k]];
+        const uint32_t nc = s_nc[k];
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (p0 + u < nq) d[u] = gather(p0 + u, d[u]) + fa.dpsi[p0 + u];
+        for (int c = 0; c < 3; ++c)
+          if (c < (int)nc) w += ex[(size_t)j * estride + s_e[c][k]];
+        v[u] = w;
+      }
+    }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int p = p0 + u;
-      if (p < nq) {
-        M[(size_t)p * P + n] = d[u];
-        drho += d[u];
-        const real Qx = a.tab.qx[p], Qy = a.tab.qy[p], Fx = a.tab.fx[p], Fy = a.tab.fy[p];
-        txx += d[u] * Fx * Qx;
-        txy += d[u] * Fx * Qy;
-        tyy += d[u] * Fy * Qy;
+    for (int u = 0; u < FIX_BATCH; ++u) {
+      const int it = b0 + u * FIX_T + tid;
+      if (it < nitems) {
+        const int j = it / NB, k = it - j * NB;
+        if (j < nq) {
+          const real d = v[u] + fa.dpsi[j];
+          M[(size_t)j * P + s_n[k]] = d;
+          s_d[j * NB + k] = d;
+        } else if (j == nq) {
+          s_d[nq * NB + k] = v[u];
+        } else {
+          M[(size_t)j * P + s_n[k]] = v[u] + (j == nq + 1 ? fa.dvx : fa.dvy);
+        }
       }
     }
   }
-  M[(size_t)(nq + M_DRHO) * P + n] = drho;
-  M[(size_t)(nq + M_JX) * P + n] = jx;
-  M[(size_t)(nq + M_JY) * P + n] = jy;
-  M[(size_t)(nq + M_THXX) * P + n] = a.hl2h * txx;
-  M[(size_t)(nq + M_THXY) * P + n] = a.hl2h * txy;
-  M[(size_t)(nq + M_THYY) * P + n] = a.hl2h * tyy;
+  __syncthreads();
+  if (tid < NB) {
+    const size_t n = s_n[tid];
+    real drho = s_d[nq * NB + tid], txx = 0, txy = 0, tyy = 0;
+    for (int p = 0; p < nq; ++p) {
+      const real d = s_d[p * NB + tid];
+      drho += d;
+      const real Qx = a.tab.qx[p], Qy = a.tab.qy[p], Fx = a.tab.fx[p], Fy = a.tab.fy[p];
+      txx += d * Fx * Qx;
+      txy += d * Fx * Qy;
+      tyy += d * Fy * Qy;
+    }
+    M[(size_t)(nq + M_DRHO) * P + n] = drho;
+    M[(size_t)(nq + M_THXX) * P + n] = a.hl2h * txx;
+    M[(size_t)(nq + M_THXY) * P + n] = a.hl2h * txy;
+    M[(size_t)(nq + M_THYY) * P + n] = a.hl2h * tyy;
+  }
 }
 
 template <typename real>
-__global__ void __launch_bounds__(128) fixup_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
-  fixup_body<real, TY>(a, fa, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
+__global__ void __launch_bounds__(FIX_T) fixup_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
+  extern __shared__ __align__(16) unsigned char fix_raw[];
+  fixup_body<real, TY>(a, fa, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y, (real*)fix_raw);
 }
 
 // ---------------------------------------------------------------- batches
@@ -727,7 +760,7 @@ step_fused_batch_kernel(const BatchRun<real>* runs, const int* tile_start, int n
 }
 
 template <typename real, int H>
-__global__ void __launch_bounds__(128) fixup_batch_kernel(const BatchRun<real>* runs,
+__global__ void __launch_bounds__(FIX_T) fixup_batch_kernel(const BatchRun<real>* runs,
                                                           const int* tile_start, int nruns,
                                                           int parity) {
   __shared__ KernelArgs<real> sa;
@@ -740,7 +773,8 @@ __global__ void __launch_bounds__(128) fixup_batch_kernel(const BatchRun<real>* 
   copy_words(&sf, &br.f[parity], threadIdx.x, blockDim.x);
   __syncthreads();
   const int local = blockIdx.x - tile_start[s_run];
-  fixup_body<real, H>(sa, sf, local % br.ntx, local / br.ntx, br.ntx, br.nty);
+  extern __shared__ __align__(16) unsigned char fix_raw[];
+  fixup_body<real, H>(sa, sf, local % br.ntx, local / br.ntx, br.ntx, br.nty, (real*)fix_raw);
 }
 
 }  // namespace
@@ -802,7 +836,13 @@ cudaError_t launch_step_fused(const KernelArgs<real>& a, const FusedArgs<real>& 
 
 template <typename real>
 cudaError_t launch_fixup(const KernelArgs<real>& a, const FusedArgs<real>& f, cudaStream_t s) {
-  fixup_kernel<real><<<dim3(a.nx / TX, a.ny / TY), 128, 0, s>>>(a, f);
+  const size_t smem = fix_smem_bytes<real, TY>(a.nq);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(fixup_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  fixup_kernel<real><<<dim3(a.nx / TX, a.ny / TY), FIX_T, smem, s>>>(a, f);
   return cudaGetLastError();
 }
 
@@ -830,7 +870,13 @@ cudaError_t launch_batch_step_h(const BatchRun<float>* runs, const int* tile_sta
       runs, tile_start, nruns, parity);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  fixup_batch_kernel<float, H><<<total_tiles, 128, 0, s>>>(runs, tile_start, nruns, parity);
+  const size_t fsmem = fix_smem_bytes<float, H>(max_nq);
+  if (fsmem > 48 * 1024) {
+    e = cudaFuncSetAttribute(fixup_batch_kernel<float, H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)fsmem);
+    if (e != cudaSuccess) return e;
+  }
+  fixup_batch_kernel<float, H><<<total_tiles, FIX_T, fsmem, s>>>(runs, tile_start, nruns, parity);
   return cudaGetLastError();
 }
 
