@@ -44,7 +44,7 @@ struct Geo {
   static constexpr int NT = TX * H;
   static constexpr int RING = 2 * (TX + 2) + 2 * H;
   static constexpr int HY = H + 4;
-  static constexpr int HSZ = (TX + 4) * (H + 4);
+  static constexpr int HSZ = (TX + 2) * (H + 2);
   static constexpr int MINB = NT >= 512 ? 1 : 512 / NT;   // blocks per SM at 128 registers
 };
 
@@ -128,33 +128,50 @@ __device__ __forceinline__ void load_vec(T* out, const T* src) {
   }
 }
 
-constexpr int HX = TX + 4;       // exchange-buffer row: the tile plus a 2-node zero halo
+// The GQ = 16 signed bytes of a Q-node's target table, from one 16-byte load.
+__device__ __forceinline__ void load_targets(int* out, const int8_t* src) {
+  const int4 v = *reinterpret_cast<const int4*>(src);
+  const int w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+  for (int k = 0; k < 16; ++k) out[k] = (int)(int8_t)(w[k >> 2] >> (8 * (k & 3)));
+}
+
+// Exchange buffer: per velocity a plane of (H + 2) rows of HX = TX + 2 cells,
+// the tile plus a one-node zero halo, and two zero rows before the first and
+// after the last plane. A ring node's pull of a velocity that cannot reach it
+// from the tile falls up to two nodes out; in this layout such a read wraps
+// into a halo cell of the same or the neighbouring plane (or the end rows),
+// which all stay zero, so the ring sums need neither masks nor a wider halo.
+// (Keeping shared memory small matters: it leaves the L1 room for the pulls.)
+constexpr int HX = TX + 2;
+constexpr int HPAD = 2 * HX;     // zero cells before the first and after the last plane
 constexpr int DQ = 28;           // per-Q-node stride of the shift table (vector loads)
-constexpr int GQ = 12;           // per-Q-node stride of the target table (vector loads)
+constexpr int GQ = 16;           // per-Q-node stride of the target table (bytes, one vector load)
 
 template <typename real>
 struct Smem {
-  real* hb;          // [20][HY][HX] collided values of the r-moving velocities, zero halo
+  real* hb;          // [20][H+2][HX] collided values of the r-moving velocities, zero halo
   real* A;           // [nq][NT] own-node arrival sums per Q-node
   real* Ar;          // [nq][RING] ring-node arrival sums per Q-node
-  real* Ux;          // [H+2][TX+2]
-  real* Uy;
+  real* Ux;          // [H+2][TX+2] velocity on the tile and its ring; shares the
+  real* Uy;          // space of A, which is cleared only after its last use
   const void** pptr; // [nq*25] source plane of each pull in the current source buffer,
                      // or (lean variant) its element offset as a long long
   real* delta;       // [nq][DQ] pull shift differences
-  int* tgt;          // [nq][GQ] target Q-node of each Q-displacement group, -1: bounce-back
+  int8_t* tgt;       // [nq][GQ] target Q-node of each Q-displacement group, -1: bounce-back
 };
 
 template <typename real, int H>
 __host__ __device__ constexpr size_t smem_layout(int nq, size_t* o_A, size_t* o_Ar, size_t* o_U,
                                                  size_t* o_poff, size_t* o_delta, size_t* o_tgt) {
-  size_t o = sizeof(real) * 20 * Geo<H>::HSZ;
+  size_t o = sizeof(real) * (20 * Geo<H>::HSZ + 2 * HPAD);
+  o = (o + 15) & ~(size_t)15;
   *o_A = o;
-  o += sizeof(real) * (size_t)nq * Geo<H>::NT;
+  *o_U = o;
+  const size_t a_elems = (size_t)nq * Geo<H>::NT, u_elems = 2 * (H + 2) * (TX + 2);
+  o += sizeof(real) * (a_elems > u_elems ? a_elems : u_elems);
   *o_Ar = o;
   o += sizeof(real) * (size_t)nq * Geo<H>::RING;
-  *o_U = o;
-  o += sizeof(real) * 2 * (H + 2) * (TX + 2);
   o = (o + 15) & ~(size_t)15;
   *o_poff = o;
   o += sizeof(long long) * (size_t)nq * 25;
@@ -163,7 +180,7 @@ __host__ __device__ constexpr size_t smem_layout(int nq, size_t* o_A, size_t* o_
   o += sizeof(real) * (size_t)nq * DQ;
   o = (o + 15) & ~(size_t)15;
   *o_tgt = o;
-  o += sizeof(int) * (size_t)nq * GQ;
+  o += (size_t)nq * GQ;
   return o;
 }
 
@@ -172,14 +189,14 @@ __device__ __forceinline__ Smem<real> carve(unsigned char* base, int nq) {
   size_t oA, oAr, oU, op, od, ot;
   smem_layout<real, H>(nq, &oA, &oAr, &oU, &op, &od, &ot);
   Smem<real> s;
-  s.hb = (real*)base;
+  s.hb = (real*)base + HPAD;
   s.A = (real*)(base + oA);
   s.Ar = (real*)(base + oAr);
   s.Ux = (real*)(base + oU);
   s.Uy = s.Ux + (H + 2) * (TX + 2);
   s.pptr = (const void**)(base + op);
   s.delta = (real*)(base + od);
-  s.tgt = (int*)(base + ot);
+  s.tgt = (int8_t*)(base + ot);
   return s;
 }
 
@@ -243,7 +260,7 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
   // ---- stage: tables, zeroed accumulators and exchange halo, U on the tile and its ring
   for (int k = tid; k < nq * GQ; k += NT) {
     const int q = k / GQ, g = k % GQ;
-    sm.tgt[k] = g < 9 ? fa.tgt[q * 9 + g] : -1;
+    sm.tgt[k] = (int8_t)(g < 9 ? fa.tgt[q * 9 + g] : -1);
   }
   for (int k = tid; k < nq * 25; k += NT) {
     if constexpr (LEAN) reinterpret_cast<long long*>(sm.pptr)[k] = fa.poff[k];
@@ -253,8 +270,7 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
     const int q = k / DQ, i = k % DQ;
     sm.delta[k] = i < 25 ? a.tab.delta[q * 25 + i] : real(0);
   }
-  for (int k = tid; k < 20 * HSZ; k += NT) sm.hb[k] = real(0);
-  for (int p = 0; p < nq; ++p) sm.A[p * NT + tid] = real(0);
+  for (int k = tid; k < 20 * HSZ + 2 * HPAD; k += NT) sm.hb[k - HPAD] = real(0);
   for (int k = tid; k < nq * RING; k += NT) sm.Ar[k] = real(0);
   for (int k = tid; k < (TX + 2) * (TY + 2); k += NT) {
     const int hx = k % (TX + 2), hy = k / (TX + 2);
@@ -277,11 +293,11 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
 
   // exchange-buffer cells: own node, and (threads < RING) one ring node; a
   // source outside the tile falls on the zero halo, so the sums need no masks
-  const int hcell = (ly + 2) * HX + (lx + 2);
+  const int hcell = (ly + 1) * HX + (lx + 1);
   const bool ring_thread = tid < RING;
   int rex = 0, rey = 0;
   if (ring_thread) ring_coords<H>(tid, rex, rey);
-  const int rcell = (rey + 2) * HX + (rex + 2);
+  const int rcell = (rey + 1) * HX + (rex + 1);
 
   const real rho = a.rho0 + Min[(size_t)(nq + M_DRHO) * P + n];
   const real force = rho * a.tab.arow[y];
@@ -291,7 +307,7 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
   // Bounce-back mask of Q-node q: bit g set when q + displacement g leaves the disk.
   auto bounce_mask = [&](int q) {
     int tv[GQ];
-    load_vec<GQ>(tv, sm.tgt + q * GQ);
+    load_targets(tv, sm.tgt + q * GQ);
     uint32_t m = 0;
 #pragma unroll
     for (int g = 0; g < 9; ++g)
@@ -378,6 +394,9 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
     });
   }
   __syncthreads();
+  // every thread has read the staged velocity (it shares A's space): clear
+  // this thread's column of the arrival sums
+  for (int p = 0; p < nq; ++p) sm.A[p * NT + tid] = real(0);
 
   // a learned block's pending increment: dpsi(q) = p0(q) (B0 Qx^2 + B1 Qx Qy + B2 Qy^2 + B3)
   real B0 = 0, B1 = 0, B2 = 0, B3 = 0, rpt0 = 0;
@@ -526,7 +545,7 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
       acc<cv.ry>(jy_arr, v);
     });
     int tq[GQ];
-    load_vec<GQ>(tq, sm.tgt + q * GQ);
+    load_targets(tq, sm.tgt + q * GQ);
 #pragma unroll
     for (int g = 0; g < 9; ++g) {
       const int t = g == 4 ? q : tq[g];
@@ -546,7 +565,7 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
       });
 #pragma unroll
       for (int g = 0; g < 9; ++g) {
-        const int t = g == 4 ? q : sm.tgt[q * GQ + g];
+        const int t = g == 4 ? q : tq[g];
         if (t >= 0) sm.Ar[t * RING + tid] += gr[g];
       }
     }
@@ -808,7 +827,9 @@ size_t fused_export_capacity(int nx, int ny, int nq) {
 }
 
 bool fused_supported(int nx, int ny, int nq, size_t real_bytes, int ty) {
-  return nx % TX == 0 && ny % ty == 0 && fused_smem_bytes(nq, real_bytes, ty) <= 227 * 1024;
+  // nq <= 127: the target table holds Q-node indices in signed bytes
+  return nx % TX == 0 && ny % ty == 0 && nq <= 127 &&
+         fused_smem_bytes(nq, real_bytes, ty) <= 227 * 1024;
 }
 
 template <typename real, typename S>
