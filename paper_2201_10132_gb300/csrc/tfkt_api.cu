@@ -138,11 +138,8 @@ size_t store_size(const Lattice& L) {
   return L.precision == TFKT_FP64 ? 8 : (L.precision == TFKT_FP16 ? 2 : 4);
 }
 
-int diag_blocks_for(const Lattice& L) {
-  const size_t N = (size_t)L.nx * L.ny;
-  const size_t want = (N + DIAG_THREADS - 1) / DIAG_THREADS;
-  return (int)(want < 608 ? want : 608);
-}
+// Blocks of the diagnostics reduction: one or more rows each, at most 8 per SM.
+int diag_blocks_for(const Lattice& L) { return L.ny < 8 * 152 ? L.ny : 8 * 152; }
 
 // Workspace layout; returns the total size.
 size_t layout(const Lattice& L, Workspace* w) {
@@ -373,10 +370,8 @@ tfkt_status init_state(Ctx* c, const double* perturb) {
   }
   a.perturb = dpert;
   a.dst = (char*)c->ws.base + c->ws.off_pop[0];
-  TFKT_CUDA(c, launch_init<real, S>(a, c->stream));
+  TFKT_CUDA(c, launch_init<real, S>(a, c->stream));   // populations and their moments
   c->cur = 0;
-  KernelArgs<real> m = make_args<real>(c);
-  TFKT_CUDA(c, launch_moments<real, S>(m, c->stream));
   c->m_valid = true;
   TFKT_CUDA(c, cudaStreamSynchronize(c->stream));
   return TFKT_OK;

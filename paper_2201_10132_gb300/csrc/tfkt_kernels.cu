@@ -71,6 +71,10 @@ __device__ __forceinline__ void mixture_velocity(const KernelArgs<real>& a, int 
 // U = base flow + perturbation, J^r_eq = psi U, J^Q_eq = psi (Q . grad U -
 // kappa Q) (grad_r psi = 0). Each value is written to the slot that the
 // first pull reads for it, so the first step starts from exactly this state.
+// For the same reason the pulled populations of a node are its own stored
+// values: the kernel also writes the state's moment planes M, rebuilding each
+// value from its stored form and summing exactly as moments_kernel does, so
+// the moments need no second pass over the populations.
 template <typename real, typename S>
 __global__ void __launch_bounds__(256) init_kernel(KernelArgs<real> a) {
   S* __restrict__ dst = (S*)a.dst;
@@ -95,18 +99,26 @@ __global__ void __launch_bounds__(256) init_kernel(KernelArgs<real> a) {
   const Offsets off = node_offsets(x, y, nx, ny, a.pitch);
   const size_t P = a.plane;
   const real usq = ux * ux + uy * uy;
+  real drho = 0, jx = 0, jy = 0;
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
     const real cu = real(c9x(i)) * ux + real(c9y(i)) * uy;
     const real h = real(w9(i)) * (real(3) * cu + real(4.5) * cu * cu - real(1.5) * usq);
-    dst[(size_t)i * P + off.o[shift_index(-c9x(i), -c9y(i))]] = to_store<S>(h);
+    const S st = to_store<S>(h);
+    dst[(size_t)i * P + off.o[shift_index(-c9x(i), -c9y(i))]] = st;
+    const real v = from_store<real>(st);
+    drho += v;
+    jx += real(c9x(i)) * v;
+    jy += real(c9y(i)) * v;
   }
+  real txx = 0, txy = 0, tyy = 0;
   for (int q = 0; q < a.nq; ++q) {
     const real Qx = a.tab.qx[q], Qy = a.tab.qy[q], psi = a.tab.psi0[q];
     const real Fx = a.tab.fx[q], Fy = a.tab.fy[q];
     const real jrx = psi * ux, jry = psi * uy;
     const real jqx = psi * (Qx * G00 + Qy * G10 - a.kappa * Fx);
     const real jqy = psi * (Qx * G01 + Qy * G11 - a.kappa * Fy);
+    real dpsi = 0, rx = 0, ry = 0;
 #pragma unroll
     for (int i = 0; i < 25; ++i) {
       const V4 c = c25(i);
@@ -115,9 +127,29 @@ __global__ void __launch_bounds__(256) init_kernel(KernelArgs<real> a) {
       const int e = a.tab.pull[q * 25 + i];
       const size_t o = e >= 0 ? off.o[shift_index(-c.rx, -c.ry)] : off.o[4];
       const int p = e >= 0 ? e : ~e;
-      dst[(size_t)p * P + o] = to_store<S>((h - a.tab.delta[q * 25 + i]) * a.pscale);
+      const S st = to_store<S>((h - a.tab.delta[q * 25 + i]) * a.pscale);
+      dst[(size_t)p * P + o] = st;
+      const real v = from_store<real>(st) * a.pinv + a.tab.delta[q * 25 + i];
+      dpsi += v;
+      rx += real(c.rx) * v;
+      ry += real(c.ry) * v;
     }
+    a.M[(size_t)q * P + off.o[4]] = dpsi;
+    drho += dpsi;
+    jx += rx;
+    jy += ry;
+    txx += dpsi * Fx * Qx;
+    txy += dpsi * Fx * Qy;
+    tyy += dpsi * Fy * Qy;
   }
+  const size_t n = off.o[4];
+  const int nq = a.nq;
+  a.M[(size_t)(nq + M_DRHO) * P + n] = drho;
+  a.M[(size_t)(nq + M_JX) * P + n] = jx;
+  a.M[(size_t)(nq + M_JY) * P + n] = jy;
+  a.M[(size_t)(nq + M_THXX) * P + n] = a.hl2h * txx;
+  a.M[(size_t)(nq + M_THXY) * P + n] = a.hl2h * txy;
+  a.M[(size_t)(nq + M_THYY) * P + n] = a.hl2h * tyy;
 }
 
 // --------------------------------------------------------------- moments
@@ -526,26 +558,55 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Block partial sums of the global diagnostics (Sec. VII follows the
+// enstrophy and Q_rms). A block takes whole rows, a thread every DIAG_THREADS-th
+// node of a row. Per node only what the sums need is formed, in the context's
+// precision and as deviations from the rest state (sum_q delta psi, and
+// sum_q delta psi Q^2 for Q_rms); the rest-state constants are added once.
+// Values are summed in that precision along a row segment of one thread and
+// in FP64 across segments, blocks and the final reduction: FP64 arithmetic,
+// slow on this GPU, stays out of the per-node work of FP32 contexts, while
+// FP64 contexts keep FP64 throughout.
 template <typename real>
 __global__ void __launch_bounds__(DIAG_THREADS) diag_partial_kernel(KernelArgs<real> a,
                                                                     double* partials) {
+  const int nq = a.nq;
+  const size_t P = a.plane;
+  real s0 = 0;   // sum_q psi0(q) |Q|^2 of the rest state
+  for (int q = 0; q < nq; ++q) {
+    const real Qx = a.tab.qx[q], Qy = a.tab.qy[q];
+    s0 += a.tab.psi0[q] * (Qx * Qx + Qy * Qy);
+  }
   double acc[TFKT_NDIAG] = {0, 0, 0, 0, 0, 0, 0, 0};
-  const size_t N = (size_t)a.nx * a.ny;
-  for (size_t k = (size_t)blockIdx.x * DIAG_THREADS + threadIdx.x; k < N;
-       k += (size_t)gridDim.x * DIAG_THREADS) {
-    const int x = int(k % a.nx), y = int(k / a.nx);
-    double f[TFKT_NFIELDS];
-    node_fields(a, x, y, f);
-    const double rho = f[TFKT_F_RHO_S] + f[TFKT_F_PSI_TOT];
-    const double ux = f[TFKT_F_UX], uy = f[TFKT_F_UY], w = f[TFKT_F_VORT];
-    acc[TFKT_D_MASS_S] += f[TFKT_F_RHO_S];
-    acc[TFKT_D_MASS_P] += f[TFKT_F_PSI_TOT];
-    acc[TFKT_D_PX] += rho * ux;
-    acc[TFKT_D_PY] += rho * uy;
-    acc[TFKT_D_KE] += 0.5 * rho * (ux * ux + uy * uy);
-    acc[TFKT_D_ENSTROPHY] += 0.5 * w * w;
-    acc[TFKT_D_QRMS_MEAN] += f[TFKT_F_QRMS];
-    acc[TFKT_D_EY2] += uy * uy;
+  for (int y = blockIdx.x; y < a.ny; y += gridDim.x) {
+    const int ym = y == 0 ? a.ny - 1 : y - 1, yp = y == a.ny - 1 ? 0 : y + 1;
+    real r[TFKT_NDIAG] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int x = threadIdx.x; x < a.nx; x += DIAG_THREADS) {
+      const size_t n = (size_t)y * a.pitch + x;
+      real dpt = 0, sq = 0;
+      for (int q = 0; q < nq; ++q) {
+        const real m = a.M[(size_t)q * P + n];
+        const real Qx = a.tab.qx[q], Qy = a.tab.qy[q];
+        dpt += m;
+        sq += m * (Qx * Qx + Qy * Qy);
+      }
+      const real drho = a.M[(size_t)(nq + M_DRHO) * P + n];
+      const real pt = a.psi_tot0 + dpt, rho = a.rho0 + drho;
+      const real ux = a.U[n], uy = a.U[P + n];
+      const int xm = x == 0 ? a.nx - 1 : x - 1, xp = x == a.nx - 1 ? 0 : x + 1;
+      const real w = real(0.5) * (a.U[P + (size_t)y * a.pitch + xp] - a.U[P + (size_t)y * a.pitch + xm]) -
+                     real(0.5) * (a.U[(size_t)yp * a.pitch + x] - a.U[(size_t)ym * a.pitch + x]);
+      r[TFKT_D_MASS_S] += drho - dpt;   // rho_s minus its rest value rho0 - psi_tot0
+      r[TFKT_D_MASS_P] += dpt;          // psi_tot minus psi_tot0
+      r[TFKT_D_PX] += rho * ux;
+      r[TFKT_D_PY] += rho * uy;
+      r[TFKT_D_KE] += real(0.5) * rho * (ux * ux + uy * uy);
+      r[TFKT_D_ENSTROPHY] += real(0.5) * w * w;
+      r[TFKT_D_QRMS_MEAN] += pt != real(0) ? sqrt(a.l2 * (s0 + sq) / pt) : real(0);
+      r[TFKT_D_EY2] += uy * uy;
+    }
+#pragma unroll
+    for (int j = 0; j < TFKT_NDIAG; ++j) acc[j] += double(r[j]);
   }
   __shared__ double red[DIAG_THREADS / 32][TFKT_NDIAG];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -562,10 +623,14 @@ __global__ void __launch_bounds__(DIAG_THREADS) diag_partial_kernel(KernelArgs<r
   }
 }
 
-__global__ void diag_final_kernel(const double* partials, int nblocks, double inv_n, double* out) {
+// base_s, base_p: the masses of the rest state, N (rho0 - psi_tot0) and N psi_tot0.
+__global__ void diag_final_kernel(const double* partials, int nblocks, double inv_n, double base_s,
+                                  double base_p, double* out) {
   if (threadIdx.x < TFKT_NDIAG) {
     double s = 0;
     for (int b = 0; b < nblocks; ++b) s += partials[(size_t)b * TFKT_NDIAG + threadIdx.x];
+    if (threadIdx.x == TFKT_D_MASS_S) s += base_s;
+    if (threadIdx.x == TFKT_D_MASS_P) s += base_p;
     out[threadIdx.x] = threadIdx.x == TFKT_D_QRMS_MEAN ? s * inv_n : s;
   }
 }
@@ -618,7 +683,10 @@ cudaError_t launch_diag(const KernelArgs<real>& a, double* partials, int nblocks
   diag_partial_kernel<real><<<nblocks, DIAG_THREADS, 0, s>>>(a, partials);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  diag_final_kernel<<<1, 32, 0, s>>>(partials, nblocks, 1.0 / ((double)a.nx * a.ny), out);
+  const double N = (double)a.nx * a.ny;
+  diag_final_kernel<<<1, 32, 0, s>>>(partials, nblocks, 1.0 / N,
+                                     N * ((double)a.rho0 - (double)a.psi_tot0), N * (double)a.psi_tot0,
+                                     out);
   return cudaGetLastError();
 }
 

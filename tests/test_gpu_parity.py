@@ -147,6 +147,7 @@ def test_fp32_within_tolerance(T, oracle_mod, case):
     with T.Solver(p, pert) as s:
         s.step(steps)
         g = s.moments()
+        diag = s.diagnostics()
     f = o.fields()
     uscale = max(np.abs(f["ux"]).max(), np.abs(f["uy"]).max())
     for k in FIELDS:
@@ -154,6 +155,19 @@ def test_fp32_within_tolerance(T, oracle_mod, case):
         scale = uscale if k in ("ux", "uy", "vort") else np.abs(f[k]).max()
         err = np.abs(g[k] - f[k]).max() / scale
         assert err < 2e-5, (k, err)
+    # global diagnostics (FP32 per node, FP64 sums): each within what the field
+    # tolerance allows summed over the grid (du = 2e-5 of the velocity scale)
+    od = o.diagnostics()
+    du = 2e-5 * uscale
+    rho = f["rho_s"] + f["psi_tot"]
+    tol = {"mass_s": 2e-5 * od["mass_s"], "mass_p": 2e-5 * max(od["mass_p"], 1e-30),
+           "px": 2 * du * rho.sum(), "py": 2 * du * rho.sum(),
+           "ke": 2 * du * (rho * (np.abs(f["ux"]) + np.abs(f["uy"]))).sum() + 1e-30,
+           "enstrophy": 4 * du * np.abs(f["vort"]).sum() + 1e-30,
+           "qrms_mean": 2e-5 * max(od["qrms_mean"], 1e-30),
+           "ey2": 2 * du * np.abs(f["uy"]).sum() + 1e-30}
+    for k, t in tol.items():
+        assert abs(diag[k] - od[k]) <= t, (k, diag[k], od[k], t)
 
 
 @pytest.mark.parametrize("case", [CASES[1], CASES[7], CASES[9]])
