@@ -159,11 +159,14 @@ __device__ __forceinline__ void node_features(const KernelArgs<float>& a, const 
 }
 
 // One block per judge tile: the network's C_new for every node, the tile's
-// largest disagreement with the plain rate, and the fallback.
-__global__ void __launch_bounds__(256) net_kernel(KernelArgs<float> a, LpmArgs l, MlpDev net) {
-  __shared__ __align__(16) MlpShared s;
-  __shared__ float red[256];
-  const int tid = threadIdx.x;
+// largest disagreement with the plain rate, and the fallback. Each warp takes
+// 32 nodes at a time: every lane forms its node's features, and the warp runs
+// the network on the tensor cores (mlp_warp_tc).
+constexpr int NET_THREADS = 256;
+__global__ void __launch_bounds__(NET_THREADS) net_kernel(KernelArgs<float> a, LpmArgs l, MlpDev net) {
+  extern __shared__ __align__(16) unsigned char net_smem[];
+  __shared__ float red[NET_THREADS];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const size_t P = a.plane;
   const int T = l.tile;
   const int tx0 = blockIdx.x * T, ty0 = blockIdx.y * T;
@@ -180,23 +183,45 @@ __global__ void __launch_bounds__(256) net_kernel(KernelArgs<float> a, LpmArgs l
     }
     return;
   }
-  mlp_stage(s, net.master, net.wmat, tid, blockDim.x);
+  MlpTc& s = *reinterpret_cast<MlpTc*>(net_smem);
+  float* Xw = reinterpret_cast<float*>(net_smem + ((sizeof(MlpTc) + 15) & ~(size_t)15)) +
+              (size_t)warp * TC_WARP_FLOATS;
+  float* Ow = Xw + TC_ROWS * TC_XLD;
+  mlp_stage_tc(s, net.master, net.wmat, tid, blockDim.x);
   __syncthreads();
   float worst = 0.f;
-  for (int k = tid; k < T * T; k += blockDim.x) {
+  const int nwarps = blockDim.x >> 5;
+  for (int base = warp * TC_ROWS; base < T * T; base += nwarps * TC_ROWS) {   // warp-uniform
+    const int k = base + lane;
     const int x = tx0 + k % T, y = ty0 + k / T;
-    if (x >= a.nx || y >= a.ny) continue;
-    const size_t n = (size_t)y * a.pitch + x;
-    float f[NIN], cdep[3], o[NOUT];
-    node_features(a, l, x, y, f, cdep);
-    mlp_forward(s, f, o);
-    for (int c = 0; c < 3; ++c) {
-      const float cn = cdep[c] + l.ce * o[c];
-      Cn[(size_t)c * P + n] = cn;
-      const float c1 = C1[(size_t)c * P + n];
-      const float plain = c1 + Kf * (c1 - Cp[(size_t)c * P + n]);
-      worst = fmaxf(worst, fabsf(cn - plain) / l.ce);
+    const bool ok = k < T * T && x < a.nx && y < a.ny;
+    float f[NIN], cdep[3] = {0.f, 0.f, 0.f};
+    float* xr = Xw + lane * TC_XLD;
+    if (ok) {
+      node_features(a, l, x, y, f, cdep);
+#pragma unroll
+      for (int i = 0; i < NIN; ++i) xr[i] = (f[i] - s.mx[i]) * s.rsx[i];
+    } else {
+#pragma unroll
+      for (int i = 0; i < NIN; ++i) xr[i] = 0.f;
     }
+#pragma unroll
+    for (int i = NIN; i < TC_K1; ++i) xr[i] = 0.f;
+    __syncwarp();
+    mlp_warp_tc(s, Xw, Ow, lane);
+    __syncwarp();
+    if (ok) {
+      const size_t n = (size_t)y * a.pitch + x;
+      for (int c = 0; c < 3; ++c) {
+        const float o = Ow[lane * 4 + c] * s.st[c] + s.mt[c];
+        const float cn = cdep[c] + l.ce * o;
+        Cn[(size_t)c * P + n] = cn;
+        const float c1 = C1[(size_t)c * P + n];
+        const float plain = c1 + Kf * (c1 - Cp[(size_t)c * P + n]);
+        worst = fmaxf(worst, fabsf(cn - plain) / l.ce);
+      }
+    }
+    __syncwarp();   // the next pass overwrites this warp's rows
   }
   red[tid] = worst;
   __syncthreads();
@@ -520,7 +545,9 @@ extern "C" tfkt_status tfkt_lpm_run(tfkt_ctx* cc, const tfkt_mlp* net, const tfk
     LPM_CUDA(launch_velocity<float>(a, st));
     prepare_kernel<<<grid, blk, 0, st>>>(a, l);
     LPM_CUDA(cudaGetLastError());
-    net_kernel<<<tiles, 256, 0, st>>>(a, l, nd);
+    const size_t nsm = tc_smem_bytes(NET_THREADS / 32);
+    LPM_CUDA(cudaFuncSetAttribute(net_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nsm));
+    net_kernel<<<tiles, NET_THREADS, nsm, st>>>(a, l, nd);
     LPM_CUDA(cudaGetLastError());
     for (int j = 0; j < o->K; ++j) {
       KernelArgs<float> aj = ctx_args<float>(c);

@@ -24,21 +24,34 @@ __device__ __forceinline__ float gelu_grad(float z) {
          z * expf(-0.5f * z * z) * 0.39894228040143268f;
 }
 
+// Inference on raw samples: one warp per TC_ROWS samples, the network on the
+// tensor cores (mlp_warp_tc).
 __global__ void __launch_bounds__(128) forward_kernel(const float* __restrict__ master,
                                                       const __nv_bfloat16* __restrict__ wmat,
                                                       const float* __restrict__ X, int64_t n,
                                                       float* __restrict__ Y) {
-  __shared__ __align__(16) MlpShared s;
-  mlp_stage(s, master, wmat, threadIdx.x, blockDim.x);
+  extern __shared__ __align__(16) unsigned char fw_smem[];
+  MlpTc& s = *reinterpret_cast<MlpTc*>(fw_smem);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* Xw = reinterpret_cast<float*>(fw_smem + ((sizeof(MlpTc) + 15) & ~(size_t)15)) +
+              (size_t)warp * TC_WARP_FLOATS;
+  float* Ow = Xw + TC_ROWS * TC_XLD;
+  mlp_stage_tc(s, master, wmat, threadIdx.x, blockDim.x);
   __syncthreads();
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  float x[NIN], y[NOUT];
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // warp-uniform pass
+  const bool ok = k < n;
+  float* xr = Xw + lane * TC_XLD;
 #pragma unroll
-  for (int i = 0; i < NIN; ++i) x[i] = X[k * NIN + i];
-  mlp_forward(s, x, y);
+  for (int i = 0; i < NIN; ++i) xr[i] = ok ? (X[k * NIN + i] - s.mx[i]) * s.rsx[i] : 0.f;
 #pragma unroll
-  for (int j = 0; j < NOUT; ++j) Y[k * NOUT + j] = y[j];
+  for (int i = NIN; i < TC_K1; ++i) xr[i] = 0.f;
+  __syncwarp();
+  mlp_warp_tc(s, Xw, Ow, lane);
+  __syncwarp();
+  if (ok) {
+#pragma unroll
+    for (int j = 0; j < NOUT; ++j) Y[k * NOUT + j] = Ow[lane * 4 + j] * s.st[j] + s.mt[j];
+  }
 }
 
 struct TrainShared {
@@ -315,7 +328,8 @@ tfkt_status tfkt_mlp_forward(tfkt_mlp* net, const float* X, int64_t n, float* Y)
   if (!net || n < 0 || (n > 0 && (!X || !Y))) return fail(TFKT_EINVAL, "bad argument");
   if (n == 0) return TFKT_OK;
   const int64_t blocks = (n + 127) / 128;
-  forward_kernel<<<(unsigned)blocks, 128, 0, net->stream>>>(net->d.master, net->d.wmat, X, n, Y);
+  forward_kernel<<<(unsigned)blocks, 128, tc_smem_bytes(4), net->stream>>>(net->d.master, net->d.wmat,
+                                                                          X, n, Y);
   MLP_CUDA(cudaGetLastError());
   return TFKT_OK;
 }
