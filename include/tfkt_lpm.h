@@ -60,7 +60,10 @@ tfkt_status tfkt_mlp_destroy(tfkt_mlp* net);
 tfkt_status tfkt_mlp_get(tfkt_mlp* net, float* params);
 tfkt_status tfkt_mlp_set(tfkt_mlp* net, const float* params);
 
-/* Y = network(X) for n >= 0 samples (raw inputs, raw outputs). */
+/* Y = network(X) for n >= 0 samples (raw inputs, raw outputs). Runs on the
+   tensor cores: bfloat16 weights, each FP32 activation as a bfloat16 high part
+   plus a bfloat16 remainder, FP32 accumulation (within about 1e-5 of the FP32
+   forward pass). */
 tfkt_status tfkt_mlp_forward(tfkt_mlp* net, const float* X, int64_t n, float* Y);
 
 /* Loss L = (1/n) sum_n sum_j (o_nj - (t_nj - mt_j)/st_j)^2 of n >= 1 samples, o the

@@ -1,7 +1,8 @@
 // The learned macro-step's network: forward pass, loss and gradient by
 // backpropagation, and Adam, as hand-written kernels (bfloat16 matrices, FP32
-// arithmetic and accumulation). Gradients are summed per block of 128 samples
-// and the block partials in a fixed order, so results are reproducible.
+// accumulation; inference on the tensor cores, training on the CUDA cores in
+// FP32). Gradients are summed per block of 128 samples and the block partials
+// in a fixed order, so results are reproducible.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
