@@ -158,33 +158,56 @@ __global__ void __launch_bounds__(256) init_kernel(KernelArgs<real> a) {
 // spring force H phi_q Q).
 template <typename real, typename S>
 __global__ void __launch_bounds__(256) moments_kernel(KernelArgs<real> a) {
+  // The pull tables go to shared memory, and the populations of Q-node q + 1
+  // are loaded into each register as soon as Q-node q has used it, so the
+  // loads of one Q-node are in flight while the previous one is summed.
+  extern __shared__ __align__(16) unsigned char mom_smem[];
+  const int nq = a.nq;
+  real* s_delta = reinterpret_cast<real*>(mom_smem);
+  int* s_pull = reinterpret_cast<int*>(mom_smem + sizeof(real) * (size_t)nq * 25);
+  const int tid = threadIdx.y * TX + threadIdx.x;
+  for (int k = tid; k < nq * 25; k += TX * TY) {
+    s_delta[k] = a.tab.delta[k];
+    s_pull[k] = a.tab.pull[k];
+  }
+  __syncthreads();
   const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
   if (x >= a.nx || y >= a.ny) return;
   const Offsets off = node_offsets(x, y, a.nx, a.ny, a.pitch);
   const size_t P = a.plane;
   const size_t n = off.o[4];
   const S* __restrict__ src = (const S*)a.src;
+  auto pull = [&](int q, int i) {
+    const V4 c = c25(i);
+    const int e = s_pull[q * 25 + i];
+    const size_t o = e >= 0 ? off.o[shift_index(-c.rx, -c.ry)] : off.o[4];
+    return src[(size_t)(e >= 0 ? e : ~e) * P + o];
+  };
+  S h[25];
+  if (nq > 0) {
+#pragma unroll
+    for (int i = 0; i < 25; ++i) h[i] = pull(0, i);
+  }
   real drho = 0, jx = 0, jy = 0;
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
-    const real h = from_store<real>(src[(size_t)i * P + off.o[shift_index(-c9x(i), -c9y(i))]]);
-    drho += h;
-    jx += real(c9x(i)) * h;
-    jy += real(c9y(i)) * h;
+    const real v = from_store<real>(src[(size_t)i * P + off.o[shift_index(-c9x(i), -c9y(i))]]);
+    drho += v;
+    jx += real(c9x(i)) * v;
+    jy += real(c9y(i)) * v;
   }
   real txx = 0, txy = 0, tyy = 0;
-  for (int q = 0; q < a.nq; ++q) {
+  for (int q = 0; q < nq; ++q) {
+    const bool more = q + 1 < nq;
     real dpsi = 0, rx = 0, ry = 0;
 #pragma unroll
     for (int i = 0; i < 25; ++i) {
       const V4 c = c25(i);
-      const int e = a.tab.pull[q * 25 + i];
-      const size_t o = e >= 0 ? off.o[shift_index(-c.rx, -c.ry)] : off.o[4];
-      const int p = e >= 0 ? e : ~e;
-      const real h = from_store<real>(src[(size_t)p * P + o]) * a.pinv + a.tab.delta[q * 25 + i];
-      dpsi += h;
-      rx += real(c.rx) * h;
-      ry += real(c.ry) * h;
+      const real v = from_store<real>(h[i]) * a.pinv + s_delta[q * 25 + i];
+      if (more) h[i] = pull(q + 1, i);
+      dpsi += v;
+      rx += real(c.rx) * v;
+      ry += real(c.ry) * v;
     }
     a.M[(size_t)q * P + n] = dpsi;
     drho += dpsi;
@@ -195,7 +218,6 @@ __global__ void __launch_bounds__(256) moments_kernel(KernelArgs<real> a) {
     txy += dpsi * Fx * Qy;
     tyy += dpsi * Fy * Qy;
   }
-  const int nq = a.nq;
   a.M[(size_t)(nq + M_DRHO) * P + n] = drho;
   a.M[(size_t)(nq + M_JX) * P + n] = jx;
   a.M[(size_t)(nq + M_JY) * P + n] = jy;
@@ -221,8 +243,16 @@ template <typename real, typename S>
 __global__ void __launch_bounds__(256) step_kernel(KernelArgs<real> a) {
   __shared__ real sUx[TY + 2][TX + 2];
   __shared__ real sUy[TY + 2][TX + 2];
+  // pull tables in shared memory (dynamic: nq * 25 shift differences, then plane entries)
+  extern __shared__ __align__(16) unsigned char step_smem[];
+  real* s_delta = reinterpret_cast<real*>(step_smem);
+  int* s_pull = reinterpret_cast<int*>(step_smem + sizeof(real) * (size_t)a.nq * 25);
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  for (int k = tid; k < a.nq * 25; k += TX * TY) {
+    s_delta[k] = a.tab.delta[k];
+    s_pull[k] = a.tab.pull[k];
+  }
   for (int k = tid; k < (TX + 2) * (TY + 2); k += TX * TY) {
     const int hx = k % (TX + 2), hy = k / (TX + 2);
     const int gx = wrapi(x0 - 1 + hx, a.nx), gy = wrapi(y0 - 1 + hy, a.ny);
@@ -279,21 +309,40 @@ __global__ void __launch_bounds__(256) step_kernel(KernelArgs<real> a) {
     }
   }
 
-  // ---- polymer, one Q-node at a time
+  // ---- polymer, one Q-node at a time; the populations (and psi neighbours) of
+  // Q-node q + 1 are loaded while Q-node q is collided
   const size_t nxm = off.o[3], nxp = off.o[5], nym = off.o[1], nyp = off.o[7];
+  auto pull = [&](int q, int i) {
+    const V4 c = c25(i);
+    const int e = s_pull[q * 25 + i];
+    const size_t o = e >= 0 ? off.o[shift_index(-c.rx, -c.ry)] : off.o[4];
+    return from_store<real>(src[(size_t)(e >= 0 ? e : ~e) * P + o]);
+  };
+  real h[25], mn[4];
+  if (nq > 0) {
+#pragma unroll
+    for (int i = 0; i < 25; ++i) h[i] = pull(0, i);
+    mn[0] = a.M[nxp];
+    mn[1] = a.M[nxm];
+    mn[2] = a.M[nyp];
+    mn[3] = a.M[nym];
+  }
   for (int q = 0; q < nq; ++q) {
-    const real* Mq = a.M + (size_t)q * P;
-    const real dpx = real(0.5) * (Mq[nxp] - Mq[nxm]);
-    const real dpy = real(0.5) * (Mq[nyp] - Mq[nym]);
-    real h[25];
+    const bool more = q + 1 < nq;
+    const real dpx = real(0.5) * (mn[0] - mn[1]);
+    const real dpy = real(0.5) * (mn[2] - mn[3]);
+    if (more) {
+      const real* Mq = a.M + (size_t)(q + 1) * P;
+      mn[0] = Mq[nxp];
+      mn[1] = Mq[nxm];
+      mn[2] = Mq[nyp];
+      mn[3] = Mq[nym];
+    }
     real dpsi = 0, rx = 0, ry = 0, qx = 0, qy = 0;
 #pragma unroll
     for (int i = 0; i < 25; ++i) {
       const V4 c = c25(i);
-      const int e = a.tab.pull[q * 25 + i];
-      const size_t o = e >= 0 ? off.o[shift_index(-c.rx, -c.ry)] : off.o[4];
-      const int p = e >= 0 ? e : ~e;
-      h[i] = from_store<real>(src[(size_t)p * P + o]) * a.pinv + a.tab.delta[q * 25 + i];
+      h[i] = h[i] * a.pinv + s_delta[q * 25 + i];
       dpsi += h[i];
       rx += real(c.rx) * h[i];
       ry += real(c.ry) * h[i];
@@ -319,6 +368,7 @@ __global__ void __launch_bounds__(256) step_kernel(KernelArgs<real> a) {
       const real fdev = real(w25(i)) * (dpsi + real(3) * (mrx * real(c.rx) + mry * real(c.ry) +
                                                            mqx * real(c.qx) + mqy * real(c.qy)));
       dq[(size_t)i * P] = to_store<S>((a.om2b * h[i] + a.tb * fdev) * a.pscale);
+      if (more) h[i] = pull(q + 1, i);
     }
   }
 }
@@ -333,8 +383,16 @@ template <typename real, typename S>
 __global__ void __launch_bounds__(256) step_stress_kernel(KernelArgs<real> a) {
   __shared__ real sUx[TY + 2][TX + 2];
   __shared__ real sUy[TY + 2][TX + 2];
+  // pull tables in shared memory (dynamic: nq * 25 shift differences, then plane entries)
+  extern __shared__ __align__(16) unsigned char stress_smem[];
+  real* s_delta = reinterpret_cast<real*>(stress_smem);
+  int* s_pull = reinterpret_cast<int*>(stress_smem + sizeof(real) * (size_t)a.nq * 25);
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  for (int k = tid; k < a.nq * 25; k += TX * TY) {
+    s_delta[k] = a.tab.delta[k];
+    s_pull[k] = a.tab.pull[k];
+  }
   for (int k = tid; k < (TX + 2) * (TY + 2); k += TX * TY) {
     const int hx = k % (TX + 2), hy = k / (TX + 2);
     const int gx = wrapi(x0 - 1 + hx, a.nx), gy = wrapi(y0 - 1 + hy, a.ny);
@@ -396,23 +454,42 @@ __global__ void __launch_bounds__(256) step_stress_kernel(KernelArgs<real> a) {
     }
   }
 
-  // ---- polymer, one Q-node at a time
+  // ---- polymer, one Q-node at a time; the populations (and psi neighbours) of
+  // Q-node q + 1 are loaded while Q-node q is collided
   const size_t nxm = off.o[3], nxp = off.o[5], nym = off.o[1], nyp = off.o[7];
+  auto pull = [&](int q, int i) {
+    const V4 c = c25(i);
+    const int e = s_pull[q * 25 + i];
+    const size_t o = e >= 0 ? off.o[shift_index(-c.rx, -c.ry)] : off.o[4];
+    return from_store<real>(src[(size_t)(e >= 0 ? e : ~e) * P + o]);
+  };
+  real h[25], mn[4];
+  if (nq > 0) {
+#pragma unroll
+    for (int i = 0; i < 25; ++i) h[i] = pull(0, i);
+    mn[0] = a.M[nxp];
+    mn[1] = a.M[nxm];
+    mn[2] = a.M[nyp];
+    mn[3] = a.M[nym];
+  }
   for (int q = 0; q < nq; ++q) {
-    const real* Mq = a.M + (size_t)q * P;
-    const real dpx = real(0.5) * (Mq[nxp] - Mq[nxm]);
-    const real dpy = real(0.5) * (Mq[nyp] - Mq[nym]);
-    real h[25];
+    const bool more = q + 1 < nq;
+    const real dpx = real(0.5) * (mn[0] - mn[1]);
+    const real dpy = real(0.5) * (mn[2] - mn[3]);
+    if (more) {
+      const real* Mq = a.M + (size_t)(q + 1) * P;
+      mn[0] = Mq[nxp];
+      mn[1] = Mq[nxm];
+      mn[2] = Mq[nyp];
+      mn[3] = Mq[nym];
+    }
     real dpsi = 0;
     // second moments of the deviations: vv (3), v Qdot (4), Qdot Qdot (3)
     real rxx = 0, rxy = 0, ryy = 0, cxx = 0, cxy = 0, cyx = 0, cyy = 0, qxx = 0, qxy = 0, qyy = 0;
 #pragma unroll
     for (int i = 0; i < 25; ++i) {
       const V4 c = c25(i);
-      const int e = a.tab.pull[q * 25 + i];
-      const size_t o = e >= 0 ? off.o[shift_index(-c.rx, -c.ry)] : off.o[4];
-      const int p = e >= 0 ? e : ~e;
-      h[i] = from_store<real>(src[(size_t)p * P + o]) * a.pinv + a.tab.delta[q * 25 + i];
+      h[i] = h[i] * a.pinv + s_delta[q * 25 + i];
       dpsi += h[i];
       rxx += real(c.rx * c.rx) * h[i];
       rxy += real(c.rx * c.ry) * h[i];
@@ -451,6 +528,7 @@ __global__ void __launch_bounds__(256) step_stress_kernel(KernelArgs<real> a) {
       const real fss_dev = real(w25(i)) * (lin + real(4.5) * sdiag + real(9) * scross);
       const real feq_dev = real(w25(i)) * lin;
       dq[(size_t)i * P] = to_store<S>((a.om2b * h[i] + a.tb * (omr * fss_dev + rmix * feq_dev)) * a.pscale);
+      if (more) h[i] = pull(q + 1, i);
     }
   }
 }
@@ -646,15 +724,33 @@ cudaError_t launch_init(const KernelArgs<real>& a, cudaStream_t s) {
 }
 template <typename real, typename S>
 cudaError_t launch_moments(const KernelArgs<real>& a, cudaStream_t s) {
-  moments_kernel<real, S><<<node_grid(a.nx, a.ny), dim3(TX, TY), 0, s>>>(a);
+  const size_t smem = (sizeof(real) + sizeof(int)) * (size_t)a.nq * 25;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(moments_kernel<real, S>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  moments_kernel<real, S><<<node_grid(a.nx, a.ny), dim3(TX, TY), smem, s>>>(a);
   return cudaGetLastError();
 }
 template <typename real, typename S>
 cudaError_t launch_step(const KernelArgs<real>& a, cudaStream_t s) {
-  if (a.qe == TFKT_QE_STRESS)
-    step_stress_kernel<real, S><<<node_grid(a.nx, a.ny), dim3(TX, TY), 0, s>>>(a);
-  else
-    step_kernel<real, S><<<node_grid(a.nx, a.ny), dim3(TX, TY), 0, s>>>(a);
+  const size_t smem = (sizeof(real) + sizeof(int)) * (size_t)a.nq * 25;   // pull tables
+  if (a.qe == TFKT_QE_STRESS) {
+    if (smem > 40 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(step_stress_kernel<real, S>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    step_stress_kernel<real, S><<<node_grid(a.nx, a.ny), dim3(TX, TY), smem, s>>>(a);
+  } else {
+    if (smem > 40 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(step_kernel<real, S>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    step_kernel<real, S><<<node_grid(a.nx, a.ny), dim3(TX, TY), smem, s>>>(a);
+  }
   return cudaGetLastError();
 }
 template <typename real>
