@@ -702,14 +702,19 @@ __global__ void __launch_bounds__(DIAG_THREADS) diag_partial_kernel(KernelArgs<r
 }
 
 // base_s, base_p: the masses of the rest state, N (rho0 - psi_tot0) and N psi_tot0.
+// One warp per diagnostic: lanes stride over the block partials, then a fixed
+// shuffle tree (the order does not depend on scheduling).
 __global__ void diag_final_kernel(const double* partials, int nblocks, double inv_n, double base_s,
                                   double base_p, double* out) {
-  if (threadIdx.x < TFKT_NDIAG) {
-    double s = 0;
-    for (int b = 0; b < nblocks; ++b) s += partials[(size_t)b * TFKT_NDIAG + threadIdx.x];
-    if (threadIdx.x == TFKT_D_MASS_S) s += base_s;
-    if (threadIdx.x == TFKT_D_MASS_P) s += base_p;
-    out[threadIdx.x] = threadIdx.x == TFKT_D_QRMS_MEAN ? s * inv_n : s;
+  const int j = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (j >= TFKT_NDIAG) return;
+  double s = 0;
+  for (int b = lane; b < nblocks; b += 32) s += partials[(size_t)b * TFKT_NDIAG + j];
+  s = warp_sum(s);
+  if (lane == 0) {
+    if (j == TFKT_D_MASS_S) s += base_s;
+    if (j == TFKT_D_MASS_P) s += base_p;
+    out[j] = j == TFKT_D_QRMS_MEAN ? s * inv_n : s;
   }
 }
 
@@ -780,7 +785,7 @@ cudaError_t launch_diag(const KernelArgs<real>& a, double* partials, int nblocks
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const double N = (double)a.nx * a.ny;
-  diag_final_kernel<<<1, 32, 0, s>>>(partials, nblocks, 1.0 / N,
+  diag_final_kernel<<<1, 32 * TFKT_NDIAG, 0, s>>>(partials, nblocks, 1.0 / N,
                                      N * ((double)a.rho0 - (double)a.psi_tot0), N * (double)a.psi_tot0,
                                      out);
   return cudaGetLastError();
