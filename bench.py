@@ -311,10 +311,11 @@ def ensemble_throughput(n_runs: int, steps: int, warmup: int):
         e1.synchronize()
         ms = e0.elapsed_time(e1)
         diag = [b.run(i).diagnostics() for i in (0, n_runs - 1)]
-        ty, tune = b.tile_height()
+        plan = b.plan()
     assert all(math.isfinite(v) for d in diag for v in d.values())
     return {"runs": n_runs, "r_nodes": nodes, "steps": steps, "ms_per_step": ms / steps,
-            "tile": [32, ty], "tuned_ms_per_step": dict(zip(("4", "8", "16"), tune)),
+            "plan": "per-run kernels" if plan["per_run"] else f"batched kernel, tile 32x{plan['tile_height']}",
+            "tuned_ms_per_step": plan["ms"],
             "value": aggregate_glups(1, nodes, steps, ms / 1e3), "unit": "GLUPS",
             "workspace_gb": ws.numel() / 1e9, "nq": 9}
 

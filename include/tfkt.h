@@ -253,14 +253,16 @@ tfkt_status tfkt_destroy(tfkt_ctx* ctx);
 
 /* ---- Batched ensembles -------------------------------------------------
    Many independent Kolmogorov runs (their own grid size, Re, Wi, beta,
-   forcing and seed) advanced together: every step is one launch of the fused
-   kernel over the tiles of all runs plus one launch of its border fix-up,
-   replayed from a CUDA graph two steps at a time. The paper runs one case at
-   a time; batching is this library's addition. Requirements: every run uses
-   TFKT_FP32 and has nx a multiple of 32 and ny a multiple of 8 (the fused
-   path); otherwise TFKT_EINVAL. A run of the batch matches the same run
-   stepped alone up to float rounding (the batched kernel sums some moments in
-   another order), not bit for bit. */
+   forcing and seed) advanced together, replayed from a CUDA graph two steps at
+   a time, in one of two plans: one launch of the batched fused kernel over the
+   tiles of all runs plus one launch of its border fix-up per step; or each
+   run's own single-run kernels as parallel branches of the graph (largest runs
+   first, up to 32 branches). The paper runs one case at a time; batching is
+   this library's addition. Requirements: every run uses TFKT_FP32 and has nx a
+   multiple of 32 and ny a multiple of 8 (the fused path); otherwise
+   TFKT_EINVAL. Under the per-run plan a run of the batch is bit-identical to
+   the same run stepped alone; under the batched kernel it matches up to float
+   rounding (that kernel sums some moments in another order). */
 typedef struct tfkt_batch tfkt_batch;
 
 /* Device bytes for the batch (the runs' workspaces and the launch tables). */
@@ -270,10 +272,12 @@ tfkt_status tfkt_batch_required_bytes(const tfkt_params* runs, int32_t n, size_t
    NULL entries, or perturbs NULL). dev_workspace/bytes as in tfkt_create. The
    batch uses the caller's stream if it is not NULL, else one it creates (a CUDA
    graph cannot capture the legacy default stream). Before the runs are
-   initialised, the batch times a few steps of its launch at each tile height
-   (4, 8 and 16 rows of 32 nodes) that every run supports and keeps the fastest;
-   the environment variable TFKT_BATCH_TILE_HEIGHT (4, 8 or 16) fixes the height
-   instead (EINVAL if a run does not support it). */
+   initialised, the batch times four steps of each candidate plan (the batched
+   kernel at each tile height, 4, 8 or 16 rows of 32 nodes, that every run
+   supports, and the per-run plan), each as its captured graph, and keeps the
+   fastest. The environment variable TFKT_BATCH_PER_RUN=1 fixes the per-run
+   plan, and TFKT_BATCH_TILE_HEIGHT (4, 8 or 16) the batched kernel at that
+   height (EINVAL if a run does not support it), instead of the timing. */
 tfkt_status tfkt_batch_create(const tfkt_params* runs, int32_t n, const double* const* perturbs,
                               void* dev_workspace, size_t workspace_bytes, void* stream,
                               tfkt_batch** out);
@@ -286,9 +290,15 @@ tfkt_status tfkt_batch_step(tfkt_batch* b, int64_t n);
    call tfkt_step or tfkt_destroy on it. */
 tfkt_status tfkt_batch_run(tfkt_batch* b, int32_t i, tfkt_ctx** run);
 
-/* The batch's tile height, and (ms: float[3] or NULL) the timed milliseconds per
-   step at heights 4, 8 and 16 (NaN where not timed). */
+/* The batch's tile height (8 under the per-run plan, the single-run tile), and
+   (ms: float[3] or NULL) the timed milliseconds per step of the batched kernel
+   at heights 4, 8 and 16 (NaN where not timed). */
 tfkt_status tfkt_batch_tile_height(const tfkt_batch* b, int32_t* ty, float* ms);
+
+/* The chosen plan: *per_run 1 for each run's own kernels, 0 for the batched
+   kernel at tile height *ty; ms (float[4] or NULL): the timed milliseconds per
+   step at heights 4, 8, 16 and of the per-run plan (NaN where not timed). */
+tfkt_status tfkt_batch_plan(const tfkt_batch* b, int32_t* per_run, int32_t* ty, float* ms);
 
 tfkt_status tfkt_batch_destroy(tfkt_batch* b);
 

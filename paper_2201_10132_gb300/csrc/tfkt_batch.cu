@@ -1,9 +1,13 @@
-// Batched ensembles: independent runs sharing one launch of the fused kernel
-// (and one of its border fix-up) per step, replayed from a CUDA graph. The
-// tile height of that launch (4, 8 or 16 rows of 32 nodes) is chosen by
-// timing each candidate on the batch itself before the runs are initialised.
+// Batched ensembles: independent runs advanced together, two steps at a time
+// replayed from a CUDA graph, in one of two plans: one launch of the batched
+// fused kernel (and one of its border fix-up) over the tiles of all runs, at
+// a tile height of 4, 8 or 16 rows of 32 nodes; or every run's own single-run
+// kernels as parallel branches of the graph, largest runs first. The plan is
+// chosen by timing each candidate on the batch itself before the runs are
+// initialised.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <limits>
@@ -26,8 +30,13 @@ struct tfkt_batch {
   cudaGraphExec_t graph = nullptr;         // two steps: parity 0 then 1
   int64_t step = 0;
   int ty = tfkt::TY;                       // tile height of the launch
-  float tune_ms[3] = {NAN, NAN, NAN};      // timed ms per step for heights 4, 8, 16
+  float tune_ms[4] = {NAN, NAN, NAN, NAN}; // timed ms per step: heights 4, 8, 16, per-run plan
   std::vector<tfkt::BatchRun<float>> host; // launch tables of the chosen height
+  bool per_run = false;                    // the per-run plan
+  std::vector<cudaStream_t> pool;          // its graph branches
+  std::vector<cudaEvent_t> join;           // one per branch
+  cudaEvent_t fork = nullptr;
+  std::vector<int> order;                  // runs, largest first
 };
 
 namespace tfkt {
@@ -73,13 +82,54 @@ void release(tfkt_batch* b) {
     if (c) tfkt_destroy(c);
   if (b->graph) cudaGraphExecDestroy(b->graph);
   if (b->owned && b->ws) cudaFree(b->ws);
+  for (cudaStream_t p : b->pool) cudaStreamDestroy(p);
+  for (cudaEvent_t e : b->join) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
 }
 
+// The per-run plan: fork from s onto the branch streams, each run's fused step
+// and fix-up on branch (position in `order`) mod branches, join back into s.
+// Inside a stream capture this records parallel graph branches.
+cudaError_t launch_per_run(tfkt_batch* b, int parity, cudaStream_t s) {
+  cudaError_t e = cudaEventRecord(b->fork, s);
+  for (size_t k = 0; k < b->pool.size() && e == cudaSuccess; ++k)
+    e = cudaStreamWaitEvent(b->pool[k], b->fork, 0);
+  for (size_t j = 0; j < b->order.size() && e == cudaSuccess; ++j) {
+    const int i = b->order[j];
+    e = launch_single_fp32(b->host[i].a[parity], b->host[i].f[parity], b->pool[j % b->pool.size()]);
+  }
+  for (size_t k = 0; k < b->pool.size() && e == cudaSuccess; ++k) {
+    e = cudaEventRecord(b->join[k], b->pool[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->join[k], 0);
+  }
+  return e;
+}
+
+// One step of the chosen plan at buffer parity `parity` on stream s.
+cudaError_t launch_plan(tfkt_batch* b, int parity, cudaStream_t s) {
+  if (b->per_run) return launch_per_run(b, parity, s);
+  return launch_batch_step(b->d_runs, b->d_tile_start, (int)b->runs.size(), b->total_tiles,
+                           b->max_nq, parity, s, b->ty);
+}
+
+// Two steps (parity 0 then 1) of the chosen plan as an instantiated graph.
+cudaError_t capture(tfkt_batch* b, cudaGraphExec_t* out) {
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaError_t e1 = launch_plan(b, 0, b->stream);
+  if (e1 == cudaSuccess) e1 = launch_plan(b, 1, b->stream);
+  e = cudaStreamEndCapture(b->stream, &g);
+  if (e == cudaSuccess) e = e1;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+  if (g) cudaGraphDestroy(g);
+  return e;
+}
+
 tfkt_status plain_step(tfkt_batch* b) {
-  cudaError_t e = launch_batch_step(b->d_runs, b->d_tile_start, (int)b->runs.size(),
-                                    b->total_tiles, b->max_nq, b->parity, b->stream, b->ty);
+  cudaError_t e = launch_plan(b, b->parity, b->stream);
   if (e != cudaSuccess) return fail(TFKT_ECUDA, std::string("batch step: ") + cudaGetErrorString(e));
   b->parity ^= 1;
   return TFKT_OK;
@@ -117,46 +167,58 @@ std::vector<int> candidates(const std::vector<Lattice>& L) {
   return out;
 }
 
-// Time `steps` batch steps at each candidate height on the current states (the
-// runs are initialised afterwards, so the states timed here are thrown away);
-// keep the fastest. TFKT_BATCH_TILE_HEIGHT (4, 8 or 16) skips the timing.
+// Time each candidate plan on the current states (the runs are initialised
+// afterwards, so the states timed here are thrown away): the batched kernel at
+// every tile height all runs admit, and the per-run plan; each as its captured
+// two-step graph, launched once to warm up and then twice (four steps) between
+// events. Keep the fastest. TFKT_BATCH_PER_RUN=1 fixes the per-run plan and
+// TFKT_BATCH_TILE_HEIGHT (4, 8 or 16) the batched kernel at that height instead.
 tfkt_status autotune(tfkt_batch* b, const std::vector<Lattice>& L) {
   const std::vector<int> cand = candidates(L);
+  const char* env_runs = std::getenv("TFKT_BATCH_PER_RUN");
   const char* env = std::getenv("TFKT_BATCH_TILE_HEIGHT");
+  const bool force_runs = env_runs && std::atoi(env_runs) == 1;
   const int forced = env ? std::atoi(env) : 0;
-  if (forced) {
+  auto use = [&](int ty) -> cudaError_t {   // ty 0: the per-run plan
+    b->per_run = ty == 0;
+    return set_tables(b, L, ty == 0 ? TY : ty);
+  };
+  if (force_runs || forced) {
+    int pick = -1;
+    if (force_runs) pick = 0;
     for (int ty : cand)
-      if (ty == forced) {
-        cudaError_t e = set_tables(b, L, ty);
-        if (e != cudaSuccess) return fail(TFKT_ECUDA, std::string("batch tables: ") + cudaGetErrorString(e));
-        return TFKT_OK;
-      }
-    return fail(TFKT_EINVAL, "TFKT_BATCH_TILE_HEIGHT names a height these runs do not support");
+      if (!force_runs && ty == forced) pick = ty;
+    if (pick < 0) return fail(TFKT_EINVAL, "TFKT_BATCH_TILE_HEIGHT names a height these runs do not support");
+    cudaError_t e = use(pick);
+    if (e != cudaSuccess) return fail(TFKT_ECUDA, std::string("batch tables: ") + cudaGetErrorString(e));
+    return TFKT_OK;
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
     return fail(TFKT_ECUDA, "cudaEventCreate");
+  }
+  std::vector<int> plans(cand);
+  plans.push_back(0);
   int best = -1;
   float best_ms = std::numeric_limits<float>::infinity();
   cudaError_t e = cudaSuccess;
-  for (int ty : cand) {
-    e = set_tables(b, L, ty);
+  for (int ty : plans) {
+    e = use(ty);
     if (e != cudaSuccess) break;
-    const int warm = 1, steps = 4;
-    for (int k = 0; k < warm + steps && e == cudaSuccess; ++k) {
-      if (k == warm) e = cudaEventRecord(e0, b->stream);
-      if (e == cudaSuccess)
-        e = launch_batch_step(b->d_runs, b->d_tile_start, (int)b->runs.size(), b->total_tiles,
-                              b->max_nq, b->parity, b->stream, ty);
-      b->parity ^= 1;
-    }
+    cudaGraphExec_t g = nullptr;
+    e = capture(b, &g);
+    if (e == cudaSuccess) e = cudaGraphLaunch(g, b->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaGraphLaunch(g, b->stream);
     if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     float ms = 0;
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (g) cudaGraphExecDestroy(g);
     if (e != cudaSuccess) break;
-    ms /= steps;
-    b->tune_ms[ty == 4 ? 0 : (ty == 8 ? 1 : 2)] = ms;
+    ms /= 4;
+    b->tune_ms[ty == 0 ? 3 : (ty == 4 ? 0 : (ty == 8 ? 1 : 2))] = ms;
     if (ms < best_ms) {
       best_ms = ms;
       best = ty;
@@ -164,7 +226,7 @@ tfkt_status autotune(tfkt_batch* b, const std::vector<Lattice>& L) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (e == cudaSuccess && best > 0) e = set_tables(b, L, best);
+  if (e == cudaSuccess && best >= 0) e = use(best);
   if (e != cudaSuccess) return fail(TFKT_ECUDA, std::string("batch tuning: ") + cudaGetErrorString(e));
   b->parity = 0;
   return TFKT_OK;
@@ -249,6 +311,26 @@ tfkt_status tfkt_batch_create(const tfkt_params* runs, int32_t n, const double* 
   }
   b->d_runs = (BatchRun<float>*)((char*)b->ws + off_tab);
   b->d_tile_start = (int*)((char*)b->ws + align256(off_tab + n * sizeof(BatchRun<float>)));
+  // the per-run plan's branches (up to 32) and its order, largest runs first
+  for (int32_t i = 0; i < n; ++i) b->order.push_back(i);
+  std::stable_sort(b->order.begin(), b->order.end(), [&](int u, int v) {
+    return (size_t)L[u].nx * L[u].ny > (size_t)L[v].nx * L[v].ny;
+  });
+  const int nbranch = n < 32 ? n : 32;
+  cudaError_t ce = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  for (int k = 0; k < nbranch && ce == cudaSuccess; ++k) {
+    cudaStream_t ps = nullptr;
+    cudaEvent_t je = nullptr;
+    ce = cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) b->pool.push_back(ps);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&je, cudaEventDisableTiming);
+    if (ce == cudaSuccess) b->join.push_back(je);
+  }
+  if (ce == cudaSuccess) ce = prepare_single_fp32(b->max_nq);
+  if (ce != cudaSuccess) {
+    release(b);
+    return fail(TFKT_ECUDA, std::string("batch streams: ") + cudaGetErrorString(ce));
+  }
   if ((s = autotune(b, L)) != TFKT_OK) {
     release(b);
     return s;
@@ -273,20 +355,8 @@ tfkt_status tfkt_batch_step(tfkt_batch* b, int64_t n) {
     s = plain_step(b);
     --left;
   }
-  if (left >= 2 && !b->graph) {
-    // capture two steps (parity 0 then 1) once
-    cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-      cudaError_t e1 = launch_batch_step(b->d_runs, b->d_tile_start, (int)b->runs.size(),
-                                         b->total_tiles, b->max_nq, 0, b->stream, b->ty);
-      cudaError_t e2 = launch_batch_step(b->d_runs, b->d_tile_start, (int)b->runs.size(),
-                                         b->total_tiles, b->max_nq, 1, b->stream, b->ty);
-      e = cudaStreamEndCapture(b->stream, &g);
-      if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : e2;
-    }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
-    if (g) cudaGraphDestroy(g);
+  if (left >= 2 && !b->graph) {   // capture two steps (parity 0 then 1) once
+    cudaError_t e = capture(b, &b->graph);
     if (e != cudaSuccess) return fail(TFKT_ECUDA, std::string("graph: ") + cudaGetErrorString(e));
   }
   while (s == TFKT_OK && left >= 2) {
@@ -318,6 +388,15 @@ tfkt_status tfkt_batch_tile_height(const tfkt_batch* b, int32_t* ty, float* ms) 
   *ty = b->ty;
   if (ms)
     for (int k = 0; k < 3; ++k) ms[k] = b->tune_ms[k];
+  return TFKT_OK;
+}
+
+tfkt_status tfkt_batch_plan(const tfkt_batch* b, int32_t* per_run, int32_t* ty, float* ms) {
+  if (!b || !per_run || !ty) return fail(TFKT_EINVAL, "NULL argument");
+  *per_run = b->per_run ? 1 : 0;
+  *ty = b->ty;
+  if (ms)
+    for (int k = 0; k < 4; ++k) ms[k] = b->tune_ms[k];
   return TFKT_OK;
 }
 

@@ -867,6 +867,30 @@ cudaError_t launch_fixup(const KernelArgs<real>& a, const FusedArgs<real>& f, cu
   return cudaGetLastError();
 }
 
+// Batches that launch each run's own single-run kernels (graph branches): the
+// attribute is set once here, so the launches below make no other API call.
+cudaError_t prepare_single_fp32(int max_nq) {
+  const size_t smem = fused_smem_bytes(max_nq, sizeof(float), TY);
+  cudaError_t e = cudaFuncSetAttribute(step_fused_kernel<float, float, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t fsmem = fix_smem_bytes<float, TY>(max_nq);
+  if (e == cudaSuccess && fsmem > 48 * 1024)
+    e = cudaFuncSetAttribute(fixup_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)fsmem);
+  return e;
+}
+
+cudaError_t launch_single_fp32(const KernelArgs<float>& a, const FusedArgs<float>& f,
+                               cudaStream_t s) {
+  const dim3 grid(a.nx / TX, a.ny / TY), block(TX, TY);
+  step_fused_kernel<float, float, false><<<grid, block, fused_smem_bytes(a.nq, sizeof(float), TY), s>>>(
+      a, f);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  fixup_kernel<float><<<grid, FIX_T, fix_smem_bytes<float, TY>(a.nq), s>>>(a, f);
+  return cudaGetLastError();
+}
+
 template <int H>
 cudaError_t prepare_batch_h(int max_nq) {
   const size_t smem = fused_smem_bytes(max_nq, sizeof(float), H);

@@ -231,6 +231,11 @@ cudaError_t launch_step_fused(const KernelArgs<real>& a, const FusedArgs<real>& 
 template <typename real>
 cudaError_t launch_fixup(const KernelArgs<real>& a, const FusedArgs<real>& f, cudaStream_t s);
 
+// Each run's single-run FP32 kernels (fused step + fix-up) without API calls
+// besides the launches, after prepare_single_fp32 for the largest nq.
+cudaError_t prepare_single_fp32(int max_nq);
+cudaError_t launch_single_fp32(const KernelArgs<float>& a, const FusedArgs<float>& f,
+                               cudaStream_t s);
 // Batched fused step (FP32): all tiles of all runs in one launch of each kernel.
 cudaError_t prepare_batch(int max_nq, int ty);
 cudaError_t launch_batch_step(const BatchRun<float>* runs, const int* tile_start, int nruns,

@@ -136,6 +136,9 @@ def lib() -> ctypes.CDLL:
         L.tfkt_batch_tile_height.argtypes = [P, ctypes.POINTER(ctypes.c_int32),
                                              ctypes.POINTER(ctypes.c_float)]
         L.tfkt_batch_tile_height.restype = S
+        L.tfkt_batch_plan.argtypes = [P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_float)]
+        L.tfkt_batch_plan.restype = S
         for n in ("tfkt_batch_required_bytes", "tfkt_batch_create", "tfkt_batch_step",
                   "tfkt_batch_run", "tfkt_batch_destroy"):
             getattr(L, n).restype = S
@@ -370,6 +373,14 @@ class Batch:
         ms = (ctypes.c_float * 3)()
         _check(lib().tfkt_batch_tile_height(self._h, ctypes.byref(ty), ms), "tfkt_batch_tile_height")
         return int(ty.value), [float(v) for v in ms]
+
+    def plan(self):
+        """{"per_run": bool, "tile_height": int, "ms": {"4", "8", "16", "per_run": timed ms per step}}."""
+        pr, ty = ctypes.c_int32(), ctypes.c_int32()
+        ms = (ctypes.c_float * 4)()
+        _check(lib().tfkt_batch_plan(self._h, ctypes.byref(pr), ctypes.byref(ty), ms), "tfkt_batch_plan")
+        return {"per_run": bool(pr.value), "tile_height": int(ty.value),
+                "ms": dict(zip(("4", "8", "16", "per_run"), [float(v) for v in ms]))}
 
     def run(self, i: int) -> Solver:
         r = ctypes.c_void_p()
