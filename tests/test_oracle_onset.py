@@ -22,27 +22,7 @@ import numpy as np
 import pytest
 
 
-def _sigma(alpha, re, n_modes=40):
-    n = np.arange(-n_modes, n_modes + 1)
-    k2 = alpha ** 2 + n ** 2
-    m = len(n)
-    A = np.zeros((m, m))
-    A[np.arange(m), np.arange(m)] = -(k2 ** 2) / re
-    A[np.arange(1, m), np.arange(m - 1)] = -(alpha / 2) * (k2[:-1] - 1)
-    A[np.arange(m - 1), np.arange(1, m)] = (alpha / 2) * (k2[1:] - 1)
-    ev = np.linalg.eigvals(A / k2[:, None])
-    return ev[np.argmax(ev.real)]
-
-
-def _onset(alpha):
-    lo, hi = 1.0, 4.0
-    for _ in range(50):
-        mid = 0.5 * (lo + hi)
-        if _sigma(alpha, mid).real > 0:
-            hi = mid
-        else:
-            lo = mid
-    return hi
+from linear_kolmogorov import onset as _onset, sigma as _sigma
 
 
 def test_eigen_solver_textbook_limits():
