@@ -1,8 +1,9 @@
 // The learned macro-step's network: forward pass, loss and gradient by
 // backpropagation, and Adam, as hand-written kernels (bfloat16 matrices, FP32
-// accumulation; inference on the tensor cores, training on the CUDA cores in
-// FP32). Gradients are summed per block of 128 samples and the block partials
-// in a fixed order, so results are reproducible.
+// accumulation, on the tensor cores for the forward pass and for the weight
+// gradients and propagated errors of the backward pass). Gradients are summed
+// per block of 128 samples and the block partials in a fixed order, so results
+// are reproducible.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -17,8 +18,6 @@ namespace tfkt {
 namespace {
 
 constexpr int TB = 128;          // samples (threads) per training block
-constexpr int XS = NIN + 1;      // padded row strides of the per-sample tables
-constexpr int HS = NH + 1;
 
 __device__ __forceinline__ float gelu_grad(float z) {
   return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) +
@@ -55,13 +54,154 @@ __global__ void __launch_bounds__(128) forward_kernel(const float* __restrict__ 
   }
 }
 
-struct TrainShared {
-  MlpShared net;
-  float xs[TB * XS];
-  float z1[TB * HS], h1[TB * HS], z2[TB * HS], h2[TB * HS];
-  float dO[TB * NOUT];
+// ---- training: forward and backward on the tensor cores
+// Per block TB = 128 samples (4 warps of 32). The forward pass is the inference
+// routine's (standardised inputs and GELU activations as bfloat16 high part plus
+// remainder, bfloat16 weights, FP32 accumulation), keeping pre-activations and
+// activations per sample. Backward: the output layer, the bias sums and the
+// GELU derivatives on the CUDA cores; the weight gradients dW2 = dz2^T h1 and
+// dW1 = dz1^T x (sums over the block's samples) and the propagated error
+// dz2 W2 as mma.sync, both FP32 operands split into high part and remainder
+// (three products per pair: high x high, high x remainder, remainder x high).
+constexpr int TR_LD = 68;   // FP32 row stride of the per-sample tables (float2-aligned)
+
+struct TrainTc {
+  MlpTc net;                         // forward weights ([out][in] bfloat16) and normalisation
+  __nv_bfloat16 w2t[NH * TC_W2LD];   // W2 transposed ([in][out]) for the propagated error
+  float xs[TB * TC_XLD];             // standardised inputs; columns NIN .. TC_K1 - 1 zero
+  float z1[TB * TR_LD], h1[TB * TR_LD], z2[TB * TR_LD], h2[TB * TR_LD];
+  float o[TB * 4], dO[TB * 4];
   double lsum[TB];
 };
+
+// Fragment pair (p, q) of an FP32 table split into bfloat16 high part and remainder.
+__device__ __forceinline__ void tr_split2(const float* p, const float* q, uint32_t& hi, uint32_t& lo) {
+  tc_split(*p, *q, hi, lo);
+}
+
+// Forward pass of the warp's 32 samples (rows wb .. wb + 31 of the tables).
+__device__ __forceinline__ void train_forward_warp(TrainTc& sh, int wb, int lane) {
+  const MlpTc& s = sh.net;
+  const int g = lane >> 2, t = lane & 3;
+#pragma unroll 1
+  for (int m = 0; m < 2; ++m) {
+    const int r0 = wb + 16 * m + g, r1 = r0 + 8;
+    const float* x0 = sh.xs + r0 * TC_XLD;
+    const float* x1 = sh.xs + r1 * TC_XLD;
+    uint32_t ah1[3][4], al1[3][4];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int c0 = 16 * k + 2 * t;
+      tc_split(x0[c0], x0[c0 + 1], ah1[k][0], al1[k][0]);
+      tc_split(x1[c0], x1[c0 + 1], ah1[k][1], al1[k][1]);
+      tc_split(x0[c0 + 8], x0[c0 + 9], ah1[k][2], al1[k][2]);
+      tc_split(x1[c0 + 8], x1[c0 + 9], ah1[k][3], al1[k][3]);
+    }
+    float c[8][4];
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+      c[n][0] = c[n][2] = s.b1[8 * n + 2 * t];
+      c[n][1] = c[n][3] = s.b1[8 * n + 2 * t + 1];
+    }
+    tc_layer<3, 8, TC_W1LD>(c, ah1, al1, s.w1, g, t);
+    uint32_t ah[4][4], al[4][4];
+    // keep z1, h1; the next layer's operands from h1
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+      const int col = 8 * n + 2 * t;
+      float a[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) a[e] = gelu(c[n][e]);
+      sh.z1[r0 * TR_LD + col] = c[n][0];
+      sh.z1[r0 * TR_LD + col + 1] = c[n][1];
+      sh.z1[r1 * TR_LD + col] = c[n][2];
+      sh.z1[r1 * TR_LD + col + 1] = c[n][3];
+      sh.h1[r0 * TR_LD + col] = a[0];
+      sh.h1[r0 * TR_LD + col + 1] = a[1];
+      sh.h1[r1 * TR_LD + col] = a[2];
+      sh.h1[r1 * TR_LD + col + 1] = a[3];
+      const int k = n >> 1, half = (n & 1) * 2;
+      tc_split(a[0], a[1], ah[k][half], al[k][half]);
+      tc_split(a[2], a[3], ah[k][half + 1], al[k][half + 1]);
+    }
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+      c[n][0] = c[n][2] = s.b2[8 * n + 2 * t];
+      c[n][1] = c[n][3] = s.b2[8 * n + 2 * t + 1];
+    }
+    tc_layer<4, 8, TC_W2LD>(c, ah, al, s.w2, g, t);
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+      const int col = 8 * n + 2 * t;
+      float a[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) a[e] = gelu(c[n][e]);
+      sh.z2[r0 * TR_LD + col] = c[n][0];
+      sh.z2[r0 * TR_LD + col + 1] = c[n][1];
+      sh.z2[r1 * TR_LD + col] = c[n][2];
+      sh.z2[r1 * TR_LD + col + 1] = c[n][3];
+      sh.h2[r0 * TR_LD + col] = a[0];
+      sh.h2[r0 * TR_LD + col + 1] = a[1];
+      sh.h2[r1 * TR_LD + col] = a[2];
+      sh.h2[r1 * TR_LD + col + 1] = a[3];
+      const int k = n >> 1, half = (n & 1) * 2;
+      tc_split(a[0], a[1], ah[k][half], al[k][half]);
+      tc_split(a[2], a[3], ah[k][half + 1], al[k][half + 1]);
+    }
+    float c3[1][4] = {{s.b3[2 * t], s.b3[2 * t + 1], s.b3[2 * t], s.b3[2 * t + 1]}};
+    tc_layer<4, 1, TC_W2LD>(c3, ah, al, s.w3, g, t);
+    if (2 * t < NOUT) {
+      sh.o[r0 * 4 + 2 * t] = c3[0][0];
+      sh.o[r1 * 4 + 2 * t] = c3[0][2];
+    }
+    if (2 * t + 1 < NOUT) {
+      sh.o[r0 * 4 + 2 * t + 1] = c3[0][1];
+      sh.o[r1 * 4 + 2 * t + 1] = c3[0][3];
+    }
+  }
+}
+
+// G[o][i] = sum over the block's TB samples s of D[s][o] B[s][i] for o in this
+// warp's 16 rows (o0 ..) and i < ni (NN n-tiles of 8), written to P[o * ld + i].
+template <int NN>
+__device__ __forceinline__ void train_weight_grad(const float* D, const float* B, int bld, int o0,
+                                                  int ni, float* P, int ld, int lane) {
+  const int g = lane >> 2, t = lane & 3;
+  float c[NN][4];
+#pragma unroll
+  for (int n = 0; n < NN; ++n) c[n][0] = c[n][1] = c[n][2] = c[n][3] = 0.f;
+#pragma unroll 1
+  for (int k = 0; k < TB / 16; ++k) {
+    const int s0 = 16 * k + 2 * t;
+    uint32_t ah[4], al[4];
+    tr_split2(D + s0 * TR_LD + o0 + g, D + (s0 + 1) * TR_LD + o0 + g, ah[0], al[0]);
+    tr_split2(D + s0 * TR_LD + o0 + g + 8, D + (s0 + 1) * TR_LD + o0 + g + 8, ah[1], al[1]);
+    tr_split2(D + (s0 + 8) * TR_LD + o0 + g, D + (s0 + 9) * TR_LD + o0 + g, ah[2], al[2]);
+    tr_split2(D + (s0 + 8) * TR_LD + o0 + g + 8, D + (s0 + 9) * TR_LD + o0 + g + 8, ah[3], al[3]);
+#pragma unroll
+    for (int n = 0; n < NN; ++n) {
+      const int i = 8 * n + g;
+      uint32_t bh0, bl0, bh1, bl1;
+      tr_split2(B + s0 * bld + i, B + (s0 + 1) * bld + i, bh0, bl0);
+      tr_split2(B + (s0 + 8) * bld + i, B + (s0 + 9) * bld + i, bh1, bl1);
+      tc_mma(c[n], ah, bh0, bh1);
+      tc_mma(c[n], ah, bl0, bl1);
+      tc_mma(c[n], al, bh0, bh1);
+    }
+  }
+#pragma unroll
+  for (int n = 0; n < NN; ++n) {
+    const int i = 8 * n + 2 * t;
+    if (i < ni) {
+      P[(o0 + g) * ld + i] = c[n][0];
+      P[(o0 + g + 8) * ld + i] = c[n][2];
+    }
+    if (i + 1 < ni) {
+      P[(o0 + g) * ld + i + 1] = c[n][1];
+      P[(o0 + g + 8) * ld + i + 1] = c[n][3];
+    }
+  }
+}
 
 // Loss and gradient partials of one block of TB samples; partial[b][NWEIGHTS].
 __global__ void __launch_bounds__(TB) loss_grad_kernel(const float* __restrict__ master,
@@ -71,103 +211,109 @@ __global__ void __launch_bounds__(TB) loss_grad_kernel(const float* __restrict__
                                                        float* __restrict__ partial,
                                                        double* __restrict__ lpart) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  TrainShared& sh = *reinterpret_cast<TrainShared*>(smem_raw);
-  const int tid = threadIdx.x;
-  mlp_stage(sh.net, master, wmat, tid, TB);
+  TrainTc& sh = *reinterpret_cast<TrainTc*>(smem_raw);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  mlp_stage_tc(sh.net, master, wmat, tid, TB);
+  for (int k = tid; k < NH * TC_W2LD; k += TB) {
+    const int i = k / TC_W2LD, o = k % TC_W2LD;
+    sh.w2t[k] = o < NH ? wmat[NH * NIN + o * NH + i] : __float2bfloat16(0.0f);
+  }
   __syncthreads();
-  const MlpShared& s = sh.net;
+  const MlpTc& s = sh.net;
   const int64_t k = (int64_t)blockIdx.x * TB + tid;
   const bool valid = k < n;
   const float inv_n = 1.0f / (float)n;
-  float* xs = sh.xs + tid * XS;
-  float* z1 = sh.z1 + tid * HS;
-  float* h1 = sh.h1 + tid * HS;
-  float* z2 = sh.z2 + tid * HS;
-  float* h2 = sh.h2 + tid * HS;
-  double lsq = 0.0;
   // ---- forward, keeping what the backward pass needs
-  if (valid) {
-    for (int i = 0; i < NIN; ++i) xs[i] = (X[k * NIN + i] - s.mx[i]) * s.rsx[i];
-    for (int o = 0; o < NH; ++o) {
-      float acc = s.b1[o];
-      for (int i = 0; i < NIN; ++i) acc = fmaf(s.w1[o * NIN + i], xs[i], acc);
-      z1[o] = acc;
-      h1[o] = gelu(acc);
-    }
-    for (int o = 0; o < NH; ++o) {
-      float acc = s.b2[o];
-      for (int i = 0; i < NH; ++i) acc = fmaf(s.w2[o * NH + i], h1[i], acc);
-      z2[o] = acc;
-      h2[o] = gelu(acc);
-    }
-    for (int j = 0; j < NOUT; ++j) {
-      float acc = s.b3[j];
-      for (int i = 0; i < NH; ++i) acc = fmaf(s.w3[j * NH + i], h2[i], acc);
-      const float t = (T[k * NOUT + j] - s.mt[j]) / s.st[j];
-      const float r = acc - t;
+  float* xs = sh.xs + tid * TC_XLD;
+#pragma unroll
+  for (int i = 0; i < NIN; ++i) xs[i] = valid ? (X[k * NIN + i] - s.mx[i]) * s.rsx[i] : 0.0f;
+#pragma unroll
+  for (int i = NIN; i < TC_XLD; ++i) xs[i] = 0.0f;
+  __syncwarp();
+  train_forward_warp(sh, warp * 32, lane);
+  __syncwarp();
+  double lsq = 0.0;
+  for (int j = 0; j < NOUT; ++j) {
+    float d = 0.0f;
+    if (valid) {
+      const float tj = (T[k * NOUT + j] - s.mt[j]) / s.st[j];
+      const float r = sh.o[tid * 4 + j] - tj;
       lsq += (double)r * (double)r;
-      sh.dO[tid * NOUT + j] = 2.0f * r * inv_n;
+      d = 2.0f * r * inv_n;
     }
-  } else {
-    for (int i = 0; i < NIN; ++i) xs[i] = 0.0f;
-    for (int o = 0; o < NH; ++o) z1[o] = h1[o] = z2[o] = h2[o] = 0.0f;
-    for (int j = 0; j < NOUT; ++j) sh.dO[tid * NOUT + j] = 0.0f;
+    sh.dO[tid * 4 + j] = d;
   }
   sh.lsum[tid] = lsq;
   __syncthreads();
   float* P = partial + (size_t)blockIdx.x * TFKT_MLP_NWEIGHTS;
-  // ---- output layer: dW3 = sum_s dO h2^T, db3 = sum_s dO
+  // ---- output layer: dW3 = sum_s dO h2^T, db3 = sum_s dO (invalid samples carry dO = 0)
   for (int e = tid; e < NOUT * NH + NOUT; e += TB) {
     float acc = 0.0f;
     if (e < NOUT * NH) {
       const int j = e / NH, i = e % NH;
-      for (int r = 0; r < TB; ++r) acc = fmaf(sh.dO[r * NOUT + j], sh.h2[r * HS + i], acc);
+      for (int r = 0; r < TB; ++r) acc = fmaf(sh.dO[r * 4 + j], sh.h2[r * TR_LD + i], acc);
       P[OW3 + e] = acc;
     } else {
       const int j = e - NOUT * NH;
-      for (int r = 0; r < TB; ++r) acc += sh.dO[r * NOUT + j];
+      for (int r = 0; r < TB; ++r) acc += sh.dO[r * 4 + j];
       P[OB3 + j] = acc;
     }
   }
-  // ---- dz2 = (W3^T dO) * GELU'(z2), in place of z2 (own row)
+  // ---- dz2 = (W3^T dO) GELU'(z2) for this thread's sample, in place of z2
   for (int o = 0; o < NH; ++o) {
     float acc = 0.0f;
-    for (int j = 0; j < NOUT; ++j) acc = fmaf(s.w3[j * NH + o], sh.dO[tid * NOUT + j], acc);
-    z2[o] = acc * gelu_grad(z2[o]);
+    for (int j = 0; j < NOUT; ++j)
+      acc = fmaf(__bfloat162float(s.w3[j * TC_W2LD + o]), sh.dO[tid * 4 + j], acc);
+    sh.z2[tid * TR_LD + o] = acc * gelu_grad(sh.z2[tid * TR_LD + o]);
   }
   __syncthreads();
-  // ---- layer 2: dW2 = sum_s dz2 h1^T, db2 = sum_s dz2
-  for (int e = tid; e < NH * NH + NH; e += TB) {
+  // ---- layer 2: dW2 = dz2^T h1 (warp: 16 output rows), db2 = sum_s dz2
+  train_weight_grad<8>(sh.z2, sh.h1, TR_LD, 16 * warp, NH, P + OW2, NH, lane);
+  if (tid < NH) {
     float acc = 0.0f;
-    if (e < NH * NH) {
-      const int o = e / NH, i = e % NH;
-      for (int r = 0; r < TB; ++r) acc = fmaf(sh.z2[r * HS + o], sh.h1[r * HS + i], acc);
-      P[OW2 + e] = acc;
-    } else {
-      const int o = e - NH * NH;
-      for (int r = 0; r < TB; ++r) acc += sh.z2[r * HS + o];
-      P[OB2 + o] = acc;
-    }
+    for (int r = 0; r < TB; ++r) acc += sh.z2[r * TR_LD + tid];
+    P[OB2 + tid] = acc;
   }
-  // ---- dz1 = (W2^T dz2) * GELU'(z1), in place of z1 (own row)
-  for (int i = 0; i < NH; ++i) {
-    float acc = 0.0f;
-    for (int o = 0; o < NH; ++o) acc = fmaf(s.w2[o * NH + i], z2[o], acc);
-    z1[i] = acc * gelu_grad(z1[i]);
+  // ---- dz1 = (dz2 W2) GELU'(z1) for the warp's 32 samples, in place of z1
+  {
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll 1
+    for (int m = 0; m < 2; ++m) {
+      const int r0 = warp * 32 + 16 * m + g, r1 = r0 + 8;
+      uint32_t ah[4][4], al[4][4];
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const int c0 = 16 * kk + 2 * t;
+        const float* d0 = sh.z2 + r0 * TR_LD;
+        const float* d1 = sh.z2 + r1 * TR_LD;
+        tc_split(d0[c0], d0[c0 + 1], ah[kk][0], al[kk][0]);
+        tc_split(d1[c0], d1[c0 + 1], ah[kk][1], al[kk][1]);
+        tc_split(d0[c0 + 8], d0[c0 + 9], ah[kk][2], al[kk][2]);
+        tc_split(d1[c0 + 8], d1[c0 + 9], ah[kk][3], al[kk][3]);
+      }
+      float c[8][4];
+#pragma unroll
+      for (int nn = 0; nn < 8; ++nn) c[nn][0] = c[nn][1] = c[nn][2] = c[nn][3] = 0.f;
+      tc_layer<4, 8, TC_W2LD>(c, ah, al, sh.w2t, g, t);
+#pragma unroll
+      for (int nn = 0; nn < 8; ++nn) {
+        const int col = 8 * nn + 2 * t;
+        float* z0 = sh.z1 + r0 * TR_LD + col;
+        float* z1r = sh.z1 + r1 * TR_LD + col;
+        z0[0] = c[nn][0] * gelu_grad(z0[0]);
+        z0[1] = c[nn][1] * gelu_grad(z0[1]);
+        z1r[0] = c[nn][2] * gelu_grad(z1r[0]);
+        z1r[1] = c[nn][3] * gelu_grad(z1r[1]);
+      }
+    }
   }
   __syncthreads();
-  // ---- layer 1: dW1 = sum_s dz1 x^T, db1 = sum_s dz1
-  for (int e = tid; e < NH * NIN + NH; e += TB) {
+  // ---- layer 1: dW1 = dz1^T x (warp: 16 output rows, inputs padded to 48), db1 = sum_s dz1
+  train_weight_grad<6>(sh.z1, sh.xs, TC_XLD, 16 * warp, NIN, P + OW1, NIN, lane);
+  if (tid < NH) {
     float acc = 0.0f;
-    if (e < NH * NIN) {
-      const int o = e / NIN, i = e % NIN;
-      for (int r = 0; r < TB; ++r) acc = fmaf(sh.z1[r * HS + o], sh.xs[r * XS + i], acc);
-      P[OW1 + e] = acc;
-    } else {
-      const int o = e - NH * NIN;
-      for (int r = 0; r < TB; ++r) acc += sh.z1[r * HS + o];
-      P[OB1 + o] = acc;
-    }
+    for (int r = 0; r < TB; ++r) acc += sh.z1[r * TR_LD + tid];
+    P[OB1 + tid] = acc;
   }
   if (tid == 0) {
     double l = 0.0;
@@ -342,7 +488,7 @@ tfkt_status tfkt_mlp_loss_grad(tfkt_mlp* net, const float* X, const float* T, in
   if (nb > (1 << 20)) return fail(TFKT_EINVAL, "batch too large (at most 2^27 samples)");
   tfkt_status s = ensure_blocks(net, (int)nb);
   if (s != TFKT_OK) return s;
-  const size_t smem = sizeof(TrainShared);
+  const size_t smem = sizeof(TrainTc);
   MLP_CUDA(cudaFuncSetAttribute(loss_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem));
   loss_grad_kernel<<<(unsigned)nb, TB, smem, net->stream>>>(net->d.master, net->d.wmat, X, T, n,
