@@ -68,7 +68,9 @@ tfkt_status tfkt_mlp_forward(tfkt_mlp* net, const float* X, int64_t n, float* Y)
 
 /* Loss L = (1/n) sum_n sum_j (o_nj - (t_nj - mt_j)/st_j)^2 of n >= 1 samples, o the
    standardised outputs, and its gradient with respect to the trainable
-   parameters (evaluated with the bfloat16 matrices). loss: host double (may be
+   parameters (evaluated with the bfloat16 matrices, on the tensor cores with
+   FP32 accumulation and activations split into bfloat16 high part and
+   remainder; within about 1e-5 of FP32 arithmetic). loss: host double (may be
    NULL); grad: device float[TFKT_MLP_NWEIGHTS] (may be NULL; the gradient is
    also kept for tfkt_mlp_adam). Deterministic: fixed reduction order. */
 tfkt_status tfkt_mlp_loss_grad(tfkt_mlp* net, const float* X, const float* T, int64_t n,
