@@ -134,10 +134,16 @@ enum {
   TFKT_NFIELDS
 };
 
-/* Global diagnostics of tfkt_diagnostics (FP64 sums over all r-nodes). */
+/* Global diagnostics of tfkt_diagnostics. MASS_S..EY2 are FP64 sums over all
+   r-nodes (QRMS_MEAN the mean); the last two are maxima over the r-nodes:
+   TFKT_D_U2_MAX holds max |u| (its square is what is reduced), a guard on the
+   low-Mach condition |u| << c_s = 1/sqrt(3) under which the D2Q9 equilibrium
+   of Sec. VI A holds, and TFKT_D_QRMS_MAX the largest local Q_rms (Sec. VII).
+   A maximum meets a NaN node as NaN. */
 enum {
   TFKT_D_MASS_S = 0, TFKT_D_MASS_P, TFKT_D_PX, TFKT_D_PY, TFKT_D_KE,
-  TFKT_D_ENSTROPHY, TFKT_D_QRMS_MEAN, TFKT_D_EY2, TFKT_NDIAG
+  TFKT_D_ENSTROPHY, TFKT_D_QRMS_MEAN, TFKT_D_EY2, TFKT_D_U2_MAX, TFKT_D_QRMS_MAX,
+  TFKT_NDIAG
 };
 
 /* Device bytes that tfkt_create needs for these parameters (two population
@@ -178,7 +184,9 @@ tfkt_status tfkt_moments(tfkt_ctx* ctx, uint32_t field_mask, double* dst, size_t
 tfkt_status tfkt_psi(tfkt_ctx* ctx, double* dst, size_t bytes, int dst_is_device);
 
 /* Global diagnostics into host out[TFKT_NDIAG]; synchronises. TFKT_ENAN if
-   any is not finite. */
+   any is not finite: out still holds all values, tfkt_last_error names the
+   first non-finite one and the step, and the context stays usable (the state
+   is neither changed nor reset). */
 tfkt_status tfkt_diagnostics(tfkt_ctx* ctx, double* out);
 
 /* The stored (post-collision, not yet streamed) populations g' as doubles in

@@ -538,8 +538,13 @@ tfkt_status do_diag(Ctx* c, double* out) {
   TFKT_CUDA(c, cudaMemcpyAsync(out, dout, TFKT_NDIAG * sizeof(double), cudaMemcpyDeviceToHost,
                                c->stream));
   TFKT_CUDA(c, cudaStreamSynchronize(c->stream));
+  static const char* const names[TFKT_NDIAG] = {"mass_s", "mass_p", "px", "py", "ke",
+                                                "enstrophy", "qrms_mean", "ey2", "umax",
+                                                "qrms_max"};
   for (int j = 0; j < TFKT_NDIAG; ++j)
-    if (!std::isfinite(out[j])) return fail(TFKT_ENAN, "non-finite diagnostic");
+    if (!std::isfinite(out[j]))
+      return fail(TFKT_ENAN, std::string("non-finite diagnostic ") + names[j] + " at step " +
+                                 std::to_string(c->step));
   return TFKT_OK;
 }
 
@@ -607,6 +612,7 @@ tfkt_status tfkt_required_bytes(const tfkt_params* p, size_t* bytes) {
 
 tfkt_status tfkt_create(const tfkt_params* p, const double* perturb, void* dev_workspace,
                         size_t workspace_bytes, void* stream, tfkt_ctx** out) {
+  NvtxRange nvtx_range("tfkt_create");
   if (!out) return fail(TFKT_EINVAL, "out is NULL");
   *out = nullptr;
   Lattice L;
@@ -653,6 +659,7 @@ tfkt_status tfkt_create(const tfkt_params* p, const double* perturb, void* dev_w
 }
 
 tfkt_status tfkt_step(tfkt_ctx* c, int64_t n) {
+  NvtxRange nvtx_range("tfkt_step");
   tfkt_status s = check_ctx(c);
   if (s != TFKT_OK) return s;
   if (n < 0) return fail(TFKT_EINVAL, "n must be >= 0");
@@ -660,6 +667,7 @@ tfkt_status tfkt_step(tfkt_ctx* c, int64_t n) {
 }
 
 tfkt_status tfkt_step_profiled(tfkt_ctx* c, int64_t n, double* kernel_ms, int64_t* launches) {
+  NvtxRange nvtx_range("tfkt_step_profiled");
   tfkt_status s = check_ctx(c);
   if (s != TFKT_OK) return s;
   if (n < 0 || !kernel_ms) return fail(TFKT_EINVAL, "n must be >= 0 and kernel_ms non-NULL");
@@ -667,6 +675,7 @@ tfkt_status tfkt_step_profiled(tfkt_ctx* c, int64_t n, double* kernel_ms, int64_
 }
 
 tfkt_status tfkt_moments(tfkt_ctx* c, uint32_t mask, double* dst, size_t bytes, int dst_is_device) {
+  NvtxRange nvtx_range("tfkt_moments");
   tfkt_status s = check_ctx(c);
   if (s != TFKT_OK) return s;
   if (!dst) return fail(TFKT_EINVAL, "dst is NULL");
@@ -677,6 +686,7 @@ tfkt_status tfkt_moments(tfkt_ctx* c, uint32_t mask, double* dst, size_t bytes, 
 }
 
 tfkt_status tfkt_psi(tfkt_ctx* c, double* dst, size_t bytes, int dst_is_device) {
+  NvtxRange nvtx_range("tfkt_psi");
   tfkt_status s = check_ctx(c);
   if (s != TFKT_OK) return s;
   if (!dst) return fail(TFKT_EINVAL, "dst is NULL");
@@ -686,6 +696,7 @@ tfkt_status tfkt_psi(tfkt_ctx* c, double* dst, size_t bytes, int dst_is_device) 
 }
 
 tfkt_status tfkt_diagnostics(tfkt_ctx* c, double* out) {
+  NvtxRange nvtx_range("tfkt_diagnostics");
   tfkt_status s = check_ctx(c);
   if (s != TFKT_OK) return s;
   if (!out) return fail(TFKT_EINVAL, "out is NULL");
@@ -693,6 +704,7 @@ tfkt_status tfkt_diagnostics(tfkt_ctx* c, double* out) {
 }
 
 tfkt_status tfkt_populations(tfkt_ctx* c, double* host_dst, size_t bytes) {
+  NvtxRange nvtx_range("tfkt_populations");
   tfkt_status s = check_ctx(c);
   if (s != TFKT_OK) return s;
   if (!host_dst) return fail(TFKT_EINVAL, "dst is NULL");

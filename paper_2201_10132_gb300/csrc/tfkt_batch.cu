@@ -253,6 +253,7 @@ tfkt_status tfkt_batch_required_bytes(const tfkt_params* runs, int32_t n, size_t
 tfkt_status tfkt_batch_create(const tfkt_params* runs, int32_t n, const double* const* perturbs,
                               void* dev_workspace, size_t workspace_bytes, void* stream,
                               tfkt_batch** out) {
+  NvtxRange nvtx_range("tfkt_batch_create");
   if (!out) return fail(TFKT_EINVAL, "out is NULL");
   *out = nullptr;
   std::vector<Lattice> L;
@@ -347,6 +348,7 @@ tfkt_status tfkt_batch_create(const tfkt_params* runs, int32_t n, const double* 
 }
 
 tfkt_status tfkt_batch_step(tfkt_batch* b, int64_t n) {
+  NvtxRange nvtx_range("tfkt_batch_step");
   if (!b) return fail(TFKT_EINVAL, "batch is NULL");
   if (n < 0) return fail(TFKT_EINVAL, "n must be >= 0");
   tfkt_status s = TFKT_OK;

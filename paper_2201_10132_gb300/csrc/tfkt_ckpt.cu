@@ -166,6 +166,7 @@ using namespace tfkt;
 extern "C" {
 
 tfkt_status tfkt_save(tfkt_ctx* ctx, const char* path) {
+  NvtxRange nvtx_range("tfkt_save");
   if (!ctx || !path) return fail(TFKT_EINVAL, "NULL context or path");
   Ctx* c = ctx_of(ctx);
   if (c->poisoned) return fail(TFKT_ESTATE, "context poisoned by an earlier CUDA error");
@@ -225,6 +226,7 @@ tfkt_status tfkt_save(tfkt_ctx* ctx, const char* path) {
 }
 
 tfkt_status tfkt_load(tfkt_ctx* ctx, const char* path) {
+  NvtxRange nvtx_range("tfkt_load");
   if (!ctx || !path) return fail(TFKT_EINVAL, "NULL context or path");
   Ctx* c = ctx_of(ctx);
   if (c->poisoned) return fail(TFKT_ESTATE, "context poisoned by an earlier CUDA error");

@@ -4,6 +4,7 @@
 
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstddef>
 #include <cstdint>
@@ -13,6 +14,16 @@
 #include "tfkt.h"
 
 namespace tfkt {
+
+// Scoped NVTX range naming one call of the C interface (create, step,
+// diagnostics, ...) on a profiler timeline. NVTX v3 is header-only; with no
+// tool attached a push or pop is a call into an empty function.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ---------------------------------------------------------------- lattices
 // D2Q9 (Sec. VI-A): rest, the four axis velocities, the four diagonals.

@@ -636,8 +636,25 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Block partial sums of the global diagnostics (Sec. VII follows the
-// enstrophy and Q_rms). A block takes whole rows, a thread every DIAG_THREADS-th
+// Maximum that keeps a NaN once it has met one (fmax would drop it), so that
+// a non-finite node shows in the maximum diagnostics too.
+template <typename T>
+__device__ __forceinline__ T nan_max(T m, T v) {
+  return (v > m || v != v) ? v : m;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) v = nan_max(v, __shfl_down_sync(0xffffffffu, v, s));
+  return v;
+}
+// Diagnostics reduced by maximum rather than by sum.
+__host__ __device__ constexpr bool diag_is_max(int j) {
+  return j == TFKT_D_U2_MAX || j == TFKT_D_QRMS_MAX;
+}
+
+// Block partials of the global diagnostics (Sec. VII follows the enstrophy
+// and Q_rms): sums, and the maxima of |u|^2 (a Mach-number guard, since the
+// lattice scheme holds only for |u| well below c_s) and of Q_rms. A block takes whole rows, a thread every DIAG_THREADS-th
 // node of a row. Per node only what the sums need is formed, in the context's
 // precision and as deviations from the rest state (sum_q delta psi, and
 // sum_q delta psi Q^2 for Q_rms); the rest-state constants are added once.
@@ -655,10 +672,10 @@ __global__ void __launch_bounds__(DIAG_THREADS) diag_partial_kernel(KernelArgs<r
     const real Qx = a.tab.qx[q], Qy = a.tab.qy[q];
     s0 += a.tab.psi0[q] * (Qx * Qx + Qy * Qy);
   }
-  double acc[TFKT_NDIAG] = {0, 0, 0, 0, 0, 0, 0, 0};
+  double acc[TFKT_NDIAG] = {};
   for (int y = blockIdx.x; y < a.ny; y += gridDim.x) {
     const int ym = y == 0 ? a.ny - 1 : y - 1, yp = y == a.ny - 1 ? 0 : y + 1;
-    real r[TFKT_NDIAG] = {0, 0, 0, 0, 0, 0, 0, 0};
+    real r[TFKT_NDIAG] = {};
     for (int x = threadIdx.x; x < a.nx; x += DIAG_THREADS) {
       const size_t n = (size_t)y * a.pitch + x;
       real dpt = 0, sq = 0;
@@ -680,24 +697,30 @@ __global__ void __launch_bounds__(DIAG_THREADS) diag_partial_kernel(KernelArgs<r
       r[TFKT_D_PY] += rho * uy;
       r[TFKT_D_KE] += real(0.5) * rho * (ux * ux + uy * uy);
       r[TFKT_D_ENSTROPHY] += real(0.5) * w * w;
-      r[TFKT_D_QRMS_MEAN] += pt != real(0) ? sqrt(a.l2 * (s0 + sq) / pt) : real(0);
+      const real qrms = pt != real(0) ? sqrt(a.l2 * (s0 + sq) / pt) : real(0);
+      r[TFKT_D_QRMS_MEAN] += qrms;
       r[TFKT_D_EY2] += uy * uy;
+      r[TFKT_D_U2_MAX] = nan_max(r[TFKT_D_U2_MAX], ux * ux + uy * uy);
+      r[TFKT_D_QRMS_MAX] = nan_max(r[TFKT_D_QRMS_MAX], qrms);
     }
 #pragma unroll
-    for (int j = 0; j < TFKT_NDIAG; ++j) acc[j] += double(r[j]);
+    for (int j = 0; j < TFKT_NDIAG; ++j)
+      acc[j] = diag_is_max(j) ? nan_max(acc[j], double(r[j])) : acc[j] + double(r[j]);
   }
   __shared__ double red[DIAG_THREADS / 32][TFKT_NDIAG];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int j = 0; j < TFKT_NDIAG; ++j) {
-    const double v = warp_sum(acc[j]);
+    const double v = diag_is_max(j) ? warp_max(acc[j]) : warp_sum(acc[j]);
     if (lane == 0) red[warp][j] = v;
   }
   __syncthreads();
   if (threadIdx.x < TFKT_NDIAG) {
+    const int j = threadIdx.x;
     double s = 0;
-    for (int w = 0; w < DIAG_THREADS / 32; ++w) s += red[w][threadIdx.x];
-    partials[(size_t)blockIdx.x * TFKT_NDIAG + threadIdx.x] = s;
+    for (int w = 0; w < DIAG_THREADS / 32; ++w)
+      s = diag_is_max(j) ? nan_max(s, red[w][j]) : s + red[w][j];
+    partials[(size_t)blockIdx.x * TFKT_NDIAG + j] = s;
   }
 }
 
@@ -708,13 +731,19 @@ __global__ void diag_final_kernel(const double* partials, int nblocks, double in
                                   double base_p, double* out) {
   const int j = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (j >= TFKT_NDIAG) return;
+  const bool mx = diag_is_max(j);
   double s = 0;
-  for (int b = lane; b < nblocks; b += 32) s += partials[(size_t)b * TFKT_NDIAG + j];
-  s = warp_sum(s);
+  for (int b = lane; b < nblocks; b += 32) {
+    const double v = partials[(size_t)b * TFKT_NDIAG + j];
+    s = mx ? nan_max(s, v) : s + v;
+  }
+  s = mx ? warp_max(s) : warp_sum(s);
   if (lane == 0) {
     if (j == TFKT_D_MASS_S) s += base_s;
     if (j == TFKT_D_MASS_P) s += base_p;
-    out[j] = j == TFKT_D_QRMS_MEAN ? s * inv_n : s;
+    if (j == TFKT_D_QRMS_MEAN) s *= inv_n;
+    if (j == TFKT_D_U2_MAX) s = sqrt(s);   // reported as max |u|
+    out[j] = s;
   }
 }
 

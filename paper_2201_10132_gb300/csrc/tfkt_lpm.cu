@@ -513,6 +513,7 @@ using namespace tfkt;
 
 extern "C" tfkt_status tfkt_lpm_run(tfkt_ctx* cc, const tfkt_mlp* net, const tfkt_lpm_opts* o,
                                     int64_t nblocks, int64_t* flagged) {
+  NvtxRange nvtx_range("tfkt_lpm_run");
   if (!cc || !o) return fail(TFKT_EINVAL, "NULL argument");
   Ctx* c = ctx_of(cc);
   tfkt_status s = check(c, o->K);
@@ -575,6 +576,7 @@ extern "C" tfkt_status tfkt_lpm_run(tfkt_ctx* cc, const tfkt_mlp* net, const tfk
 }
 
 extern "C" tfkt_status tfkt_lpm_features(tfkt_ctx* cc, int32_t K, float* X, float* Cdep) {
+  NvtxRange nvtx_range("tfkt_lpm_features");
   if (!cc || !X || !Cdep) return fail(TFKT_EINVAL, "NULL argument");
   Ctx* c = ctx_of(cc);
   tfkt_status s = check(c, K);
@@ -594,6 +596,7 @@ extern "C" tfkt_status tfkt_lpm_features(tfkt_ctx* cc, int32_t K, float* X, floa
 }
 
 extern "C" tfkt_status tfkt_lpm_targets(tfkt_ctx* cc, const float* Cdep, float* T) {
+  NvtxRange nvtx_range("tfkt_lpm_targets");
   if (!cc || !Cdep || !T) return fail(TFKT_EINVAL, "NULL argument");
   Ctx* c = ctx_of(cc);
   tfkt_status s = check(c, 2);

@@ -472,6 +472,7 @@ tfkt_status tfkt_mlp_set(tfkt_mlp* net, const float* params) {
 }
 
 tfkt_status tfkt_mlp_forward(tfkt_mlp* net, const float* X, int64_t n, float* Y) {
+  NvtxRange nvtx_range("tfkt_mlp_forward");
   if (!net || n < 0 || (n > 0 && (!X || !Y))) return fail(TFKT_EINVAL, "bad argument");
   if (n == 0) return TFKT_OK;
   const int64_t blocks = (n + 127) / 128;
@@ -483,6 +484,7 @@ tfkt_status tfkt_mlp_forward(tfkt_mlp* net, const float* X, int64_t n, float* Y)
 
 tfkt_status tfkt_mlp_loss_grad(tfkt_mlp* net, const float* X, const float* T, int64_t n,
                                double* loss, float* grad) {
+  NvtxRange nvtx_range("tfkt_mlp_loss_grad");
   if (!net || n < 1 || !X || !T) return fail(TFKT_EINVAL, "bad argument");
   const int64_t nb = (n + TB - 1) / TB;
   if (nb > (1 << 20)) return fail(TFKT_EINVAL, "batch too large (at most 2^27 samples)");
@@ -509,6 +511,7 @@ tfkt_status tfkt_mlp_loss_grad(tfkt_mlp* net, const float* X, const float* T, in
 }
 
 tfkt_status tfkt_mlp_adam(tfkt_mlp* net, float lr, float beta1, float beta2, float eps) {
+  NvtxRange nvtx_range("tfkt_mlp_adam");
   if (!net) return fail(TFKT_EINVAL, "NULL argument");
   if (!(lr >= 0) || !(beta1 >= 0 && beta1 < 1) || !(beta2 >= 0 && beta2 < 1) || !(eps > 0))
     return fail(TFKT_EINVAL, "bad Adam hyper-parameters");

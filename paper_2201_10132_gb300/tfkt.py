@@ -19,10 +19,11 @@ FP64, FP32, FP16 = 0, 1, 2
 FIELDS = ["rho_s", "psi_tot", "ux", "uy", "cxx", "cxy", "cyy", "thxx", "thxy", "thyy", "qrms",
           "vort"]
 KERNELS = ["moments", "step", "fused", "fixup"]
-DIAGS = ["mass_s", "mass_p", "px", "py", "ke", "enstrophy", "qrms_mean", "ey2"]
+DIAGS = ["mass_s", "mass_p", "px", "py", "ke", "enstrophy", "qrms_mean", "ey2", "umax",
+         "qrms_max"]
 STATUS = {0: "TFKT_OK", 1: "TFKT_EINVAL", 2: "TFKT_ENOMEM", 3: "TFKT_ECUDA", 4: "TFKT_ENAN",
           5: "TFKT_ESTATE", 6: "TFKT_EIO"}
-EINVAL, EIO = 1, 6
+EINVAL, ENAN, EIO = 1, 4, 6
 
 
 class TfktError(RuntimeError):

@@ -134,6 +134,9 @@ def test_fp64_matches_oracle(T, oracle_mod, case):
         assert diag[k] == pytest.approx(od[k], rel=1e-12, abs=1e-300), k
     for k in ("px", "py"):
         assert diag[k] == pytest.approx(od[k], rel=1e-9, abs=1e-13 * max(1.0, od["mass_s"])), k
+    # maxima over the nodes of the oracle's own fields
+    assert diag["umax"] == pytest.approx(np.hypot(f["ux"], f["uy"]).max(), rel=1e-12, abs=1e-300)
+    assert diag["qrms_max"] == pytest.approx(f["qrms"].max(), rel=1e-12, abs=1e-300)
 
 
 @pytest.mark.parametrize("case", [CASES[1], CASES[2], CASES[3], CASES[7], CASES[9], FENE[1],
@@ -168,6 +171,9 @@ def test_fp32_within_tolerance(T, oracle_mod, case):
            "ey2": 2 * du * np.abs(f["uy"]).sum() + 1e-30}
     for k, t in tol.items():
         assert abs(diag[k] - od[k]) <= t, (k, diag[k], od[k], t)
+    umax = np.hypot(f["ux"], f["uy"]).max()
+    assert abs(diag["umax"] - umax) <= 2 * du, (diag["umax"], umax)
+    assert abs(diag["qrms_max"] - f["qrms"].max()) <= 2e-5 * max(f["qrms"].max(), 1e-30)
 
 
 @pytest.mark.parametrize("case", [CASES[1], CASES[7], CASES[9]])
