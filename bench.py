@@ -221,6 +221,56 @@ def precision_sweep(W, steps: int):
     return out
 
 
+def capacity_run(steps: int, warmup: int):
+    """The largest run that one GPU holds: 8192^2 r-nodes, N_Q = 32, with FP16 polymer
+    storage (FP32 solvent); FP32 storage would need more memory than the GPU has. Time
+    per step, GLUPS, the fused kernel's algorithmic bandwidth, and mass conservation
+    over the timed steps. Skipped (with the sizes) when the workspace does not fit."""
+    import numpy as np
+    import torch
+    from paper_2201_10132_gb300 import tfkt
+    from paper_2201_10132_gb300.inputs import KOLMOGOROV_8192 as W, perturbation
+    p = tfkt.Params.from_workload(W, tfkt.FP16)
+    need16 = tfkt.required_bytes(p)
+    need32 = tfkt.required_bytes(tfkt.Params.from_workload(W, tfkt.FP32))
+    free, total = torch.cuda.mem_get_info()
+    out = {"workload": W.name, "storage": "fp16 polymer (scaled deviations), fp32 solvent",
+           "workspace_gb": need16 / 1e9, "fp32_workspace_gb": need32 / 1e9,
+           "device_total_gb": total / 1e9, "device_free_gb": free / 1e9}
+    if need16 > 0.97 * free:
+        out["skipped"] = "workspace does not fit the free device memory"
+        return out
+    ws = torch.empty(need16, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.Stream()
+    with tfkt.Solver(p, perturbation(W.nx, W.ny, W.seed, W.amp, W.u0), workspace=ws,
+                     stream=stream.cuda_stream) as s:
+        s.step(warmup)
+        d0 = s.diagnostics()
+        kms = np.zeros(len(tfkt.KERNELS))
+        n = np.zeros(len(tfkt.KERNELS), np.int64)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step_profiled(steps, kms, n)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        d1 = s.diagnostics()
+        info = s.info
+    k = tfkt.KERNELS.index("fused")
+    fused_ms = kms[k] / max(n[k], 1)
+    nodes = W.nx * W.ny
+    peak, kind = _peaks()
+    gbs = info["bytes_per_node_step"] * nodes / (fused_ms / 1e3) / 1e9
+    m0, m1 = d0["mass_s"] + d0["mass_p"], d1["mass_s"] + d1["mass_p"]
+    out.update({"steps": steps, "ms_per_step": ms, "value": aggregate_glups(1, nodes, steps, ms * steps / 1e3),
+                "unit": "GLUPS", "fused_ms": fused_ms, "fused_algorithmic_gbs": gbs,
+                "fused_frac_of_hbm": gbs / peak, "peak_kind": kind,
+                "bytes_per_node_step": info["bytes_per_node_step"],
+                "mass_rel_drift": abs(m1 - m0) / m0, "umax": d1["umax"]})
+    return out
+
+
 def learned_vs_plain(W, nblocks: int, warm: int, only: bool = False):
     """The learned macro-step (1 plain step + K solvent sub-steps per block, the
     committed network) against the plain FP32 step and the FP64 step on the same
@@ -333,6 +383,8 @@ def main():
                     help="instead of the throughput line: a seeded ensemble advanced as one batch")
     ap.add_argument("--precision-sweep", type=int, default=0, metavar="STEPS",
                     help="instead of the throughput line: FP64 vs FP32 vs FP16 errors and times")
+    ap.add_argument("--capacity", action="store_true",
+                    help="instead of the throughput line: the 8192^2 run in FP16 storage")
     ap.add_argument("--learned", type=int, default=0, metavar="BLOCKS",
                     help="instead of the throughput line: the learned macro-step against the "
                          "plain step (speed, field and growth-rate errors)")
@@ -350,6 +402,11 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         print(json.dumps({"ensemble": ensemble_throughput(args.ensemble, args.steps,
                                                           args.warmup)}), flush=True)
+        return
+    if args.capacity:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        print(json.dumps({"capacity": capacity_run(args.steps, args.warmup)}), flush=True)
         return
     if args.learned:
         import torch

@@ -50,8 +50,9 @@ typedef enum {
 typedef enum {
   TFKT_FP64 = 0,    /* populations stored and updated in double */
   TFKT_FP32 = 1,    /* populations stored as float deviations from rest, updated in float */
-  TFKT_FP16 = 2     /* populations stored as half deviations from rest (rounded to nearest),
-                       updated in float; moment planes in float */
+  TFKT_FP16 = 2     /* polymer populations stored as half deviations from rest (rounded to
+                       nearest, scaled by a power of two), solvent populations as float
+                       deviations; updated in float; moment planes in float */
 } tfkt_precision;
 
 /* Quasi-equilibrium of the collision (Sec. V): which variables the fast
@@ -207,10 +208,12 @@ tfkt_status tfkt_populations(tfkt_ctx* ctx, double* host_dst, size_t bytes);
    pops:   device pointer to a population buffer in a context's storage
            layout. A context created on workspace W keeps its state, after
            n steps, at W + (n mod 2) * B with B = the population bytes
-           (9 + 25 nq) * ny * pitch * element size rounded up to 256
-           (nq, pitch from tfkt_get_info; element size 8 for TFKT_FP64,
-           4 for TFKT_FP32, 2 for TFKT_FP16), but never less than
-           TFKT_NFIELDS * ny * nx * 8 bytes.
+           rounded up to 256, but never less than TFKT_NFIELDS * ny * nx * 8
+           bytes. The population bytes are (9 + 25 nq) * ny * pitch * e (nq,
+           pitch from tfkt_get_info; e = 8 for TFKT_FP64, 4 for TFKT_FP32,
+           2 for TFKT_FP16): planes 0..8 the solvent, 9 + 25 q + i the
+           polymer; under TFKT_FP16 planes 0..8 are unused and the nine
+           solvent planes follow as floats, 9 * ny * pitch * 4 bytes more.
    dst:    device pointer, popcount(field_mask) * ny * nx doubles; bytes is
            its size.
    stream: cudaStream_t or NULL. The lattice tables are copied from host

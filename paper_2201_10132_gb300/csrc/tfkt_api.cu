@@ -138,6 +138,13 @@ size_t store_size(const Lattice& L) {
   return L.precision == TFKT_FP64 ? 8 : (L.precision == TFKT_FP16 ? 2 : 4);
 }
 
+// 9 + 25 nq plane slots of the storage type, and under FP16 storage the nine
+// FP32 solvent planes after them (the layout of solvent_planes).
+size_t population_bytes(const Lattice& L) {
+  const size_t slots = (size_t)L.npl * L.plane * store_size(L);
+  return L.precision == TFKT_FP16 ? slots + 9 * L.plane * sizeof(float) : slots;
+}
+
 // Blocks of the diagnostics reduction: one or more rows each, at most 8 per SM.
 int diag_blocks_for(const Lattice& L) { return L.ny < 8 * 152 ? L.ny : 8 * 152; }
 
@@ -147,7 +154,7 @@ size_t layout(const Lattice& L, Workspace* w) {
   size_t o = 0;
   // a population buffer also stages field output (doubles) and the initial perturbation
   const size_t N = (size_t)L.nx * L.ny;
-  size_t pop = (size_t)L.npl * L.plane * store_size(L);
+  size_t pop = population_bytes(L);
   if (pop < (size_t)TFKT_NFIELDS * N * sizeof(double)) pop = (size_t)TFKT_NFIELDS * N * sizeof(double);
   w->off_pop[0] = o;
   o = align_up(o + pop, A);
@@ -740,7 +747,7 @@ tfkt_status tfkt_get_info(const tfkt_ctx* c, tfkt_info* info) {
   i.workspace_bytes = c->ws.bytes;
   i.pitch = L.pitch;
   // each population read once and written once, each moment plane read and written once
-  i.bytes_per_node_step = (size_t)L.npl * 2 * store_size(L) + (size_t)L.nm * 2 * real_size(L);
+  i.bytes_per_node_step = 2 * population_bytes(L) / L.plane + (size_t)L.nm * 2 * real_size(L);
   *info = i;
   return TFKT_OK;
 }

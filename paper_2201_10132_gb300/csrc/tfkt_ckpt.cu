@@ -5,7 +5,7 @@
 // header (magic, version, the derived lattice parameters that fix the meaning
 // of the state, the step count, the payload sizes and a checksum), then the
 // raw current population buffer (9 + 25 nq planes of the storage type, row
-// pitch included) and, when they are valid, the current moment planes (the
+// pitch included, and under FP16 storage the FP32 solvent planes after them) and, when they are valid, the current moment planes (the
 // fused path carries them from step to step). Resuming from the file gives
 // the same trajectory bit for bit as the run that was never stopped.
 //
@@ -153,7 +153,7 @@ struct File {
   }
 };
 
-size_t pop_bytes(const Lattice& L) { return (size_t)L.npl * L.plane * store_size(L); }
+size_t pop_bytes(const Lattice& L) { return population_bytes(L); }
 size_t m_bytes(const Lattice& L) { return (size_t)L.nm * L.plane * real_size(L); }
 char* pop_ptr(Ctx* c) { return (char*)c->ws.base + c->ws.off_pop[c->cur]; }
 char* m_ptr(Ctx* c) { return (char*)c->ws.base + (c->mcur ? c->ws.off_M2 : c->ws.off_M); }

@@ -244,8 +244,11 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
   const size_t P = a.plane;
   const real* __restrict__ Min = fa.Min;
   real* __restrict__ Mout = fa.Mout;
+  using SS = SolventT<S>;
   const S* __restrict__ src = (const S*)a.src;
   S* __restrict__ dst = (S*)a.dst;
+  const SS* __restrict__ ssrc = solvent_planes<S>(a.src, P, a.nq);
+  SS* __restrict__ sdst = solvent_planes<S>(a.dst, P, a.nq);
 
   // pull offsets within a plane (32-bit: a plane holds < 2^31 elements)
   const int xm = x == 0 ? a.nx - 1 : x - 1, xp = x == a.nx - 1 ? 0 : x + 1;
@@ -328,12 +331,18 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
   };
   // The populations of a Q-node are loaded one Q-node ahead: register h[i] is
   // refilled for Q-node q + 1 as soon as the collision of Q-node q has used it,
-  // so the loads are in flight during the exchange and the barriers.
+  // so the loads are in flight during the exchange and the barriers. A
+  // converted storage type (FP16) is refilled into hr[i] in its stored form and
+  // converted where the next Q-node starts, so that no conversion waits for a
+  // load before the barriers (h[i] and hr[i] are never live at once).
+  constexpr bool RAW = std::is_same<S, real>::value;
+  S hr[25];
   real h[25], mn[4];
   if (nq > 0) {
     const uint32_t bm0 = bounce_mask(0);
     static_for<0, 25>([&](auto I) {
-      h[decltype(I)::value] = from_store<real>(*pull_offset(I, 0, bm0));
+      if constexpr (RAW) h[decltype(I)::value] = *pull_offset(I, 0, bm0);
+      else hr[decltype(I)::value] = *pull_offset(I, 0, bm0);
     });
     mn[0] = Min[off[5]];
     mn[1] = Min[off[3]];
@@ -347,7 +356,7 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
     real drs = 0, jsx = 0, jsy = 0;
     static_for<0, 9>([&](auto I) {
       constexpr int i = I;
-      hs[i] = from_store<real>(src[(size_t)i * P + off[shift_index(-c9x(i), -c9y(i))]]);
+      hs[i] = from_store<real>(ssrc[(size_t)i * P + off[shift_index(-c9x(i), -c9y(i))]]);
       drs += hs[i];
       acc<c9x(i)>(jsx, hs[i]);
       acc<c9y(i)>(jsy, hs[i]);
@@ -371,7 +380,7 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
                                                       real(4.5) * (a.omr * cus * cus + a.r * cu * cu) -
                                                       real(1.5) * sq));
       const real hp = a.om2b * hs[i] + a.tb * feq_dev + a.omb * real(w9(i)) * gx * force;
-      dst[(size_t)i * P + n] = to_store<S>(hp);
+      sdst[(size_t)i * P + n] = to_store<SS>(hp);
       if constexpr (i == 0) ms_arr += hp;
       else sm.hb[(i - 1) * HSZ + hcell] = hp;
     });
@@ -416,8 +425,8 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
       load_vec<DQ>(dl, sm.delta + q * DQ);
 #pragma unroll
       for (int i = 0; i < 25; ++i) {   // unscale (FP16 storage), shift to this Q-node
-        if constexpr (std::is_same<S, real>::value) h[i] += dl[i];
-        else h[i] = h[i] * a.pinv + dl[i];
+        if constexpr (RAW) h[i] += dl[i];
+        else h[i] = from_store<real>(hr[i]) * a.pinv + dl[i];
       }
     }
     if constexpr (RESHAPE) {
@@ -532,7 +541,11 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
         acc<-c25(i).rx>(jx_arr, back);
         acc<-c25(i).ry>(jy_arr, back);
       }
-      if (more) h[i] = from_store<real>(*pull_offset(I, q + 1, bmn));
+      if constexpr (RAW) {
+        if (more) h[i] = *pull_offset(I, q + 1, bmn);
+      } else {
+        if (more) hr[i] = *pull_offset(I, q + 1, bmn);
+      }
     });
     __syncthreads();
     // arrivals from the other r-nodes of the tile

@@ -118,9 +118,34 @@ __host__ __device__ __forceinline__ S to_store(real v) { return (S)v; }
 template <>
 __host__ __device__ __forceinline__ __half to_store<__half, float>(float v) { return __float2half_rn(v); }
 
+// Storage type of the nine solvent planes. FP16 storage keeps them in FP32:
+// the solvent carries nearly all of the mixture momentum, and its stored
+// deviations w_i (3 c_i.u + ...) ~ 1e-2 round in FP16 to ~1e-5, the size of a
+// small velocity perturbation's share of them; they are 9 of 9 + 25 nq planes,
+// so FP32 costs ~1% of the bytes. FP64 and FP32 store them like the polymer.
+template <typename S> struct SolventStore { using type = S; };
+template <> struct SolventStore<__half> { using type = float; };
+template <typename S> using SolventT = typename SolventStore<S>::type;
+
+// A population buffer of storage S holds 9 + 25 nq plane slots of S, `plane`
+// elements each: polymer plane k (k >= 9) in slot k. Solvent planes of the
+// storage type itself fill slots 0..8; FP32 solvent planes under FP16 storage
+// follow the last slot instead (slots 0..8 stay unused), so that the polymer
+// planes keep the addresses they have when every plane is FP16.
+template <typename S>
+__host__ __device__ __forceinline__ const SolventT<S>* solvent_planes(const void* buf, size_t plane,
+                                                                       int nq) {
+  if (sizeof(SolventT<S>) == sizeof(S)) return (const SolventT<S>*)buf;
+  return (const SolventT<S>*)((const S*)buf + (size_t)(9 + 25 * nq) * plane);
+}
+template <typename S>
+__host__ __device__ __forceinline__ SolventT<S>* solvent_planes(void* buf, size_t plane, int nq) {
+  return const_cast<SolventT<S>*>(solvent_planes<S>((const void*)buf, plane, nq));
+}
+
 template <typename real>
 struct KernelArgs {
-  const void* src;               // populations read (pull), storage type of the context
+  const void* src;               // populations read (pull): plane slots, see solvent_planes
   void* dst;                     // populations written
   real* M;                       // moment planes
   real* U;                       // scratch: 2 planes (U_x, U_y)
@@ -199,6 +224,7 @@ size_t align_up(size_t v, size_t a);
 tfkt_status map_params(const tfkt_params* p, Lattice* L);
 size_t real_size(const Lattice& L);   // bytes of the compute type (moment planes, tables)
 size_t store_size(const Lattice& L);  // bytes of the population storage type
+size_t population_bytes(const Lattice& L);  // one population buffer: solvent + polymer planes
 // Polymer populations are stored as (deviation x scale): a power of two that
 // brings them to order one in FP16 storage (exact, so FP16 keeps its full 11
 // bits instead of falling into the subnormal range); 1 for FP32 and FP64.

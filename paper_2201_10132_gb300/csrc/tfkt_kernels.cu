@@ -77,6 +77,8 @@ __device__ __forceinline__ void mixture_velocity(const KernelArgs<real>& a, int 
 // the moments need no second pass over the populations.
 template <typename real, typename S>
 __global__ void __launch_bounds__(256) init_kernel(KernelArgs<real> a) {
+  using SS = SolventT<S>;
+  SS* __restrict__ sdst = solvent_planes<S>(a.dst, a.plane, a.nq);
   S* __restrict__ dst = (S*)a.dst;
   const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
   if (x >= a.nx || y >= a.ny) return;
@@ -104,8 +106,8 @@ __global__ void __launch_bounds__(256) init_kernel(KernelArgs<real> a) {
   for (int i = 0; i < 9; ++i) {
     const real cu = real(c9x(i)) * ux + real(c9y(i)) * uy;
     const real h = real(w9(i)) * (real(3) * cu + real(4.5) * cu * cu - real(1.5) * usq);
-    const S st = to_store<S>(h);
-    dst[(size_t)i * P + off.o[shift_index(-c9x(i), -c9y(i))]] = st;
+    const SS st = to_store<SS>(h);
+    sdst[(size_t)i * P + off.o[shift_index(-c9x(i), -c9y(i))]] = st;
     const real v = from_store<real>(st);
     drho += v;
     jx += real(c9x(i)) * v;
@@ -177,6 +179,7 @@ __global__ void __launch_bounds__(256) moments_kernel(KernelArgs<real> a) {
   const size_t P = a.plane;
   const size_t n = off.o[4];
   const S* __restrict__ src = (const S*)a.src;
+  const SolventT<S>* __restrict__ ssrc = solvent_planes<S>(a.src, P, a.nq);
   auto pull = [&](int q, int i) {
     const V4 c = c25(i);
     const int e = s_pull[q * 25 + i];
@@ -191,7 +194,7 @@ __global__ void __launch_bounds__(256) moments_kernel(KernelArgs<real> a) {
   real drho = 0, jx = 0, jy = 0;
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
-    const real v = from_store<real>(src[(size_t)i * P + off.o[shift_index(-c9x(i), -c9y(i))]]);
+    const real v = from_store<real>(ssrc[(size_t)i * P + off.o[shift_index(-c9x(i), -c9y(i))]]);
     drho += v;
     jx += real(c9x(i)) * v;
     jy += real(c9y(i)) * v;
@@ -276,8 +279,11 @@ __global__ void __launch_bounds__(256) step_kernel(KernelArgs<real> a) {
   const int nq = a.nq;
   const real rho = a.rho0 + a.M[(size_t)(nq + M_DRHO) * P + n];
   const real force = rho * a.tab.arow[y];
+  using SS = SolventT<S>;
   const S* __restrict__ src = (const S*)a.src;
   S* __restrict__ dst = (S*)a.dst;
+  const SS* __restrict__ ssrc = solvent_planes<S>(a.src, P, a.nq);
+  SS* __restrict__ sdst = solvent_planes<S>(a.dst, P, a.nq);
 
   // ---- solvent
   {
@@ -285,7 +291,7 @@ __global__ void __launch_bounds__(256) step_kernel(KernelArgs<real> a) {
     real drs = 0, jsx = 0, jsy = 0;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-      h[i] = from_store<real>(src[(size_t)i * P + off.o[shift_index(-c9x(i), -c9y(i))]]);
+      h[i] = from_store<real>(ssrc[(size_t)i * P + off.o[shift_index(-c9x(i), -c9y(i))]]);
       drs += h[i];
       jsx += real(c9x(i)) * h[i];
       jsy += real(c9y(i)) * h[i];
@@ -305,7 +311,7 @@ __global__ void __launch_bounds__(256) step_kernel(KernelArgs<real> a) {
                                      real(4.5) * (a.omr * cus * cus + a.r * cu * cu) -
                                      real(1.5) * sq));
       const real srcterm = real(w9(i)) * (real(3) * (cx - Ux) + real(9) * cu * cx) * force;
-      dst[(size_t)i * P + n] = to_store<S>(a.om2b * h[i] + a.tb * feq_dev + a.omb * srcterm);
+      sdst[(size_t)i * P + n] = to_store<SS>(a.om2b * h[i] + a.tb * feq_dev + a.omb * srcterm);
     }
   }
 
@@ -415,8 +421,11 @@ __global__ void __launch_bounds__(256) step_stress_kernel(KernelArgs<real> a) {
   const int nq = a.nq;
   const real rho = a.rho0 + a.M[(size_t)(nq + M_DRHO) * P + n];
   const real force = rho * a.tab.arow[y];
+  using SS = SolventT<S>;
   const S* __restrict__ src = (const S*)a.src;
   S* __restrict__ dst = (S*)a.dst;
+  const SS* __restrict__ ssrc = solvent_planes<S>(a.src, P, a.nq);
+  SS* __restrict__ sdst = solvent_planes<S>(a.dst, P, a.nq);
   const real cs2 = real(1) / real(3);
   const real rmix = a.r, omr = a.omr;
 
@@ -426,7 +435,7 @@ __global__ void __launch_bounds__(256) step_stress_kernel(KernelArgs<real> a) {
     real drs = 0, pxx = 0, pxy = 0, pyy = 0;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-      h[i] = from_store<real>(src[(size_t)i * P + off.o[shift_index(-c9x(i), -c9y(i))]]);
+      h[i] = from_store<real>(ssrc[(size_t)i * P + off.o[shift_index(-c9x(i), -c9y(i))]]);
       drs += h[i];
       pxx += real(c9x(i) * c9x(i)) * h[i];
       pxy += real(c9x(i) * c9y(i)) * h[i];
@@ -449,8 +458,8 @@ __global__ void __launch_bounds__(256) step_stress_kernel(KernelArgs<real> a) {
       const real fss_dev = real(w9(i)) * (drs + real(3) * rs * cu + real(4.5) * pneq);
       const real feq_dev = real(w9(i)) * (drs + rs * (real(3) * cu + real(4.5) * cu * cu - real(1.5) * usq));
       const real srcterm = real(w9(i)) * (real(3) * (cx - Ux) + real(9) * cu * cx) * force;
-      dst[(size_t)i * P + n] =
-          to_store<S>(a.om2b * h[i] + a.tb * (omr * fss_dev + rmix * feq_dev) + a.omb * srcterm);
+      sdst[(size_t)i * P + n] =
+          to_store<SS>(a.om2b * h[i] + a.tb * (omr * fss_dev + rmix * feq_dev) + a.omb * srcterm);
     }
   }
 
@@ -613,12 +622,13 @@ __global__ void __launch_bounds__(256) psi_kernel(KernelArgs<real> a, double* ou
 template <typename real, typename S>
 __global__ void __launch_bounds__(256) populations_kernel(KernelArgs<real> a, double* out) {
   const S* src = (const S*)a.src;
+  const SolventT<S>* ssrc = solvent_planes<S>(a.src, a.plane, a.nq);
   const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
   if (x >= a.nx || y >= a.ny) return;
   const size_t n = (size_t)y * a.pitch + x, k = (size_t)y * a.nx + x,
                N = (size_t)a.nx * a.ny;
   for (int i = 0; i < 9; ++i)
-    out[(size_t)i * N + k] = w9(i) + from_store<double>(src[(size_t)i * a.plane + n]);
+    out[(size_t)i * N + k] = w9(i) + from_store<double>(ssrc[(size_t)i * a.plane + n]);
   for (int q = 0; q < a.nq; ++q)
     for (int i = 0; i < 25; ++i) {
       const int p = 9 + 25 * q + i;

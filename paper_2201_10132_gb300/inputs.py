@@ -104,7 +104,12 @@ KOLMOGOROV_1024 = Workload("kolmogorov-1024x1024-nq32", 1024, 1024, 6, 3.0, 10.0
 # Profiling case small enough for a full ncu capture (inputs still larger than L2).
 KOLMOGOROV_512 = Workload("kolmogorov-512x512-nq32", 512, 512, 6, 3.0, 10.0, 1.0, 0.2, 0.05,
                           8, 0, 1e-3)
-WORKLOADS = {w.name: w for w in (KOLMOGOROV_64, KOLMOGOROV_512, KOLMOGOROV_1024, KOLMOGOROV_4096)}
+# Capacity case: the same lattice parameters at 8192^2 (forcing wavelength 64 nodes); it
+# fits one GPU's memory only with FP16 polymer storage.
+KOLMOGOROV_8192 = Workload("kolmogorov-8192x8192-nq32", 8192, 8192, 6, 3.0, 10.0, 1.0, 0.2, 0.05,
+                           128, 0, 1e-3)
+WORKLOADS = {w.name: w for w in (KOLMOGOROV_64, KOLMOGOROV_512, KOLMOGOROV_1024, KOLMOGOROV_4096,
+                                 KOLMOGOROV_8192)}
 
 
 def ensemble(n: int = 256, seed: int = 0, q_side: int = 3, q_radius: float = 1.5):

@@ -178,11 +178,12 @@ def test_fp32_within_tolerance(T, oracle_mod, case):
 
 @pytest.mark.parametrize("case", [CASES[1], CASES[7], CASES[9]])
 def test_fp16_storage_within_tolerance(T, oracle_mod, case):
-    """FP16 storage (half deviations, polymer scaled by a power of two, FP32
-    arithmetic): each stored value is rounded to 11 bits every step, so the
-    velocity error after n steps is about sqrt(n) 2^-12 times the deviation scale
-    (~0.15 w_i) summed over ~25 nq + 9 terms; allowed: 3e-3 of the velocity
-    scale and 3e-3 of each other field's largest magnitude for n <= 25."""
+    """FP16 storage (polymer deviations in half, scaled by a power of two; solvent
+    deviations in float; FP32 arithmetic): each stored polymer value is rounded
+    to 11 bits every step, so the conformation error after n steps is about
+    sqrt(n) 2^-12 times the deviation scale summed over 25 nq terms; allowed:
+    3e-3 of the velocity scale and 3e-3 of each other field's largest magnitude
+    for n <= 25."""
     from paper_2201_10132_gb300.inputs import perturbation
     nx, ny, S, R, re, wi, beta, kp, tau2, ic, steps, fb, qe = _case(case)
     pert = perturbation(nx, ny, 7, 0.05, 0.05)
