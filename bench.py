@@ -26,14 +26,15 @@ sys.path.insert(0, ROOT)
 L2_BYTES = 129e6
 
 
-def _measured_traffic(nodes: int):
+def _measured_traffic(nodes: int, storage: str = "fp32"):
     """DRAM bytes of one fused-kernel launch, scaled by r-nodes from the committed ncu
-    summary of the small case; None once the kernel source no longer matches it."""
+    summary of the small case in the same storage; None once the kernel source no
+    longer matches it."""
     import hashlib
     import re
+    name = "step_fused_kernel_kolmogorov_512x512_nq32" + ("" if storage == "fp32" else "_" + storage)
     try:
-        text = open(os.path.join(ROOT, "profiles",
-                                 "step_fused_kernel_kolmogorov_512x512_nq32.md")).read()
+        text = open(os.path.join(ROOT, "profiles", name + ".md")).read()
         src = open(os.path.join(ROOT, "paper_2201_10132_gb300", "csrc", "tfkt_fused.cu"),
                    "rb").read()
     except OSError:
@@ -378,6 +379,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="kolmogorov-4096x4096-nq32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16"],
+                    help="population storage of the throughput run (compute is FP32 in both)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--ensemble", type=int, default=0, metavar="RUNS",
                     help="instead of the throughput line: a seeded ensemble advanced as one batch")
@@ -444,7 +447,7 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    p = tfkt.Params.from_workload(W, tfkt.FP32)
+    p = tfkt.Params.from_workload(W, tfkt.FP16 if args.storage == "fp16" else tfkt.FP32)
     nodes = W.nx * W.ny
     ws = torch.empty(tfkt.required_bytes(p), dtype=torch.uint8, device="cuda")
     pert = torch.from_numpy(perturbation(W.nx, W.ny, replica_seed(W.seed, rank), W.amp,
@@ -498,12 +501,14 @@ def main():
 
     if rank == 0:
         hbm_peak, peak_kind = _peaks()
-        s = 4  # bytes per stored value (FP32)
+        s = 4  # bytes per moment value (FP32)
         npl, nm = 9 + 25 * info["nq"], info["nq"] + 6
+        # bytes of a node's populations: FP32, or FP32 solvent and FP16 polymer
+        pb = npl * s if args.storage == "fp32" else 9 * 4 + 25 * info["nq"] * 2
         # algorithmic bytes per launch: each population read once and written once;
         # moment planes read once (and written once where the kernel produces them)
-        model = {"moments": nodes * (npl + nm) * s, "step": nodes * (2 * npl + nm) * s,
-                 "fused": nodes * (2 * npl + 2 * nm) * s, "fixup": None}
+        model = {"moments": nodes * (pb + nm * s), "step": nodes * (2 * pb + nm * s),
+                 "fused": nodes * (2 * pb + 2 * nm * s), "fixup": None}
         per = {}
         for k, name in enumerate(tfkt.KERNELS):
             if launches[k]:
@@ -522,16 +527,17 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": W.name, "nx": W.nx, "ny": W.ny, "nq": info["nq"],
                        "re": W.re, "wi": W.wi, "beta": W.beta, "k_periods": W.k_periods,
-                       "storage": "fp32 deviations from rest",
-                       "l2": f"inputs larger than L2 (populations {nodes * npl * s / 1e9:.2f} GB "
+                       "storage": "fp32 deviations from rest" if args.storage == "fp32" else
+                                  "fp16 polymer deviations (scaled), fp32 solvent deviations",
+                       "l2": f"inputs larger than L2 (populations {nodes * pb / 1e9:.2f} GB "
                              "per buffer, L2 129 MB)",
                        "parallelism": f"{world} independent runs"},
             "roofline": {"bound": "hbm", "kernel": top + "_kernel", "achieved": ach,
                          "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
                          "peak_kind": peak_kind,
-                         "traffic": _measured_traffic(nodes) if top == "fused" else None,
+                         "traffic": _measured_traffic(nodes, args.storage) if top == "fused" else None,
                          "bytes_per_launch": per[top]["bytes_per_launch"],
-                         "step_model_gbs": nodes * (2 * npl + 2 * nm) * s / (ms / args.steps / 1e3) / 1e9,
+                         "step_model_gbs": nodes * (2 * pb + 2 * nm * s) / (ms / args.steps / 1e3) / 1e9,
                          "kernels": per},
             "e2e": e2e,
             "gpu_launches": int(launches.sum()),

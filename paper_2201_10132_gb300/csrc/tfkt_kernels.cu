@@ -646,11 +646,17 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Maximum that keeps a NaN once it has met one (fmax would drop it), so that
-// a non-finite node shows in the maximum diagnostics too.
-template <typename T>
-__device__ __forceinline__ T nan_max(T m, T v) {
-  return (v > m || v != v) ? v : m;
+// Maximum of non-negative values (|u|^2, Q_rms) that keeps a NaN once it has
+// met one (fmax would drop it), so that a non-finite node shows in the maximum
+// diagnostics too. For IEEE values with the sign bit clear the order of the
+// bit patterns read as unsigned integers is the numeric order, and every NaN
+// (of either sign) lies above +inf: one integer maximum.
+__device__ __forceinline__ float nan_max(float m, float v) {
+  return __uint_as_float(max(__float_as_uint(m), __float_as_uint(v)));
+}
+__device__ __forceinline__ double nan_max(double m, double v) {
+  return __longlong_as_double((long long)max((unsigned long long)__double_as_longlong(m),
+                                             (unsigned long long)__double_as_longlong(v)));
 }
 __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
@@ -672,16 +678,23 @@ __host__ __device__ constexpr bool diag_is_max(int j) {
 // in FP64 across segments, blocks and the final reduction: FP64 arithmetic,
 // slow on this GPU, stays out of the per-node work of FP32 contexts, while
 // FP64 contexts keep FP64 throughout.
+// |Q|^2 of every Q-node is staged in shared memory; a node's moment planes
+// are loaded eight at a time so that several loads are in flight per thread
+// (the sums still run in Q-node order).
 template <typename real>
 __global__ void __launch_bounds__(DIAG_THREADS) diag_partial_kernel(KernelArgs<real> a,
                                                                     double* partials) {
+  extern __shared__ unsigned char diag_smem[];
+  real* q2 = reinterpret_cast<real*>(diag_smem);
   const int nq = a.nq;
   const size_t P = a.plane;
-  real s0 = 0;   // sum_q psi0(q) |Q|^2 of the rest state
-  for (int q = 0; q < nq; ++q) {
+  for (int q = threadIdx.x; q < nq; q += DIAG_THREADS) {
     const real Qx = a.tab.qx[q], Qy = a.tab.qy[q];
-    s0 += a.tab.psi0[q] * (Qx * Qx + Qy * Qy);
+    q2[q] = Qx * Qx + Qy * Qy;
   }
+  __syncthreads();
+  real s0 = 0;   // sum_q psi0(q) |Q|^2 of the rest state
+  for (int q = 0; q < nq; ++q) s0 += a.tab.psi0[q] * q2[q];
   double acc[TFKT_NDIAG] = {};
   for (int y = blockIdx.x; y < a.ny; y += gridDim.x) {
     const int ym = y == 0 ? a.ny - 1 : y - 1, yp = y == a.ny - 1 ? 0 : y + 1;
@@ -689,11 +702,22 @@ __global__ void __launch_bounds__(DIAG_THREADS) diag_partial_kernel(KernelArgs<r
     for (int x = threadIdx.x; x < a.nx; x += DIAG_THREADS) {
       const size_t n = (size_t)y * a.pitch + x;
       real dpt = 0, sq = 0;
-      for (int q = 0; q < nq; ++q) {
-        const real m = a.M[(size_t)q * P + n];
-        const real Qx = a.tab.qx[q], Qy = a.tab.qy[q];
+      const real* mp = a.M + n;
+      int q = 0;
+      for (; q + 8 <= nq; q += 8) {
+        real m[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) m[k] = mp[(size_t)(q + k) * P];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          dpt += m[k];
+          sq += m[k] * q2[q + k];
+        }
+      }
+      for (; q < nq; ++q) {
+        const real m = mp[(size_t)q * P];
         dpt += m;
-        sq += m * (Qx * Qx + Qy * Qy);
+        sq += m * q2[q];
       }
       const real drho = a.M[(size_t)(nq + M_DRHO) * P + n];
       const real pt = a.psi_tot0 + dpt, rho = a.rho0 + drho;
@@ -820,7 +844,7 @@ cudaError_t launch_populations(const KernelArgs<real>& a, double* out, cudaStrea
 template <typename real>
 cudaError_t launch_diag(const KernelArgs<real>& a, double* partials, int nblocks, double* out,
                         cudaStream_t s) {
-  diag_partial_kernel<real><<<nblocks, DIAG_THREADS, 0, s>>>(a, partials);
+  diag_partial_kernel<real><<<nblocks, DIAG_THREADS, (size_t)a.nq * sizeof(real), s>>>(a, partials);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const double N = (double)a.nx * a.ny;
