@@ -58,6 +58,7 @@ CASES = [
     (32, 8, 8, 4.0, 5.0, 0.5, 0.2, 1, 0.0, 0, 9),        # one tile: its ring wraps onto itself
     (96, 16, 6, 3.0, 4.0, 1.0, 0.5, 2, 0.3, 1, 15),      # tau2 > tau1
     (64, 16, 4, 2.0, 3.0, 0.0, 1.0, 1, 0.0, 1, 10),      # Newtonian
+    (64, 16, 14, 7.0, 3.0, 0.5, 0.2, 1, 0.0, 1, 10),     # 156 Q-nodes: two-pass on a tile-multiple grid
     (32, 16, 2, 1.0, 5.0, 0.5, 0.2, 1, 0.0, 1, 9),       # every Q-move bounces
     # FENE springs (last entry b): disks at ~0.85 Q0 and R ~ 1.5-2.5 sigma_Q, spring
     # factor up to ~3 at the edge. (A disk of R = 6.6 sigma_Q with b = 60 is
@@ -71,7 +72,8 @@ CASES = [
     (64, 32, 6, 3.0, 5.0, 2.0, 0.5, 1, 0.03, 1, 12, 0.0, 1),   # a grid the fused path would take
     (33, 9, 4, 2.0, 3.0, 0.0, 1.0, 1, 0.05, 1, 10, 0.0, 1),    # Newtonian
 ]
-FUSED = [c for c in CASES if c[0] % 32 == 0 and c[1] % 8 == 0 and (len(c) < 13 or c[12] == 0)]
+FUSED = [c for c in CASES if c[0] % 32 == 0 and c[1] % 8 == 0 and (len(c) < 13 or c[12] == 0)
+         and c[2] * c[2] <= 127]   # the fused kernel holds at most 127 Q-nodes
 FENE = [c for c in CASES if len(c) > 11 and c[11] > 0]
 STRESS = [c for c in CASES if len(c) > 12 and c[12] == 1]
 
@@ -81,7 +83,7 @@ def _case(case):
     return tuple(case) + (0.0, 0)[len(case) - 11:] if len(case) < 13 else tuple(case)
 
 
-@pytest.mark.parametrize("case", [CASES[2], CASES[7], FENE[0], FENE[1], STRESS[1]])
+@pytest.mark.parametrize("case", [CASES[2], CASES[7], CASES[11], FENE[0], FENE[1], STRESS[1]])
 def test_path_dispatch(T, case):
     """Tile-multiple grids run the fused kernel plus its border fix-up; others the
     moments + step pair."""

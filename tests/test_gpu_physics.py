@@ -46,3 +46,53 @@ def test_growth_rate_matches_linear_theory(T, re):
     rate = np.polyfit(t[h:], la[h:], 1)[0]
     assert np.sign(rate) == np.sign(pred) == (1 if re > onset(alpha) else -1)
     assert rate == pytest.approx(pred, rel=0.05)
+
+
+def _uniform_seed(nx, ny, u0, amp=1e-3, modes=8, seed=1):
+    """u_y = sum_m sin(2 pi m x / nx + theta_m), uniform in y (divergence-free),
+    rms amp * u0: the long-wave eigenmodes of Kolmogorov flow are nearly uniform
+    in y (stream-function harmonic 0), so this seed feeds them directly."""
+    rng = np.random.default_rng(seed)
+    x = np.arange(nx)
+    uy = sum(np.sin(2 * np.pi * m * x / nx + rng.uniform(0, 2 * np.pi)) for m in range(1, modes + 1))
+    uy *= amp * u0 / np.sqrt(np.mean(uy ** 2))
+    p = np.zeros((2, ny, nx))
+    p[1] = uy[None, :]
+    return p
+
+
+@pytest.mark.parametrize("re", [1.2, 1.4, 1.6, 2.0, 3.0])
+def test_onset_sweep_at_scale_fp32(T, re):
+    """Newtonian onset at validation scale: 2048 x 512 r-nodes, FP32 storage,
+    20 000 steps, forcing wavelength 64 nodes (8 periods), so that the long-wave
+    modes alpha = m/32 (m = 1..8) fit the box. The amplitude of each mode (the
+    x-Fourier coefficient of the y-mean of u_y) must grow or decay at the linear
+    theory's rate sigma(alpha, Re) U0/l, fitted over steps 5 000-20 000. Away
+    from the onset the rate carries the lattice's O(dx^2) and O(Ma^2) errors
+    (64 nodes per wavelength, Ma = 0.087): 5% plus 1e-6 per step. Near the onset
+    (Re = 1.4, 1.6) the rate is a small difference of O(alpha^2) terms whose
+    absolute error shows in full: 20% plus 1.5e-6 per step (3e-4 U0/l). All
+    modes decay at Re = 1.2 and grow at Re = 1.6, which brackets Re_c."""
+    nx, ny, u0, lam, steps, every = 2048, 512, 0.05, 64, 20000, 500
+    l = lam / (2 * np.pi)
+    p = T.Params(nx, ny, 1, 1.0, re, 0.0, 1.0, u0, ny // lam, 0.0, 0.0, 1, T.FP32)
+    t, amp = [], []
+    with T.Solver(p, _uniform_seed(nx, ny, u0)) as s:
+        for k in range(steps // every + 1):
+            if k:
+                s.step(every)
+            uy = s.moments(["uy"])["uy"]
+            amp.append(np.abs(np.fft.rfft(uy.mean(axis=0))[1:9]))
+            t.append(k * every)
+    t, amp = np.array(t), np.array(amp)
+    h = len(t) // 4
+    near = re in (1.4, 1.6)
+    for m in range(1, 9):
+        meas = np.polyfit(t[h:], np.log(amp[h:, m - 1]), 1)[0]
+        pred = sigma(m * lam / nx, re).real * u0 / l
+        tol = (0.2 if near else 0.05) * abs(pred) + (1.5e-6 if near else 1e-6)
+        assert abs(meas - pred) <= tol, (re, m, meas, pred)
+        if re == 1.2:
+            assert meas < 0, (m, meas)
+        if re == 1.6:
+            assert meas > 0, (m, meas)
