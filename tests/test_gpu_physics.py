@@ -96,3 +96,31 @@ def test_onset_sweep_at_scale_fp32(T, re):
             assert meas < 0, (m, meas)
         if re == 1.6:
             assert meas > 0, (m, meas)
+
+
+def test_laminar_profile_at_scale_fp32(T, oracle_mod):
+    """Newtonian limit at validation scale: 1024^2 r-nodes, FP32, forcing
+    wavelength 64 nodes (k_p = 16), Re = 1 (below the onset), from rest; after
+    14 viscous times 1/(nu k^2) the flow is the steady laminar profile. It is an
+    x-independent lattice problem, so every node must equal the FP64 oracle's
+    steady state on a 4 x 64 strip with the same parameters, within 1e-5 U0 (FP32
+    deviations reach a steady state; their rounding does not accumulate); and that
+    lattice profile is the continuum a0/(nu k^2) sin(k y) up to the scheme's
+    O(k^2) error (1.34% at tau1 = 1.53, k = 2 pi/64; it converges at second order,
+    tests/test_oracle_physics.py)."""
+    nx, ny, lam, u0 = 1024, 1024, 64, 0.05
+    lat = oracle_mod.map_params(4, lam, 1, 1.0, 1.0, 0.0, 1.0, u0, 1)
+    steps = int(14 / (lat.nu * lat.kf ** 2))
+    o = oracle_mod.Oracle(lat)
+    o.init(None, 0)
+    o.step(steps)
+    ref = o.fields()["ux"][:, 0]
+    y = np.arange(lam)
+    cont = lat.a0 / (lat.nu * lat.kf ** 2) * np.sin(lat.kf * y)
+    assert np.abs(ref - cont).max() / np.abs(cont).max() < 0.015
+    p = T.Params(nx, ny, 1, 1.0, 1.0, 0.0, 1.0, u0, ny // lam, 0.0, 0.0, 0, T.FP32)
+    with T.Solver(p) as s:
+        s.step(steps)
+        g = s.moments(["ux", "uy"])
+    assert np.abs(g["ux"] - np.tile(ref, ny // lam)[:, None]).max() < 1e-5 * u0
+    assert np.abs(g["uy"]).max() < 1e-5 * u0
