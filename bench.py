@@ -539,6 +539,8 @@ def main():
                          "bytes_per_launch": per[top]["bytes_per_launch"],
                          "step_model_gbs": nodes * (2 * pb + 2 * nm * s) / (ms / args.steps / 1e3) / 1e9,
                          "kernels": per},
+            "updates": {"hyper_lattice_per_s": value * 1e9 * info["nq"],
+                        "populations_per_s": value * 1e9 * npl},
             "e2e": e2e,
             "gpu_launches": int(launches.sum()),
             "clocks": clocks,

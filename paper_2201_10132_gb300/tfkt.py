@@ -238,6 +238,7 @@ class Solver:
         if getattr(self, "_h", None) and self._h.value:
             _check(lib().tfkt_destroy(self._h), "tfkt_destroy")
             self._h = ctypes.c_void_p()
+        self._workspace = None   # a closed context no longer keeps the caller's buffer alive
 
     def __del__(self):
         try:

@@ -203,34 +203,49 @@ def test_fp16_storage_within_tolerance(T, oracle_mod, case):
     assert max(errs.values()) < 3e-3, errs
 
 
-def test_full_size_tiled_matches_oracle(T, oracle_mod):
+@pytest.mark.parametrize("size,storage,tol", [(4096, "FP32", 2e-5), (4096, "FP16", 3e-3),
+                                               (8192, "FP16", 3e-3)])
+def test_full_size_tiled_matches_oracle(T, oracle_mod, size, storage, tol):
     """The 4096^2, N_Q = 32 throughput workload in its benchmark launch configuration
-    (FP32), started from a perturbation that repeats every 64 nodes: with the
-    forcing period also 64 nodes, the solution is the 64^2 oracle run tiled 64 x 64
-    times, so every node of the full-size launch is checked."""
+    (FP32, and FP16 storage as in the precision sweep), and the 8192^2 capacity run
+    that fits one GPU only in FP16 storage (248.5 GB), started from a perturbation
+    that repeats every 64 nodes: with the forcing period also 64 nodes, the solution
+    is the 64^2 oracle run tiled, so every node of the full-size launch is checked
+    (FP16 storage within the tolerance of the small FP16 cases)."""
     import torch
-    from paper_2201_10132_gb300.inputs import KOLMOGOROV_4096 as W, perturbation
+    from paper_2201_10132_gb300.inputs import KOLMOGOROV_4096, KOLMOGOROV_8192, perturbation
+    W = KOLMOGOROV_4096 if size == 4096 else KOLMOGOROV_8192
     n0 = 64
     steps = 6
     small = perturbation(n0, n0, 11, 1e-2, W.u0)
     pert = np.tile(small, (1, W.ny // n0, W.nx // n0))
-    p = T.Params.from_workload(W, T.FP32)
+    p = T.Params.from_workload(W, getattr(T, storage))
+    torch.cuda.empty_cache()   # earlier tests' cached blocks: the 8192^2 workspace is 248.5 GB
     ws = torch.empty(T.required_bytes(p), dtype=torch.uint8, device="cuda")
     with T.Solver(p, pert, workspace=ws) as s:
         assert s.info["nq"] == 32
         s.step(steps)
-        g = s.moments(["ux", "uy", "rho_s", "cxy"])
+        g = s.moments(["ux", "uy", "rho_s", "cxx", "cyy", "cxy"])
+    del ws, pert
+    torch.cuda.empty_cache()
     o = _oracle_run(oracle_mod, n0, n0, W.q_side, W.q_radius, W.re, W.wi, W.beta, 1, 0.0, small,
                     0, steps)
     f = o.fields()
     uscale = max(np.abs(f["ux"]).max(), np.abs(f["uy"]).max())
-    for k in ("ux", "uy", "rho_s", "cxy"):
+    # FP16 rounds each stored polymer value relative to its own size, which is
+    # set by the equilibrium conformation: its C_xy error is measured against the
+    # conformation scale (C_xy itself is still small a few steps from rest)
+    cscale = max(np.abs(f["cxx"]).max(), np.abs(f["cyy"]).max())
+    for k in ("ux", "uy", "rho_s", "cxx", "cyy", "cxy"):
         ref = np.tile(f[k], (W.ny // n0, W.nx // n0))
-        scale = uscale if k in ("ux", "uy") else np.abs(ref).max()
+        if k in ("ux", "uy"):
+            scale = uscale
+        elif k == "cxy" and storage == "FP16":
+            scale = cscale
+        else:
+            scale = np.abs(ref).max()
         err = np.abs(g[k] - ref).max() / scale
-        assert err < 2e-5, (k, err)
-    del ws
-    torch.cuda.empty_cache()
+        assert err < tol, (k, err)
 
 
 def test_caller_workspace_and_stream(T, oracle_mod):
