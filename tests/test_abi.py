@@ -73,3 +73,17 @@ def test_fene_disk_inside_q0_is_accepted(T, oracle_mod):
     T.required_bytes(T.Params(64, 64, 8, 0.999 * q0, 5.0, 0.5, 0.2, fene_b=25.0))
     with pytest.raises(T.TfktError):
         T.required_bytes(T.Params(64, 64, 8, 1.001 * q0, 5.0, 0.5, 0.2, fene_b=25.0))
+
+
+def test_fp16_population_buffer_layout(T):
+    """FP16 storage keeps 9 + 25 nq plane slots of half and the nine solvent planes
+    as floats after them (include/tfkt.h): against FP32 storage each of the two
+    population buffers is 2 bytes per slot smaller and 9 x 4 bytes per node larger;
+    everything else in the workspace (float moment planes, tables) is the same."""
+    base = dict(nx=1024, ny=1024, q_side=6, q_radius=3.0, re=10.0, wi=1.0, beta=0.2, u0=0.05,
+                k_periods=16)
+    p32 = T.required_bytes(T.Params(**base, precision=T.FP32))
+    p16 = T.required_bytes(T.Params(**base, precision=T.FP16))
+    plane = 1024 * 1024            # pitch 1024: planes are multiples of 256 bytes
+    npl = 9 + 25 * 32
+    assert p32 - p16 == 2 * (npl * plane * 2 - 9 * plane * 4)
