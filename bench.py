@@ -131,14 +131,33 @@ def aggregate_glups(world: int, nodes: int, steps: int, seconds: float) -> float
     return world * nodes * steps / seconds / 1e9
 
 
-def oracle_sample(W, target_s: float = 12.0):
+def host_cpu() -> str:
+    """The host CPU's model name (x86 'model name'; Arm implementer and part numbers)."""
+    try:
+        info = open("/proc/cpuinfo").read()
+    except OSError:
+        return "unknown"
+    for key in ("model name", "Model"):
+        for line in info.splitlines():
+            if line.startswith(key):
+                return line.split(":", 1)[1].strip()
+    fields = {}
+    for line in info.splitlines():
+        if ":" in line:
+            k, v = (t.strip() for t in line.split(":", 1))
+            fields.setdefault(k, v)
+    return f"implementer {fields.get('CPU implementer', '?')} part {fields.get('CPU part', '?')}"
+
+
+def oracle_sample(W, target_s: float = 12.0, threads: int | None = None):
     """Time the CPU oracle on a bounded sample of the workload: 256 x 256 r-nodes
-    with the same lattice parameters (forcing wavelength 64 nodes), N_Q = 32."""
+    with the same lattice parameters (forcing wavelength 64 nodes), N_Q = 32, on
+    all host cores (or `threads`)."""
     from oracle import oracle as O
     from paper_2201_10132_gb300.inputs import perturbation
     n = 256
     kp = W.k_periods * n // W.ny
-    cores = O.set_threads(os.cpu_count() or 1)
+    cores = O.set_threads(threads or os.cpu_count() or 1)
     lat = O.map_params(n, n, W.q_side, W.q_radius, W.re, W.wi, W.beta, W.u0, kp, W.tau2)
     o = O.Oracle(lat)
     o.init(perturbation(n, n, W.seed, W.amp, W.u0), W.ic_mode)
@@ -172,7 +191,8 @@ def run_reference(args, W):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": W.name, "sample": per_step[-1]["sample"]},
             "cpu_baseline": {"value": value, "unit": "GLUPS", "cores": per_step[-1]["cores"],
-                             "kind": "oracle", "sample": per_step[-1]["sample"]},
+                             "kind": "oracle", "sample": per_step[-1]["sample"],
+                             "host": {"cpu": host_cpu(), "nproc": os.cpu_count()}},
             "e2e": {"value": value, "unit": "GLUPS", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -431,6 +451,9 @@ def main():
     cpu_base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu_base = oracle_sample(W)
+        one = oracle_sample(W, target_s=4.0, threads=1)
+        cpu_base["single_thread"] = {"value": one["value"], "sample": one["sample"]}
+        cpu_base["host"] = {"cpu": host_cpu(), "nproc": os.cpu_count()}
 
     import numpy as np
     import torch
