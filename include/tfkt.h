@@ -164,8 +164,15 @@ tfkt_status tfkt_required_bytes(const tfkt_params* p, size_t* bytes);
 tfkt_status tfkt_create(const tfkt_params* p, const double* perturb, void* dev_workspace,
                         size_t workspace_bytes, void* stream, tfkt_ctx** out);
 
-/* Advance n >= 0 time steps (stream, moments, collide). Asynchronous on the
-   context stream. */
+/* Advance n >= 0 time steps. One step is the scheme of Sec. VI: pull-stream
+   both lattices (Sec. VI-A, VI-B, bounce-back at the Q-disk, Sec. VI-D), take
+   the moments, form the mixture velocity and the imposed velocities, convert g
+   to f (Sec. VI-C), collide with the two-relaxation update and the body force
+   of Sec. VII, and write the post-collision populations to the other buffer.
+   Asynchronous on the context stream. Errors: TFKT_EINVAL if n < 0 (nothing
+   launched); TFKT_ESTATE on a poisoned context; TFKT_ECUDA if a launch fails
+   (the context is then poisoned). A NaN in the state is not an error here;
+   tfkt_diagnostics reports it. */
 tfkt_status tfkt_step(tfkt_ctx* ctx, int64_t n);
 
 /* Same as tfkt_step, with CUDA events recorded on the context stream around
@@ -174,14 +181,21 @@ tfkt_status tfkt_step(tfkt_ctx* ctx, int64_t n);
    the launch counts to launches[TFKT_NKERNELS] (host, may be NULL). */
 tfkt_status tfkt_step_profiled(tfkt_ctx* ctx, int64_t n, double* kernel_ms, int64_t* launches);
 
-/* Macroscopic fields of the current state (see TFKT_F_*), as doubles.
-   dst: device pointer if dst_is_device, else host pointer; bytes is its size
+/* Macroscopic fields of the current state (see TFKT_F_*: the moments of
+   Sec. VI-A and VI-B, the mixture velocity of f of Sec. VI-C, the
+   conformation and Q_rms of Sec. VII, the vorticity), as doubles, layout
+   [field][ny][nx] in increasing bit order of field_mask. dst: device pointer
+   if dst_is_device, else host pointer, owned by the caller; bytes is its size
    and must hold popcount(field_mask) * ny * nx doubles. Synchronises the
-   stream when dst is host memory. */
+   stream when dst is host memory. Errors: TFKT_EINVAL for a NULL dst, an
+   empty or out-of-range mask, or dst too small; TFKT_ESTATE / TFKT_ECUDA as
+   for tfkt_step. */
 tfkt_status tfkt_moments(tfkt_ctx* ctx, uint32_t field_mask, double* dst, size_t bytes,
                          int dst_is_device);
 
-/* psi(x, q) of the current state as doubles, layout [ny][nx][nq]. */
+/* psi(x, q) = sum_i g_i(x, q) of the current state (Sec. VI-B, the
+   conformation density on the Q-grid) as doubles, layout [ny][nx][nq]; dst
+   and bytes as for tfkt_moments (nq * ny * nx doubles), same errors. */
 tfkt_status tfkt_psi(tfkt_ctx* ctx, double* dst, size_t bytes, int dst_is_device);
 
 /* Global diagnostics into host out[TFKT_NDIAG]; synchronises. TFKT_ENAN if
@@ -190,9 +204,14 @@ tfkt_status tfkt_psi(tfkt_ctx* ctx, double* dst, size_t bytes, int dst_is_device
    is neither changed nor reset). */
 tfkt_status tfkt_diagnostics(tfkt_ctx* ctx, double* out);
 
-/* The stored (post-collision, not yet streamed) populations g' as doubles in
-   host memory, layout [plane][ny][nx]: planes 0..8 solvent (tfkt_lattice
-   order), then plane 9 + 25 q + i for the polymer. Synchronises. */
+/* The stored (post-collision, not yet streamed) populations g' of Sec. VI-C
+   as doubles in host memory owned by the caller, layout [plane][ny][nx]:
+   planes 0..8 solvent (tfkt_lattice order), then plane 9 + 25 q + i for the
+   polymer; the storage shift (w_i for the solvent, w_i psi0(q) for the
+   polymer) is added back. bytes must hold (9 + 25 nq) * ny * nx doubles.
+   Allocates a temporary device buffer of that size. Synchronises. Errors:
+   TFKT_EINVAL for a NULL or too small dst; TFKT_ESTATE / TFKT_ECUDA as for
+   tfkt_step. */
 tfkt_status tfkt_populations(tfkt_ctx* ctx, double* host_dst, size_t bytes);
 
 /* Macroscopic fields without any device allocation. The paper has no
@@ -293,7 +312,9 @@ tfkt_status tfkt_batch_create(const tfkt_params* runs, int32_t n, const double* 
                               void* dev_workspace, size_t workspace_bytes, void* stream,
                               tfkt_batch** out);
 
-/* Advance every run by n >= 0 steps (asynchronous on the batch stream). */
+/* Advance every run by n >= 0 steps of the scheme of tfkt_step
+   (asynchronous on the batch stream). Errors: TFKT_EINVAL for a NULL batch or
+   n < 0; TFKT_ECUDA if a launch or a graph launch fails. */
 tfkt_status tfkt_batch_step(tfkt_batch* b, int64_t n);
 
 /* The context of run i (0 <= i < n), for tfkt_moments, tfkt_diagnostics,
@@ -311,8 +332,12 @@ tfkt_status tfkt_batch_tile_height(const tfkt_batch* b, int32_t* ty, float* ms);
    step at heights 4, 8, 16 and of the per-run plan (NaN where not timed). */
 tfkt_status tfkt_batch_plan(const tfkt_batch* b, int32_t* per_run, int32_t* ty, float* ms);
 
+/* Release the batch, its runs, streams and graph (and the workspace if the
+   library allocated it). Synchronises first; NULL is accepted. */
 tfkt_status tfkt_batch_destroy(tfkt_batch* b);
 
+/* Static one-line description of a status code ("ok", "invalid argument",
+   ...; "unknown status" for other values); never NULL. */
 const char* tfkt_status_string(tfkt_status s);
 /* Text of the last error seen by this thread ("" if none). */
 const char* tfkt_last_error(void);
