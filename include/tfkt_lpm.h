@@ -53,8 +53,12 @@ extern "C" {
 typedef struct tfkt_mlp tfkt_mlp;
 
 /* A network on the current device from a host parameter vector (copied).
-   stream: the stream its kernels run on (NULL: the legacy default stream). */
+   stream: the stream its kernels run on (NULL: the legacy default stream).
+   Errors (all network calls): TFKT_EINVAL for NULL arguments, n out of range,
+   non-positive scales sx, st or bad Adam hyper-parameters (nothing launched);
+   TFKT_ENOMEM if an allocation fails; TFKT_ECUDA if a CUDA call fails. */
 tfkt_status tfkt_mlp_create(const float* params, void* stream, tfkt_mlp** out);
+/* Free the network's device memory; NULL is accepted. */
 tfkt_status tfkt_mlp_destroy(tfkt_mlp* net);
 /* Copy the FP32 master parameters to / from a host vector of TFKT_MLP_NPARAM. */
 tfkt_status tfkt_mlp_get(tfkt_mlp* net, float* params);

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -406,7 +407,8 @@ extern "C" {
 tfkt_status tfkt_mlp_create(const float* params, void* stream, tfkt_mlp** out) {
   if (!params || !out) return fail(TFKT_EINVAL, "NULL argument");
   *out = nullptr;
-  tfkt_mlp* net = new tfkt_mlp;
+  tfkt_mlp* net = new (std::nothrow) tfkt_mlp();   // nothing may throw across the C interface
+  if (!net) return fail(TFKT_ENOMEM, "host allocation failed");
   net->stream = (cudaStream_t)stream;
   auto bad = [&](cudaError_t e, const char* what) {
     tfkt_mlp_destroy(net);
@@ -418,8 +420,11 @@ tfkt_status tfkt_mlp_create(const float* params, void* stream, tfkt_mlp** out) {
       (e = cudaMalloc(&net->m, TFKT_MLP_NWEIGHTS * sizeof(float))) != cudaSuccess ||
       (e = cudaMalloc(&net->v, TFKT_MLP_NWEIGHTS * sizeof(float))) != cudaSuccess ||
       (e = cudaMalloc(&net->grad, TFKT_MLP_NWEIGHTS * sizeof(float))) != cudaSuccess ||
-      (e = cudaMalloc(&net->loss_dev, sizeof(double))) != cudaSuccess)
-    return bad(e, "cudaMalloc");
+      (e = cudaMalloc(&net->loss_dev, sizeof(double))) != cudaSuccess) {
+    tfkt_mlp_destroy(net);
+    cudaGetLastError();   // clear the allocation error
+    return fail(TFKT_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
   if ((e = cudaMemsetAsync(net->m, 0, TFKT_MLP_NWEIGHTS * sizeof(float), net->stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(net->v, 0, TFKT_MLP_NWEIGHTS * sizeof(float), net->stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(net->grad, 0, TFKT_MLP_NWEIGHTS * sizeof(float), net->stream)) != cudaSuccess)
