@@ -97,3 +97,31 @@ def test_record_nonfinite_is_null_and_json_strict():
     assert json.loads(text) == {"step": 7, "status": "ok", "a": None, "umax": None, "b": 1.5,
                                 "mach": None, "wall_ms": 2.0}
     assert np.isclose(monitor.CS, 1 / np.sqrt(3))
+
+
+def test_defaults_come_from_the_binding():
+    """Without explicit names the log uses the library's diagnostics (including
+    the maxima umax and qrms_max) and its TFKT_ENAN status."""
+    from paper_2201_10132_gb300 import tfkt
+
+    class Fake:
+        def __init__(self):
+            self.t = 0
+
+        def step(self, n):
+            self.t += n
+
+        def diagnostics_into(self, out):
+            out[:] = np.arange(len(out), dtype=float) + 0.5
+            out[tfkt.DIAGS.index("umax")] = 0.01
+            if self.t >= 4:
+                e = RuntimeError("non-finite diagnostic ke at step 4")
+                e.status = tfkt.ENAN
+                raise e
+
+    buf = io.StringIO()
+    last = monitor.run_logged(Fake(), 10, 2, buf)
+    recs = [json.loads(line) for line in buf.getvalue().splitlines()]
+    assert set(tfkt.DIAGS) <= set(recs[0]) and "umax" in tfkt.DIAGS and "qrms_max" in tfkt.DIAGS
+    assert [r["step"] for r in recs] == [0, 2, 4] and last["status"] == "nan"
+    assert recs[0]["mach"] == pytest.approx(0.01 * math.sqrt(3.0))
