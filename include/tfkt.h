@@ -228,25 +228,34 @@ tfkt_status tfkt_populations(tfkt_ctx* ctx, double* host_dst, size_t bytes);
            layout. A context created on workspace W keeps its state, after
            n steps, at W + (n mod 2) * B with B = the population bytes
            rounded up to 256, but never less than TFKT_NFIELDS * ny * nx * 8
-           bytes. The population bytes are (9 + 25 nq) * ny * pitch * e (nq,
+           bytes. After a learned block (tfkt_lpm_run) that buffer lacks the
+           block's polymer increment, which waits for the context's next
+           step; tfkt_populations and tfkt_save add it to the buffer. Until
+           then this call gives the fields without the increment, where
+           tfkt_moments gives them with it. The population bytes are (9 + 25 nq) * ny * pitch * e (nq,
            pitch from tfkt_get_info; e = 8 for TFKT_FP64, 4 for TFKT_FP32,
            2 for TFKT_FP16): planes 0..8 the solvent, 9 + 25 q + i the
            polymer; under TFKT_FP16 planes 0..8 are unused and the nine
            solvent planes follow as floats, 9 * ny * pitch * 4 bytes more.
    dst:    device pointer, popcount(field_mask) * ny * nx doubles; bytes is
            its size.
-   stream: cudaStream_t or NULL. The lattice tables are copied from host
-           memory and the stream is synchronised once before the kernels are
-           queued; the kernels then run asynchronously on the stream.
+   stream: cudaStream_t or NULL. The kernels run asynchronously on the
+           stream. The lattice tables are kept in the array with the
+           parameters they belong to: the first call on a device, and a call
+           whose parameters differ from those of the last upload, copies them
+           from host memory and synchronises the stream before queuing the
+           kernels; a call with the same parameters as the last upload only
+           queues the kernels.
    Errors: TFKT_EINVAL for invalid parameters, pointers or mask, and when the
            grid needs more scratch than TFKT_NOALLOC_SCRATCH_BYTES (the
            message gives both sizes); TFKT_ECUDA if a CUDA call fails.
    The first call on a device looks up the address of the static array on
    that device (with the device current); make that first call before any
    stream capture. All calls share the one array, which keeps what the last
-   call left in it; every value a call reads from it is written by the same
-   call first, so nothing needs clearing. Calls whose work overlaps on the
-   GPU (other streams, other threads) race on the array. */
+   call left in it; every moment and velocity value a call reads from it is
+   written by the same call first, and the tables are re-uploaded whenever
+   the parameters change, so nothing needs clearing. Calls whose work
+   overlaps on the GPU (other streams, other threads) race on the array. */
 #define TFKT_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
 tfkt_status tfkt_moments_noalloc(const tfkt_params* p, const void* pops, uint32_t field_mask,
                                  double* dst, size_t bytes, void* stream);

@@ -23,8 +23,20 @@ namespace {
 constexpr int kMaxDevices = 128;
 std::mutex g_scratch_mu;
 void* g_scratch_addr[kMaxDevices] = {};
+// Parameters whose lattice tables the array of each device holds (valid once
+// an upload has completed); a call with the same parameters reuses them.
+tfkt_params g_tables_of[kMaxDevices];
+bool g_tables_valid[kMaxDevices] = {};
 
-tfkt_status scratch_address(void** out) {
+bool same_params(const tfkt_params& a, const tfkt_params& b) {
+  return a.nx == b.nx && a.ny == b.ny && a.q_side == b.q_side && a.q_radius == b.q_radius &&
+         a.re == b.re && a.wi == b.wi && a.beta == b.beta && a.u0 == b.u0 &&
+         a.k_periods == b.k_periods && a.tau2 == b.tau2 && a.ell == b.ell &&
+         a.ic_mode == b.ic_mode && a.precision == b.precision && a.fene_b == b.fene_b &&
+         a.qe_model == b.qe_model;
+}
+
+tfkt_status scratch_address(void** out, int* device) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(TFKT_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
@@ -38,12 +50,13 @@ tfkt_status scratch_address(void** out) {
     g_scratch_addr[dev] = p;
   }
   *out = g_scratch_addr[dev];
+  *device = dev;
   return TFKT_OK;
 }
 
 template <typename real, typename S>
-tfkt_status moments_noalloc(const Lattice& L, const void* pops, uint32_t mask, double* dst,
-                            cudaStream_t stream) {
+tfkt_status moments_noalloc(const tfkt_params& p, const Lattice& L, const void* pops,
+                            uint32_t mask, double* dst, cudaStream_t stream) {
   // scratch layout: M planes, U planes, then the tables
   const size_t sz = sizeof(real), A = 256, nq = L.nq;
   size_t o = 0;
@@ -64,29 +77,41 @@ tfkt_status moments_noalloc(const Lattice& L, const void* pops, uint32_t mask, d
                                  " bytes of scratch, the static scratch holds " +
                                  std::to_string((size_t)TFKT_NOALLOC_SCRATCH_BYTES));
   void* base = nullptr;
-  tfkt_status s = scratch_address(&base);
+  int dev = 0;
+  tfkt_status s = scratch_address(&base, &dev);
   if (s != TFKT_OK) return s;
   char* b = (char*)base;
 
-  // lattice tables into the scratch (each call rewrites all of them)
-  const HostTables t = build_tables(L);
-  const std::vector<double>* src[NT] = {&t.qx,    &t.qy,    &t.fx,   &t.fy,  &t.psi0,
-                                        nullptr, &t.delta, &t.arow, &t.urow};
-  std::vector<real> conv[NT];
-  for (int k = 0; k < NT; ++k) {
-    cudaError_t e;
-    if (k == KPULL) {
-      e = cudaMemcpyAsync(b + off_t[k], t.pull.data(), tsz[k], cudaMemcpyHostToDevice, stream);
-    } else {
-      conv[k].assign(src[k]->begin(), src[k]->end());
-      e = cudaMemcpyAsync(b + off_t[k], conv[k].data(), tsz[k], cudaMemcpyHostToDevice, stream);
+  // Lattice tables: uploaded when the array does not hold those of these
+  // parameters yet (the first call on the device, or other parameters than the
+  // last upload). The host copies are pageable, so the stream is synchronised
+  // before they go out of scope; a call that finds its tables in place only
+  // queues the kernels.
+  cudaError_t e = cudaSuccess;
+  {
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_tables_valid[dev] || !same_params(g_tables_of[dev], p)) {
+      g_tables_valid[dev] = false;
+      const HostTables t = build_tables(L);
+      const std::vector<double>* src[NT] = {&t.qx,    &t.qy,    &t.fx,   &t.fy,  &t.psi0,
+                                            nullptr, &t.delta, &t.arow, &t.urow};
+      std::vector<real> conv[NT];
+      for (int k = 0; k < NT; ++k) {
+        if (k == KPULL) {
+          e = cudaMemcpyAsync(b + off_t[k], t.pull.data(), tsz[k], cudaMemcpyHostToDevice, stream);
+        } else {
+          conv[k].assign(src[k]->begin(), src[k]->end());
+          e = cudaMemcpyAsync(b + off_t[k], conv[k].data(), tsz[k], cudaMemcpyHostToDevice, stream);
+        }
+        if (e != cudaSuccess)
+          return fail(TFKT_ECUDA, std::string("table upload: ") + cudaGetErrorString(e));
+      }
+      e = cudaStreamSynchronize(stream);
+      if (e != cudaSuccess) return fail(TFKT_ECUDA, std::string("sync: ") + cudaGetErrorString(e));
+      g_tables_of[dev] = p;
+      g_tables_valid[dev] = true;
     }
-    if (e != cudaSuccess)
-      return fail(TFKT_ECUDA, std::string("table upload: ") + cudaGetErrorString(e));
   }
-  // host staging of pageable copies must outlive them
-  cudaError_t e = cudaStreamSynchronize(stream);
-  if (e != cudaSuccess) return fail(TFKT_ECUDA, std::string("sync: ") + cudaGetErrorString(e));
 
   KernelArgs<real> a{};
   a.src = pops;
@@ -118,9 +143,10 @@ tfkt_status moments_noalloc(const Lattice& L, const void* pops, uint32_t mask, d
   a.tab.delta = (const real*)(b + off_t[6]);
   a.tab.arow = (const real*)(b + off_t[7]);
   a.tab.urow = (const real*)(b + off_t[8]);
-  // every scratch value read below is written first by these kernels: the
-  // moments kernel writes all M planes of every node, the velocity kernel both
-  // U planes of every node, so nothing needs clearing between calls
+  // every plane read below is written first by these kernels: the moments
+  // kernel writes all M planes of every node, the velocity kernel both U
+  // planes of every node, so nothing needs clearing between calls (the tables
+  // are those of these parameters, checked above)
   if ((e = launch_moments<real, S>(a, stream)) != cudaSuccess ||
       (e = launch_velocity<real>(a, stream)) != cudaSuccess ||
       (e = launch_fields<real>(a, mask, dst, stream)) != cudaSuccess)
@@ -143,8 +169,8 @@ extern "C" tfkt_status tfkt_moments_noalloc(const tfkt_params* p, const void* po
   const size_t need = (size_t)__builtin_popcount(field_mask) * L.nx * L.ny * sizeof(double);
   if (bytes < need) return fail(TFKT_EINVAL, "dst too small");
   if (L.precision == TFKT_FP64)
-    return moments_noalloc<double, double>(L, pops, field_mask, dst, (cudaStream_t)stream);
+    return moments_noalloc<double, double>(*p, L, pops, field_mask, dst, (cudaStream_t)stream);
   if (L.precision == TFKT_FP32)
-    return moments_noalloc<float, float>(L, pops, field_mask, dst, (cudaStream_t)stream);
-  return moments_noalloc<float, __half>(L, pops, field_mask, dst, (cudaStream_t)stream);
+    return moments_noalloc<float, float>(*p, L, pops, field_mask, dst, (cudaStream_t)stream);
+  return moments_noalloc<float, __half>(*p, L, pops, field_mask, dst, (cudaStream_t)stream);
 }

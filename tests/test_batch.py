@@ -162,3 +162,59 @@ def test_batch_forced_height_must_fit(T, monkeypatch):
     monkeypatch.setenv("TFKT_BATCH_TILE_HEIGHT", "16")
     with pytest.raises(T.TfktError):
         T.Batch([_params(T, RUNS[2])], None)         # ny = 24
+
+
+# Runs of different grid sizes, Re, Wi and beta, one with tau2 > tau1; every ny
+# is a multiple of 16 so that each tile height can take every run.
+ORACLE_RUNS = [
+    # nx, ny, S, R, re, wi, beta, kp, tau2, ic, seed
+    (64, 32, 6, 3.0, 5.0, 0.5, 0.2, 1, 0.0, 1, 3),
+    (32, 16, 4, 2.0, 3.0, 1.0, 0.5, 1, 0.0, 0, 4),
+    (96, 16, 6, 3.0, 8.0, 0.3, 0.1, 1, 0.0, 1, 5),
+    (64, 48, 6, 3.0, 4.0, 1.0, 0.5, 1, 0.3, 1, 6),
+]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("plan", ["4", "8", "16", "per_run"])
+def test_batch_matches_oracle(T, oracle_mod, plan, monkeypatch):
+    """Every run of a heterogeneous batch, under each plan, against the FP64 oracle
+    at the FP32 parity tolerance (fields and global diagnostics)."""
+    from paper_2201_10132_gb300.inputs import perturbation
+    monkeypatch.delenv("TFKT_BATCH_TILE_HEIGHT", raising=False)
+    monkeypatch.delenv("TFKT_BATCH_PER_RUN", raising=False)
+    if plan == "per_run":
+        monkeypatch.setenv("TFKT_BATCH_PER_RUN", "1")
+    else:
+        monkeypatch.setenv("TFKT_BATCH_TILE_HEIGHT", plan)
+    steps = 9
+    params, perts = [], []
+    for nx, ny, S, R, re, wi, beta, kp, tau2, ic, seed in ORACLE_RUNS:
+        params.append(T.Params(nx, ny, S, R, re, wi, beta, 0.05, kp, tau2, 0.0, ic, T.FP32))
+        perts.append(perturbation(nx, ny, seed, 0.05, 0.05))
+    with T.Batch(params, perts) as b:
+        pl = b.plan()
+        assert pl["per_run"] if plan == "per_run" else pl["tile_height"] == int(plan)
+        b.step(steps)
+        got = [b.run(i).moments() for i in range(len(params))]
+        diag = [b.run(i).diagnostics() for i in range(len(params))]
+    for i, (r, pert) in enumerate(zip(ORACLE_RUNS, perts)):
+        nx, ny, S, R, re, wi, beta, kp, tau2, ic, _ = r
+        lat = oracle_mod.map_params(nx, ny, S, R, re, wi, beta, 0.05, kp, tau2)
+        o = oracle_mod.Oracle(lat)
+        o.init(pert, ic)
+        o.step(steps)
+        f = o.fields()
+        _close(got[i], {k: f[k] for k in got[i]})
+        od = o.diagnostics()
+        uscale = max(np.abs(f["ux"]).max(), np.abs(f["uy"]).max())
+        du = 2e-5 * uscale
+        rho = f["rho_s"] + f["psi_tot"]
+        tol = {"mass_s": 2e-5 * od["mass_s"], "mass_p": 2e-5 * max(od["mass_p"], 1e-30),
+               "px": 2 * du * rho.sum(), "py": 2 * du * rho.sum(),
+               "ke": 2 * du * (rho * (np.abs(f["ux"]) + np.abs(f["uy"]))).sum() + 1e-30,
+               "enstrophy": 4 * du * np.abs(f["vort"]).sum() + 1e-30,
+               "qrms_mean": 2e-5 * max(od["qrms_mean"], 1e-30),
+               "ey2": 2 * du * np.abs(f["uy"]).sum() + 1e-30}
+        for k, t in tol.items():
+            assert abs(diag[i][k] - od[k]) <= t, (plan, i, k, diag[i][k], od[k], t)
