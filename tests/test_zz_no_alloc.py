@@ -44,6 +44,7 @@ def _compare(got, ref, names, tol, what):
 
 
 def _noalloc(tfkt, p, ptr, mask, shape):
+    """The fields of mask, in increasing bit order, from the population buffer at ptr."""
     import torch
     got = torch.full(shape, float("nan"), dtype=torch.float64, device="cuda")
     tfkt.moments_noalloc(p, ptr, mask, got.data_ptr(), got.numel() * 8)
@@ -115,7 +116,7 @@ def test_noalloc_after_learned_block():
     nx, ny = 64, 32
     p = tfkt.Params(nx, ny, 6, 3.0, 10.0, 1.0, 0.2, 0.05, 1, ic_mode=1, precision=tfkt.FP32)
     ws = torch.empty(tfkt.required_bytes(p), dtype=torch.uint8, device="cuda")
-    names = ["ux", "uy", "cxx", "cxy", "cyy", "psi_tot"]
+    names = ["psi_tot", "ux", "uy", "cxx", "cxy", "cyy"]    # the output's order: bit order
     mask = tfkt.field_mask(names)
     vec, _ = train_lpm.load()
     net = tfkt.Mlp(vec)
