@@ -26,24 +26,42 @@ sys.path.insert(0, ROOT)
 L2_BYTES = 129e6
 
 
-def _measured_traffic(nodes: int, storage: str = "fp32"):
-    """DRAM bytes of one fused-kernel launch, scaled by r-nodes from the committed ncu
-    summary of the small case in the same storage; None once the kernel source no
-    longer matches it."""
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per r-node of one
+# fused-kernel launch, from the ncu capture of the 512^2 case of the same lattice
+# parameters (profiles/step_fused_kernel_kolmogorov_512x512_nq32*.md; traffic grows
+# in proportion to the node count), with the sha256 prefix of the kernel sources
+# the capture was taken on.
+FUSED_TRAFFIC = {
+    "fp32": (6661.0, "b8d255c0025f6cf5"),
+    "fp16": (3479.0, "b8d255c0025f6cf5"),
+}
+KERNEL_SOURCES = ("paper_2201_10132_gb300/csrc/tfkt_fused.cu",
+                  "paper_2201_10132_gb300/csrc/tfkt_fused.cuh")
+
+
+def kernel_source_sha() -> str:
+    """sha256 prefix (16 hex digits) of the fused kernel's sources, in order."""
     import hashlib
-    import re
-    name = "step_fused_kernel_kolmogorov_512x512_nq32" + ("" if storage == "fp32" else "_" + storage)
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def fused_traffic(nodes: int, storage: str = "fp32"):
+    """DRAM bytes of one fused-kernel launch over `nodes` r-nodes, scaled from the
+    512^2 capture; None for a storage without a capture, or once the kernel sources
+    differ from those the counters were taken on."""
+    if storage not in FUSED_TRAFFIC:
+        return None
+    per_node, sha = FUSED_TRAFFIC[storage]
     try:
-        text = open(os.path.join(ROOT, "profiles", name + ".md")).read()
-        src = open(os.path.join(ROOT, "paper_2201_10132_gb300", "csrc", "tfkt_fused.cu"),
-                   "rb").read()
+        if kernel_source_sha() != sha:
+            return None
     except OSError:
         return None
-    h = re.search(r"sha256 prefix `([0-9a-f]+)`", text)
-    b = re.search(r"per r-node: .*?\*\*(\d+) B\*\*", text, re.S)
-    if not h or not b or hashlib.sha256(src).hexdigest()[:len(h.group(1))] != h.group(1):
-        return None
-    return float(b.group(1)) * nodes
+    return per_node * nodes
 
 
 def _peaks():
@@ -391,6 +409,199 @@ def ensemble_throughput(n_runs: int, steps: int, warmup: int):
             "workspace_gb": ws.numel() / 1e9, "nq": 9}
 
 
+SUB_FIELDS = ["ux", "uy", "cxx", "cxy", "cyy"]
+
+
+def _hbm_roofline(kernel: str, bytes_per_launch: float, ms: float, traffic=None, **extra):
+    peak, kind = _peaks()
+    ach = bytes_per_launch / (ms / 1e3) / 1e9
+    r = {"bound": "hbm", "kernel": kernel, "achieved": ach, "peak": peak, "unit": "GB/s",
+         "frac": ach / peak, "peak_kind": kind, "bytes_per_launch": bytes_per_launch,
+         "traffic": traffic}
+    r.update(extra)
+    return r
+
+
+def fp16_sub(W, steps: int, warmup: int, fp32_ms_per_step: float, fp32_fused_ms: float,
+             ref_fields: dict):
+    """The throughput workload with FP16 polymer storage (FP32 solvent, FP32
+    arithmetic) from the identical seeded state: time per step, the fused kernel
+    against the HBM roofline at its own algorithmic bytes, the speedup over the FP32
+    line just measured, and the largest field errors against that FP32 run after
+    the same number of steps (velocity against the velocity scale, conformation
+    against the largest diagonal conformation)."""
+    import numpy as np
+    import torch
+    from paper_2201_10132_gb300 import tfkt
+    from paper_2201_10132_gb300.inputs import perturbation
+    p = tfkt.Params.from_workload(W, tfkt.FP16)
+    ws = torch.empty(tfkt.required_bytes(p), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.Stream()
+    s = tfkt.Solver(p, perturbation(W.nx, W.ny, W.seed, W.amp, W.u0), workspace=ws,
+                    stream=stream.cuda_stream)
+    info = s.info
+    s.step(warmup)
+    s.sync()
+    kms = np.zeros(len(tfkt.KERNELS))
+    n = np.zeros(len(tfkt.KERNELS), np.int64)
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step_profiled(steps, kms, n)
+    e1.record(stream)
+    e1.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / steps
+    f = s.moments(SUB_FIELDS)
+    s.close()
+    del s, ws
+    torch.cuda.empty_cache()
+    nodes = W.nx * W.ny
+    k = tfkt.KERNELS.index("fused")
+    fused_ms = kms[k] / max(n[k], 1)
+    pb = 9 * 4 + 25 * info["nq"] * 2
+    nm = info["nq"] + 6
+    us = max(np.abs(ref_fields["ux"]).max(), np.abs(ref_fields["uy"]).max())
+    cs = max(np.abs(ref_fields["cxx"]).max(), np.abs(ref_fields["cyy"]).max())
+    err = {name: float(np.abs(f[name] - ref_fields[name]).max() /
+                       (us if name in ("ux", "uy") else cs)) for name in SUB_FIELDS}
+    return {"storage": "fp16 polymer deviations (scaled), fp32 solvent deviations; fp32 arithmetic",
+            "ms_per_step": ms, "value": nodes / (ms / 1e3) / 1e9, "unit": "GLUPS",
+            "fused_ms": fused_ms, "speedup_vs_fp32_step": fp32_ms_per_step / ms,
+            "speedup_vs_fp32_fused": fp32_fused_ms / fused_ms,
+            "roofline": _hbm_roofline("fused", nodes * (2 * pb + 2 * nm * 4), fused_ms,
+                                      fused_traffic(nodes, "fp16"),
+                                      traffic_source="ncu capture of the 512^2 case, scaled by r-nodes"),
+            "linf_vs_fp32_after_steps": err, "steps": steps,
+            "gpu_launches": int(n.sum()), "clocks": clocks}
+
+
+def ensemble_sub(n_runs: int, steps: int, warmup: int):
+    """The seeded 256-run ensemble advanced as one batch: the autotuned plan's time per
+    step for all runs together, and the step's algorithmic bytes against the HBM
+    roofline (the step is a replayed graph of each run's fused and fix-up kernels, so
+    the time is the whole step's)."""
+    import torch
+    from paper_2201_10132_gb300.inputs import ensemble
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    r = ensemble_throughput(n_runs, steps, warmup)
+    r["clocks"] = sampler.stop()
+    nq = r["nq"]
+    per_node = 2 * (9 + 25 * nq) * 4 + 2 * (nq + 6) * 4
+    r["roofline"] = _hbm_roofline("fused + fix-up of every run (whole step)",
+                                  r["r_nodes"] * per_node, r["ms_per_step"],
+                                  algorithmic_bytes_per_node=per_node)
+    r["workload"] = f"{n_runs} seeded runs: square grids 128-1024, Re 1-20, Wi 0.1-2, " \
+                    f"beta 0.1/0.2/0.5, N_Q = {nq}, FP32"
+    return r
+
+
+def _growth_rate(t, ey2):
+    """Least-squares slope of log(sum U_y^2) against steps over the second half."""
+    import numpy as np
+    h = len(t) // 2
+    return float(np.polyfit(np.asarray(t[h:], float), np.log(np.asarray(ey2[h:])), 1)[0])
+
+
+def learned_sub(W, blocks: int = 6, warm: int = 40, grid: int = 1024, growth_blocks: int = 36):
+    """The learned macro-step (one plain step, the network in place of K polymer
+    steps, K solvent sub-steps; the committed weights) against the plain step:
+    (1) speed at the throughput workload's size, block against 1 + K plain steps;
+    (2) the growth rate of sum U_y^2 in a growing phase against the FP64 plain run:
+    the same lattice parameters on grid^2 r-nodes (forcing wavelength kept) started
+    on the laminar profile with the seeded perturbation, `growth_blocks` blocks, the
+    rate fitted over the second half; the plain FP32 run and the block without the
+    network are reported beside it."""
+    import numpy as np
+    import torch
+    from dataclasses import replace
+    from paper_2201_10132_gb300 import tfkt, train_lpm
+    from paper_2201_10132_gb300.inputs import perturbation
+    vec, meta = train_lpm.load()
+    K, thr = meta["K"], meta["threshold"]
+    net = tfkt.Mlp(vec)
+    out = {"K": K, "threshold": thr}
+    # (1) speed at the full size
+    p = tfkt.Params.from_workload(W, tfkt.FP32)
+    ws = torch.empty(tfkt.required_bytes(p), dtype=torch.uint8, device="cuda")
+    st = torch.cuda.Stream()
+    s = tfkt.Solver(p, perturbation(W.nx, W.ny, W.seed, W.amp, W.u0), workspace=ws,
+                    stream=st.cuda_stream)
+    s.step(warm)
+    tfkt.lpm_run(s, net, 1, K=K, tile=32, threshold=thr)     # warm-up block
+    s.sync()
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    kms = np.zeros(len(tfkt.KERNELS))
+    n = np.zeros(len(tfkt.KERNELS), np.int64)
+    e0.record(st)
+    s.step_profiled(1 + K, kms, n)
+    e1.record(st)
+    e1.synchronize()
+    plain_ms = e0.elapsed_time(e1)
+    fl = 0
+    e0.record(st)
+    for _ in range(blocks):
+        fl += tfkt.lpm_run(s, net, 1, K=K, tile=32, threshold=thr)
+    e1.record(st)
+    e1.synchronize()
+    block_ms = e0.elapsed_time(e1) / blocks
+    clocks = sampler.stop()
+    nq = s.info["nq"]
+    s.close()
+    del s, ws
+    torch.cuda.empty_cache()
+    nodes = W.nx * W.ny
+    k = tfkt.KERNELS.index("fused")
+    fused_ms = kms[k] / max(n[k], 1)
+    info_bytes = 2 * (9 + 25 * nq) * 4 + 2 * (nq + 6) * 4
+    out["speed"] = {"workload": W.name, "ms_per_block": block_ms, "plain_ms_per_1_plus_K": plain_ms,
+                    "speedup_vs_fp32": plain_ms / block_ms,
+                    "glups_equivalent": nodes * (1 + K) / (block_ms / 1e3) / 1e9,
+                    "fallback_tiles": fl, "blocks": blocks,
+                    "roofline": _hbm_roofline("fused (the block's plain step)", nodes * info_bytes,
+                                              fused_ms,
+                                              share_of_block=fused_ms / block_ms),
+                    "clocks": clocks}
+    # (2) growth rate in a growing phase
+    G = replace(W, name=f"laminar-start-{grid}x{grid}-nq32", nx=grid, ny=grid,
+                k_periods=W.k_periods * grid // W.ny, ic_mode=1)
+    pert = perturbation(G.nx, G.ny, G.seed, G.amp, G.u0)
+    rates, ey = {}, {}
+    for label in ("fp64", "fp32", "net", "frozen"):
+        pg = tfkt.Params.from_workload(G, tfkt.FP64 if label == "fp64" else tfkt.FP32)
+        sg = tfkt.Solver(pg, pert)
+        t, e = [], []
+        for b in range(growth_blocks):
+            if label in ("fp64", "fp32"):
+                sg.step(1 + K)
+            elif label == "net":
+                tfkt.lpm_run(sg, net, 1, K=K, tile=32, threshold=thr)
+            else:
+                tfkt.lpm_run(sg, None, 1, K=K, tile=32, threshold=thr, mode=tfkt.LPM_FROZEN)
+            t.append((b + 1) * (1 + K))
+            e.append(sg.diagnostics()["ey2"])
+        sg.close()
+        rates[label] = _growth_rate(t, e)
+        ey[label] = (e[0], e[-1])
+    net.close()
+    torch.cuda.empty_cache()
+    out["growth"] = {"workload": G.name, "steps": growth_blocks * (1 + K),
+                     "ey2_first_last": ey, "ey2_rate_per_step": rates,
+                     "rate_rel_err_vs_fp64": {k: abs(rates[k] / rates["fp64"] - 1)
+                                              for k in ("fp32", "net", "frozen")},
+                     "growing": rates["fp64"] > 0}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -414,6 +625,9 @@ def main():
     ap.add_argument("--learned-warm", type=int, default=240)
     ap.add_argument("--learned-only", action="store_true",
                     help="time the learned block alone (no reference runs; for profiling)")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="the throughput line only, without the fp16 / ensemble / learned "
+                         "sub-records (profiling runs)")
     args = ap.parse_args()
     from paper_2201_10132_gb300.inputs import WORKLOADS
     W = WORKLOADS[args.workload]
@@ -498,6 +712,8 @@ def main():
     ms = max_over_ranks(e0.elapsed_time(e1), dist)
     diag = solver.diagnostics()
     assert all(math.isfinite(v) for v in diag.values()), diag
+    subs = rank == 0 and world == 1 and not args.no_sub
+    ref_fields = solver.moments(SUB_FIELDS) if subs and args.storage == "fp32" else None
     solver.close()
 
     # end to end through the C-ABI with pinned host buffers: create from the host
@@ -558,7 +774,8 @@ def main():
             "roofline": {"bound": "hbm", "kernel": top + "_kernel", "achieved": ach,
                          "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
                          "peak_kind": peak_kind,
-                         "traffic": _measured_traffic(nodes, args.storage) if top == "fused" else None,
+                         "traffic": fused_traffic(nodes, args.storage) if top == "fused" else None,
+                         "traffic_source": "ncu capture of the 512^2 case, scaled by r-nodes",
                          "bytes_per_launch": per[top]["bytes_per_launch"],
                          "step_model_gbs": nodes * (2 * pb + 2 * nm * s) / (ms / args.steps / 1e3) / 1e9,
                          "kernels": per},
@@ -569,6 +786,19 @@ def main():
             "clocks": clocks,
             "cpu_baseline": cpu_base,
         }
+        if subs:
+            # the side modes, each timed on its own with its own clock record
+            del ws
+            torch.cuda.empty_cache()
+            sub_launches = 0
+            if ref_fields is not None:
+                line["fp16"] = fp16_sub(W, args.steps, args.warmup, ms / args.steps,
+                                        per["fused"]["ms_per_launch"], ref_fields)
+                sub_launches += line["fp16"]["gpu_launches"]
+                del ref_fields
+            line["ensemble"] = ensemble_sub(256, 4, 2)
+            line["learned"] = learned_sub(W)
+            line["gpu_launches_sub_records"] = sub_launches
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

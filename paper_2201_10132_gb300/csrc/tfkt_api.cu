@@ -172,7 +172,7 @@ size_t layout(const Lattice& L, Workspace* w) {
   o = align_up(o + (size_t)diag_blocks_for(L) * TFKT_NDIAG * sizeof(double), A);
   w->off_diag = o;
   o = align_up(o + TFKT_NDIAG * sizeof(double), A);
-  if (L.qe_model == TFKT_QE_MOMENTUM && fused_supported(L.nx, L.ny, L.nq, sz)) {
+  if (fused_path(L)) {
     w->off_M2 = o;
     o = align_up(o + (size_t)L.nm * L.plane * sz, A);
     w->off_exp = o;
@@ -629,7 +629,7 @@ tfkt_status tfkt_create(const tfkt_params* p, const double* perturb, void* dev_w
   if (!c) return fail(TFKT_ENOMEM, "host allocation failed");
   c->L = L;
   c->stream = (cudaStream_t)stream;
-  c->fused = L.qe_model == TFKT_QE_MOMENTUM && fused_supported(L.nx, L.ny, L.nq, real_size(L));
+  c->fused = fused_path(L);
   const size_t need = layout(L, &c->ws);
   c->diag_blocks = diag_blocks_for(L);
   if (dev_workspace) {

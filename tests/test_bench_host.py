@@ -1,50 +1,55 @@
-"""Host logic of bench.py that needs no GPU: the measured DRAM traffic is taken
-from the committed ncu summary only while the kernel source still matches it,
-and the clock sampler reports the throttle reasons that were active."""
-import hashlib
+"""Host logic of bench.py that needs no GPU: the DRAM traffic of a fused launch is
+the per-node figure of the committed ncu capture scaled by the node count, and only
+while the kernel sources are those the capture was taken on; the clock sampler
+reports the throttle reasons that were active; the growth-rate fit."""
 import os
 import shutil
 import sys
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 import bench  # noqa: E402
 
-NAME = "step_fused_kernel_kolmogorov_512x512_nq32"
 
-
-def _copy_tree(tmp_path):
-    """bench's inputs for the traffic lookup: the profile summaries and the kernel source."""
+def _copy_sources(tmp_path):
     root = tmp_path / "repo"
-    shutil.copytree(os.path.join(ROOT, "profiles"), root / "profiles")
-    csrc = root / "paper_2201_10132_gb300" / "csrc"
-    csrc.mkdir(parents=True)
-    shutil.copy(os.path.join(ROOT, "paper_2201_10132_gb300", "csrc", "tfkt_fused.cu"), csrc)
+    for rel in bench.KERNEL_SOURCES:
+        (root / os.path.dirname(rel)).mkdir(parents=True, exist_ok=True)
+        shutil.copy(os.path.join(ROOT, rel), root / rel)
     return root
 
 
 @pytest.mark.parametrize("storage", ["fp32", "fp16"])
-def test_traffic_scales_per_node_while_the_source_matches(tmp_path, monkeypatch, storage):
-    root = _copy_tree(tmp_path)
+def test_traffic_scales_per_node_while_the_sources_match(tmp_path, monkeypatch, storage):
+    root = _copy_sources(tmp_path)
     monkeypatch.setattr(bench, "ROOT", str(root))
-    text = open(root / "profiles" / (NAME + ("" if storage == "fp32" else "_fp16") + ".md")).read()
-    src = open(root / "paper_2201_10132_gb300" / "csrc" / "tfkt_fused.cu", "rb").read()
-    assert hashlib.sha256(src).hexdigest()[:16] in text   # the committed summary is current
-    per_node = bench._measured_traffic(1, storage)
-    assert per_node is not None and per_node > 1000
-    assert bench._measured_traffic(4096 * 4096, storage) == pytest.approx(per_node * 4096 * 4096)
-    # any change of the kernel source makes the counters stale: no traffic
-    with open(root / "paper_2201_10132_gb300" / "csrc" / "tfkt_fused.cu", "ab") as f:
+    per_node, sha = bench.FUSED_TRAFFIC[storage]
+    assert bench.kernel_source_sha() == sha          # the committed figure is current
+    assert bench.fused_traffic(1, storage) == per_node > 1000
+    assert bench.fused_traffic(4096 * 4096, storage) == pytest.approx(per_node * 4096 * 4096)
+    # the profile summary names the same sources and figure
+    name = "step_fused_kernel_kolmogorov_512x512_nq32" + ("" if storage == "fp32" else "_fp16")
+    text = open(os.path.join(ROOT, "profiles", name + ".md")).read()
+    assert sha in text and f"**{per_node:.0f} B**" in text
+    # any change of a kernel source makes the counters stale: no traffic
+    with open(root / bench.KERNEL_SOURCES[1], "ab") as f:
         f.write(b"\n// changed\n")
-    assert bench._measured_traffic(4096 * 4096, storage) is None
+    assert bench.fused_traffic(4096 * 4096, storage) is None
 
 
-def test_traffic_is_none_without_a_summary(tmp_path, monkeypatch):
-    root = _copy_tree(tmp_path)
+def test_traffic_is_none_without_a_capture(tmp_path, monkeypatch):
+    root = _copy_sources(tmp_path)
     monkeypatch.setattr(bench, "ROOT", str(root))
-    assert bench._measured_traffic(100, "fp8") is None
+    assert bench.fused_traffic(100, "fp8") is None
+
+
+def test_growth_rate_fit_uses_the_second_half():
+    t = np.arange(1, 21) * 9.0
+    e = np.where(t < 90, 1.0, np.exp(2e-3 * (t - 90)))   # flat, then growing
+    assert bench._growth_rate(t, e) == pytest.approx(2e-3, rel=1e-9)
 
 
 def test_clock_sampler_parses_reasons(tmp_path):
