@@ -508,15 +508,18 @@ def _growth_rate(t, ey2):
     return float(np.polyfit(np.asarray(t[h:], float), np.log(np.asarray(ey2[h:])), 1)[0])
 
 
-def learned_sub(W, blocks: int = 6, warm: int = 40, grid: int = 1024, growth_blocks: int = 36):
+def learned_sub(W, blocks: int = 6, warm: int = 40, grid: int = 512, growth_warm: int = 1000,
+                growth_blocks: int = 60):
     """The learned macro-step (one plain step, the network in place of K polymer
     steps, K solvent sub-steps; the committed weights) against the plain step:
     (1) speed at the throughput workload's size, block against 1 + K plain steps;
     (2) the growth rate of sum U_y^2 in a growing phase against the FP64 plain run:
     the same lattice parameters on grid^2 r-nodes (forcing wavelength kept) started
-    on the laminar profile with the seeded perturbation, `growth_blocks` blocks, the
-    rate fitted over the second half; the plain FP32 run and the block without the
-    network are reported beside it."""
+    on the laminar profile with the seeded perturbation; after `growth_warm` plain
+    steps (in each run's own precision) the instability grows (sum U_y^2 by about
+    e^1 over the window), and `growth_blocks` blocks follow, the rate fitted over
+    their second half; the plain FP32 run and the block without the network are
+    reported beside it."""
     import numpy as np
     import torch
     from dataclasses import replace
@@ -579,6 +582,7 @@ def learned_sub(W, blocks: int = 6, warm: int = 40, grid: int = 1024, growth_blo
     for label in ("fp64", "fp32", "net", "frozen"):
         pg = tfkt.Params.from_workload(G, tfkt.FP64 if label == "fp64" else tfkt.FP32)
         sg = tfkt.Solver(pg, pert)
+        sg.step(growth_warm)
         t, e = [], []
         for b in range(growth_blocks):
             if label in ("fp64", "fp32"):
@@ -594,7 +598,8 @@ def learned_sub(W, blocks: int = 6, warm: int = 40, grid: int = 1024, growth_blo
         ey[label] = (e[0], e[-1])
     net.close()
     torch.cuda.empty_cache()
-    out["growth"] = {"workload": G.name, "steps": growth_blocks * (1 + K),
+    out["growth"] = {"workload": G.name, "warm_plain_steps": growth_warm,
+                     "steps": growth_blocks * (1 + K),
                      "ey2_first_last": ey, "ey2_rate_per_step": rates,
                      "rate_rel_err_vs_fp64": {k: abs(rates[k] / rates["fp64"] - 1)
                                               for k in ("fp32", "net", "frozen")},

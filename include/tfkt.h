@@ -345,6 +345,70 @@ tfkt_status tfkt_batch_plan(const tfkt_batch* b, int32_t* per_run, int32_t* ty, 
    library allocated it). Synchronises first; NULL is accepted. */
 tfkt_status tfkt_batch_destroy(tfkt_batch* b);
 
+/* ---- Domain decomposition in y (slabs) ---------------------------------
+   One run split into horizontal slabs, for example one per process or GPU.
+   The paper runs one domain; the split is this library's addition. A slab
+   context owns the global rows [y0, y0 + ny_local) of the run described by the
+   params (which name the WHOLE run: its nx, ny, forcing and parameters) and
+   computes TFKT_SLAB_GHOST ghost rows more on each side; it is an ordinary
+   context of ny_local + 2 TFKT_SLAB_GHOST rows (tfkt_step, tfkt_moments,
+   tfkt_psi, tfkt_populations, tfkt_diagnostics, tfkt_get_info and the
+   checkpoint calls act on all of them, local row j holding global row
+   (y0 - TFKT_SLAB_GHOST + j) mod ny), whose forcing and laminar profile are
+   those of the global rows. One step of the scheme (Sec. VI) reads data at
+   most three rows away, so the owned rows advance exactly as in the single-
+   domain run as long as, before every step and after tfkt_slab_create, each
+   side's ghost rows are replaced with the neighbour's current rows: pack the
+   side on the neighbour, unpack it here. Slab k's TFKT_SLAB_HIGH pack goes to
+   slab k+1's TFKT_SLAB_LOW unpack and slab k's TFKT_SLAB_LOW pack to slab
+   k-1's TFKT_SLAB_HIGH unpack (periodic: the last slab's high neighbour is
+   the first slab). The ghost width is one row of the fused path's 32 x 8
+   tiles: with y0 and ny_local multiples of 8 (and nx of 32) every slab takes
+   the fused path on tiles that are the single-domain run's tiles, so every
+   owned node sums its arrivals in the same order and the owned rows are bit-
+   identical to the single-domain run (the two-pass path is bit-identical for
+   any split). The learned block does not run on a slab context (EINVAL). */
+#define TFKT_SLAB_GHOST 8
+enum { TFKT_SLAB_LOW = 0, TFKT_SLAB_HIGH = 1 };
+
+/* Device bytes of a slab context with ny_local owned rows of the run p.
+   EINVAL for invalid params or ny_local outside [TFKT_SLAB_GHOST, ny]. */
+tfkt_status tfkt_slab_required_bytes(const tfkt_params* p, int32_t ny_local, size_t* bytes);
+
+/* Create the slab of rows [y0, y0 + ny_local) of the run p (0 <= y0 < ny) and
+   its initial state (as tfkt_create). perturb: host [2][ny_local + 2G][nx] (G =
+   TFKT_SLAB_GHOST) of the whole run's perturbation at the global rows
+   y0 - G ... y0 + ny_local + G - 1 (mod ny), or NULL; dev_workspace, bytes,
+   stream and the errors as for tfkt_create. */
+tfkt_status tfkt_slab_create(const tfkt_params* p, int32_t y0, int32_t ny_local,
+                             const double* perturb, void* dev_workspace, size_t workspace_bytes,
+                             void* stream, tfkt_ctx** out);
+
+/* Bytes of one side's halo message: TFKT_SLAB_GHOST rows of every population
+   plane (storage type; under FP16 storage also the FP32 solvent planes) and of
+   every moment plane, packed plane after plane. EINVAL on a context that is
+   not a slab. */
+tfkt_status tfkt_slab_halo_bytes(const tfkt_ctx* ctx, size_t* bytes);
+
+/* Copy the TFKT_SLAB_GHOST owned rows next to `side` of the current state into
+   dst (bytes >= tfkt_slab_halo_bytes; device memory if dst_is_device, else host
+   memory, owned by the caller). Device copies are queued on the context stream;
+   host copies synchronise it. Errors: EINVAL for a non-slab context, an unknown
+   side, NULL or too small dst; ECUDA (context poisoned) if a copy fails. */
+tfkt_status tfkt_slab_halo_pack(tfkt_ctx* ctx, int32_t side, void* dst, size_t bytes,
+                                int dst_is_device);
+
+/* Overwrite the TFKT_SLAB_GHOST ghost rows on `side` of the current state with
+   a neighbour's packed rows (src, bytes, src_is_device as for the pack). The
+   neighbour's pack must be complete (the same stream, an event, or a host
+   buffer). Errors as for tfkt_slab_halo_pack. */
+tfkt_status tfkt_slab_halo_unpack(tfkt_ctx* ctx, int32_t side, const void* src, size_t bytes,
+                                  int src_is_device);
+
+/* The slab's first owned global row, owned rows and ghost rows per side (any
+   pointer may be NULL); EINVAL for a context that is not a slab. */
+tfkt_status tfkt_slab_rows(const tfkt_ctx* ctx, int32_t* y0, int32_t* ny_local, int32_t* ghost);
+
 /* Static one-line description of a status code ("ok", "invalid argument",
    ...; "unknown status" for other values); never NULL. */
 const char* tfkt_status_string(tfkt_status s);

@@ -15,7 +15,7 @@ CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libtfkt.so")
 SOURCES = ["tfkt_kernels.cu", "tfkt_fused.cu", "tfkt_api.cu", "tfkt_noalloc.cu", "tfkt_batch.cu",
-           "tfkt_mlp.cu", "tfkt_lpm.cu", "tfkt_ckpt.cu"]
+           "tfkt_mlp.cu", "tfkt_lpm.cu", "tfkt_ckpt.cu", "tfkt_slab.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-I", os.path.join(ROOT, "include"), "-I", CSRC]

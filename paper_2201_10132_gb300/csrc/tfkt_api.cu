@@ -245,9 +245,13 @@ HostTables build_tables(const Lattice& L) {
         t.delta[(size_t)q * 25 + i] = 0.0;
       }
     }
+  // forcing and laminar profile of each row, at its global row (a slab's rows are
+  // rows of a larger run)
+  const int nyg = L.ny_global > 0 ? L.ny_global : L.ny;
   for (int y = 0; y < L.ny; ++y) {
-    t.arow.push_back(L.a0 * std::sin(L.kf * y));
-    t.urow.push_back(L.ic_mode == 1 ? L.u0 * std::sin(L.kf * y) : 0.0);
+    const int yg = ((L.y_origin + y) % nyg + nyg) % nyg;
+    t.arow.push_back(L.a0 * std::sin(L.kf * yg));
+    t.urow.push_back(L.ic_mode == 1 ? L.u0 * std::sin(L.kf * yg) : 0.0);
   }
   return t;
 }
@@ -603,6 +607,7 @@ tfkt_status ctx_ensure_moments_f32(Ctx* c) {
   if (c->L.precision != TFKT_FP32) return fail(TFKT_EINVAL, "FP32 context expected");
   return ensure_moments<float, float>(c);
 }
+tfkt_status ctx_ensure_moments(Ctx* c) { return DISPATCH(c, ensure_moments, c); }
 }  // namespace tfkt
 
 extern "C" {
@@ -625,6 +630,15 @@ tfkt_status tfkt_create(const tfkt_params* p, const double* perturb, void* dev_w
   Lattice L;
   tfkt_status s = map_params(p, &L);
   if (s != TFKT_OK) return s;
+  return ctx_create(L, perturb, dev_workspace, workspace_bytes, stream, out);
+}
+
+}  // extern "C"
+
+namespace tfkt {
+tfkt_status ctx_create(const Lattice& L, const double* perturb, void* dev_workspace,
+                       size_t workspace_bytes, void* stream, tfkt_ctx** out) {
+  tfkt_status s = TFKT_OK;
   tfkt_ctx* c = new (std::nothrow) tfkt_ctx();
   if (!c) return fail(TFKT_ENOMEM, "host allocation failed");
   c->L = L;
@@ -664,6 +678,9 @@ tfkt_status tfkt_create(const tfkt_params* p, const double* perturb, void* dev_w
   *out = c;
   return TFKT_OK;
 }
+}  // namespace tfkt
+
+extern "C" {
 
 tfkt_status tfkt_step(tfkt_ctx* c, int64_t n) {
   NvtxRange nvtx_range("tfkt_step");

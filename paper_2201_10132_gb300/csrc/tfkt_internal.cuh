@@ -84,6 +84,11 @@ struct Lattice {
   size_t plane = 0;   // elements per plane (ny * pitch)
   int npl = 0;        // population planes: 9 + 25 nq
   int nm = 0;         // moment planes: nq + 6
+  // Rows of a slab of a larger run (tfkt_slab_*): local row y holds global row
+  // (y_origin + y) mod ny_global; the forcing and the laminar profile follow the
+  // global row. ny_global = 0: the context is the whole run.
+  int y_origin = 0;
+  int ny_global = 0;
 };
 
 // Moment field planes (M): delta psi(q) for q < nq, then these.
@@ -216,6 +221,8 @@ struct Ctx {
   bool lpm_pending = false;        // an increment waits to be added at the next pull
   const float* lpm_rshp = nullptr; // its coefficient planes
   bool in_batch = false;  // a run of a tfkt_batch (its buffer parity belongs to the batch)
+  int slab_y0 = 0;        // a slab context (tfkt_slab_create): first owned global row,
+  int slab_ny = 0;        // owned rows (0: not a slab); the ghost rows are around them
 };
 
 // Host helpers (tfkt_api.cu).
@@ -282,13 +289,18 @@ cudaError_t launch_batch_step(const BatchRun<float>* runs, const int* tile_start
                               int total_tiles, int max_nq, int parity, cudaStream_t s, int ty);
 // Access to a context's internals and argument builders (tfkt_api.cu).
 Ctx* ctx_of(tfkt_ctx* c);
+// A context of an already mapped lattice: workspace, tables, initial state
+// (tfkt_create does the mapping first; tfkt_slab_create adjusts the rows).
+tfkt_status ctx_create(const Lattice& L, const double* perturb, void* dev_workspace,
+                       size_t workspace_bytes, void* stream, tfkt_ctx** out);
 size_t ctx_layout(const Lattice& L);
 template <typename real>
 KernelArgs<real> ctx_args(const Ctx* c);
 template <typename real>
 FusedArgs<real> ctx_fused(const Ctx* c);
-// Make the moment planes of an FP32 context current (tfkt_api.cu).
+// Make the moment planes of an FP32 context (of any context) current (tfkt_api.cu).
 tfkt_status ctx_ensure_moments_f32(Ctx* c);
+tfkt_status ctx_ensure_moments(Ctx* c);
 // Write the initial state (Sec. VI-D) again, from this perturbation (tfkt_api.cu).
 tfkt_status ctx_reinit(Ctx* c, const double* perturb);
 // Add a pending learned-block increment to the stored populations (tfkt_lpm.cu).

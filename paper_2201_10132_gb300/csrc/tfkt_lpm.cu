@@ -429,6 +429,8 @@ tfkt_status check(Ctx* c, int K) {
     return fail(TFKT_EINVAL, "the learned block uses the momentum quasi-equilibrium");
   if (L.nq < 4) return fail(TFKT_EINVAL, "the learned block needs at least 4 Q-nodes");
   if (K < 2 || K > 64 || (K & 1)) return fail(TFKT_EINVAL, "K must be even, 2 <= K <= 64");
+  // a block reaches further than the ghost rows of a slab refreshed once per step
+  if (c->slab_ny != 0) return fail(TFKT_EINVAL, "the learned block does not run on a slab context");
   if (c->poisoned) return fail(TFKT_ESTATE, "context is poisoned by an earlier CUDA error");
   return TFKT_OK;
 }

@@ -160,6 +160,18 @@ def lib() -> ctypes.CDLL:
                   "tfkt_mlp_forward", "tfkt_mlp_loss_grad", "tfkt_mlp_adam", "tfkt_lpm_run",
                   "tfkt_lpm_features", "tfkt_lpm_targets"):
             getattr(L, n).restype = S
+        L.tfkt_slab_required_bytes.argtypes = [ctypes.POINTER(_Params), ctypes.c_int32,
+                                                ctypes.POINTER(ctypes.c_size_t)]
+        L.tfkt_slab_create.argtypes = [ctypes.POINTER(_Params), ctypes.c_int32, ctypes.c_int32, D,
+                                       P, ctypes.c_size_t, P, ctypes.POINTER(P)]
+        L.tfkt_slab_halo_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
+        L.tfkt_slab_halo_pack.argtypes = [P, ctypes.c_int32, P, ctypes.c_size_t, ctypes.c_int]
+        L.tfkt_slab_halo_unpack.argtypes = [P, ctypes.c_int32, P, ctypes.c_size_t, ctypes.c_int]
+        I32 = ctypes.POINTER(ctypes.c_int32)
+        L.tfkt_slab_rows.argtypes = [P, I32, I32, I32]
+        for n in ("tfkt_slab_required_bytes", "tfkt_slab_create", "tfkt_slab_halo_bytes",
+                  "tfkt_slab_halo_pack", "tfkt_slab_halo_unpack", "tfkt_slab_rows"):
+            getattr(L, n).restype = S
         L.tfkt_status_string.argtypes = [S]
         L.tfkt_status_string.restype = ctypes.c_char_p
         L.tfkt_last_error.restype = ctypes.c_char_p
@@ -325,6 +337,72 @@ def batch_required_bytes(runs) -> int:
     _check(lib().tfkt_batch_required_bytes(arr, len(runs), ctypes.byref(n)),
            "tfkt_batch_required_bytes")
     return n.value
+
+
+# ---------------------------------------------------------------- slabs in y
+SLAB_GHOST = 8
+SLAB_LOW, SLAB_HIGH = 0, 1
+
+
+def slab_required_bytes(p: Params, ny_local: int) -> int:
+    n = ctypes.c_size_t()
+    _check(lib().tfkt_slab_required_bytes(ctypes.byref(p._c()), ny_local, ctypes.byref(n)),
+           "tfkt_slab_required_bytes")
+    return n.value
+
+
+class Slab(Solver):
+    """A slab of one run (tfkt_slab_*): owned global rows [y0, y0 + ny_local) plus
+    SLAB_GHOST ghost rows on each side. `params` describe the whole run; the arrays
+    the Solver calls return cover the slab's ny_local + 2 SLAB_GHOST local rows
+    (owned rows: SLAB_GHOST ... SLAB_GHOST + ny_local - 1). perturb: the whole run's
+    perturbation at the slab's local rows, [2, ny_local + 2 SLAB_GHOST, nx]."""
+
+    def __init__(self, params: Params, y0: int, ny_local: int, perturb: np.ndarray | None = None,
+                 workspace=None, stream: int | None = None):
+        from dataclasses import replace
+        ny_ext = ny_local + 2 * SLAB_GHOST
+        self.run_params = params
+        self.params = replace(params, ny=ny_ext)    # the shapes of the local arrays
+        self.y0, self.ny_local = y0, ny_local
+        self._workspace = workspace
+        if perturb is not None:
+            perturb = np.ascontiguousarray(perturb, dtype=np.float64)
+            assert perturb.shape == (2, ny_ext, params.nx)
+        ws_ptr, ws_bytes = None, 0
+        if workspace is not None:
+            ws_ptr = workspace.data_ptr()
+            ws_bytes = workspace.numel() * workspace.element_size()
+        h = ctypes.c_void_p()
+        _check(lib().tfkt_slab_create(ctypes.byref(params._c()), y0, ny_local,
+                                      None if perturb is None else _dptr(perturb), ws_ptr,
+                                      ws_bytes, stream, ctypes.byref(h)), "tfkt_slab_create")
+        self._h = h
+        self.info = self.get_info()
+
+    def halo_bytes(self) -> int:
+        n = ctypes.c_size_t()
+        _check(lib().tfkt_slab_halo_bytes(self._h, ctypes.byref(n)), "tfkt_slab_halo_bytes")
+        return n.value
+
+    def pack(self, side: int, ptr: int, nbytes: int, device: bool):
+        _check(lib().tfkt_slab_halo_pack(self._h, side, ctypes.c_void_p(ptr), nbytes, int(device)),
+               "tfkt_slab_halo_pack")
+
+    def unpack(self, side: int, ptr: int, nbytes: int, device: bool):
+        _check(lib().tfkt_slab_halo_unpack(self._h, side, ctypes.c_void_p(ptr), nbytes,
+                                           int(device)), "tfkt_slab_halo_unpack")
+
+    def rows(self):
+        y0, n, g = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().tfkt_slab_rows(self._h, ctypes.byref(y0), ctypes.byref(n), ctypes.byref(g)),
+               "tfkt_slab_rows")
+        return y0.value, n.value, g.value
+
+    def owned(self, a: np.ndarray, axis: int = -2) -> np.ndarray:
+        """The owned rows of a local array whose y axis is `axis` (fields [..., y, x]:
+        -2; psi [y, x, q]: 0)."""
+        return np.take(a, np.arange(SLAB_GHOST, SLAB_GHOST + self.ny_local), axis=axis)
 
 
 class _RunView(Solver):
