@@ -554,46 +554,68 @@ __global__ void __launch_bounds__(256) velocity_kernel(KernelArgs<real> a) {
   a.U[a.plane + n] = uy;
 }
 
-// Per-node observables (Sec. VII): rho_S, psi_tot, U, C, Theta, Q_rms, vorticity.
+// Per-node observables (Sec. VII): rho_S, psi_tot, U, C, Theta, Q_rms, vorticity,
+// the ones in `mask` (others are left unset). The sums over the Q-nodes run in
+// FP64 (the second moments behind C_xy and Theta_xy cancel between Q-nodes of
+// opposite sign, which FP32 sums would resolve only to ~1e-7 of the diagonal
+// ones) and only as far as the requested fields need them.
+constexpr uint32_t FIELDS_PSUM = (1u << TFKT_F_RHO_S) | (1u << TFKT_F_PSI_TOT) | (1u << TFKT_F_CXX) |
+                                 (1u << TFKT_F_CXY) | (1u << TFKT_F_CYY) | (1u << TFKT_F_QRMS);
+constexpr uint32_t FIELDS_CONF = (1u << TFKT_F_CXX) | (1u << TFKT_F_CXY) | (1u << TFKT_F_CYY) |
+                                 (1u << TFKT_F_QRMS);
+constexpr uint32_t FIELDS_STRESS = (1u << TFKT_F_THXX) | (1u << TFKT_F_THXY) | (1u << TFKT_F_THYY);
+
 template <typename real>
-__device__ void node_fields(const KernelArgs<real>& a, int x, int y, double f[TFKT_NFIELDS]) {
+__device__ void node_fields(const KernelArgs<real>& a, int x, int y, uint32_t mask,
+                            double f[TFKT_NFIELDS]) {
   const size_t P = a.plane;
   const size_t n = (size_t)y * a.pitch + x;
   const int nq = a.nq;
   double pt = 0, sxx = 0, sxy = 0, syy = 0, fxx = 0, fxy = 0, fyy = 0;
-  for (int q = 0; q < nq; ++q) {
-    const double p = double(a.tab.psi0[q]) + double(a.M[(size_t)q * P + n]);
-    const double Qx = a.tab.qx[q], Qy = a.tab.qy[q], Fx = a.tab.fx[q], Fy = a.tab.fy[q];
-    pt += p;
-    sxx += p * Qx * Qx;
-    sxy += p * Qx * Qy;
-    syy += p * Qy * Qy;
-    fxx += p * Fx * Qx;
-    fxy += p * Fx * Qy;
-    fyy += p * Fy * Qy;
+  if (mask & (FIELDS_PSUM | FIELDS_STRESS)) {
+    const bool conf = mask & FIELDS_CONF, stress = mask & FIELDS_STRESS;
+    for (int q = 0; q < nq; ++q) {
+      const double p = double(a.tab.psi0[q]) + double(a.M[(size_t)q * P + n]);
+      const double Qx = a.tab.qx[q], Qy = a.tab.qy[q];
+      pt += p;
+      if (conf) {
+        sxx += p * Qx * Qx;
+        sxy += p * Qx * Qy;
+        syy += p * Qy * Qy;
+      }
+      if (stress) {
+        const double Fx = a.tab.fx[q], Fy = a.tab.fy[q];
+        fxx += p * Fx * Qx;
+        fxy += p * Fx * Qy;
+        fyy += p * Fy * Qy;
+      }
+    }
   }
+  const double ptd = pt;
   const double rho = double(a.rho0) + double(a.M[(size_t)(nq + M_DRHO) * P + n]);
   const double l2 = a.l2, hh = 0.5 * double(a.H) * l2;
-  f[TFKT_F_RHO_S] = rho - pt;
-  f[TFKT_F_PSI_TOT] = pt;
+  f[TFKT_F_RHO_S] = rho - ptd;
+  f[TFKT_F_PSI_TOT] = ptd;
   f[TFKT_F_UX] = a.U[n];
   f[TFKT_F_UY] = a.U[P + n];
-  const double cxx = pt != 0 ? l2 * sxx / pt : 0, cxy = pt != 0 ? l2 * sxy / pt : 0,
-               cyy = pt != 0 ? l2 * syy / pt : 0;
+  const double cxx = ptd != 0 ? l2 * double(sxx) / ptd : 0, cxy = ptd != 0 ? l2 * double(sxy) / ptd : 0,
+               cyy = ptd != 0 ? l2 * double(syy) / ptd : 0;
   f[TFKT_F_CXX] = cxx;
   f[TFKT_F_CXY] = cxy;
   f[TFKT_F_CYY] = cyy;
-  f[TFKT_F_THXX] = hh * fxx;
-  f[TFKT_F_THXY] = hh * fxy;
-  f[TFKT_F_THYY] = hh * fyy;
+  f[TFKT_F_THXX] = hh * double(fxx);
+  f[TFKT_F_THXY] = hh * double(fxy);
+  f[TFKT_F_THYY] = hh * double(fyy);
   f[TFKT_F_QRMS] = sqrt(cxx + cyy);
-  const int xm = x == 0 ? a.nx - 1 : x - 1, xp = x == a.nx - 1 ? 0 : x + 1;
-  const int ym = y == 0 ? a.ny - 1 : y - 1, yp = y == a.ny - 1 ? 0 : y + 1;
-  const double duy_dx = 0.5 * (double(a.U[P + (size_t)y * a.pitch + xp]) -
-                               double(a.U[P + (size_t)y * a.pitch + xm]));
-  const double dux_dy =
-      0.5 * (double(a.U[(size_t)yp * a.pitch + x]) - double(a.U[(size_t)ym * a.pitch + x]));
-  f[TFKT_F_VORT] = duy_dx - dux_dy;
+  if (mask & (1u << TFKT_F_VORT)) {
+    const int xm = x == 0 ? a.nx - 1 : x - 1, xp = x == a.nx - 1 ? 0 : x + 1;
+    const int ym = y == 0 ? a.ny - 1 : y - 1, yp = y == a.ny - 1 ? 0 : y + 1;
+    const double duy_dx = 0.5 * (double(a.U[P + (size_t)y * a.pitch + xp]) -
+                                 double(a.U[P + (size_t)y * a.pitch + xm]));
+    const double dux_dy =
+        0.5 * (double(a.U[(size_t)yp * a.pitch + x]) - double(a.U[(size_t)ym * a.pitch + x]));
+    f[TFKT_F_VORT] = duy_dx - dux_dy;
+  }
 }
 
 template <typename real>
@@ -602,7 +624,7 @@ __global__ void __launch_bounds__(256) fields_kernel(KernelArgs<real> a, uint32_
   const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
   if (x >= a.nx || y >= a.ny) return;
   double f[TFKT_NFIELDS];
-  node_fields(a, x, y, f);
+  node_fields(a, x, y, mask, f);
   const size_t N = (size_t)a.nx * a.ny, k = (size_t)y * a.nx + x;
   int slot = 0;
   for (int j = 0; j < TFKT_NFIELDS; ++j)

@@ -12,6 +12,7 @@
 
 #include "tfkt_internal.cuh"
 #include "tfkt_mlp.cuh"
+#include "tfkt_umma.cuh"
 
 namespace tfkt {
 
@@ -24,7 +25,7 @@ enum { L_PSI = 0, L_C1 = 1, L_DP = 4, L_JP = 6, L_CNEW = 8, L_CPREV = 11, L_B = 
 
 struct LpmArgs {
   float* p;                 // scratch planes, plane k at p + k * plane
-  int* counter;             // tiles that fell back
+  int* counter;             // tiles that fell back; counter[1]: a tensor-core wait timed out
   float S0[3];              // sum_q psi0 Q_a Q_b (xx, xy, yy), Q lattice units
   float m0[3];              // second moments of the normalised equilibrium p0 = psi0 / psi_tot0
   float M0inv[9];           // inverse of M0[a][b] = sum_q p0 qq_a w_b (qq_b - m0_b), w = 1, 2, 1
@@ -159,14 +160,66 @@ __device__ __forceinline__ void node_features(const KernelArgs<float>& a, const 
 }
 
 // One block per judge tile: the network's C_new for every node, the tile's
-// largest disagreement with the plain rate, and the fallback. Each warp takes
-// 32 nodes at a time: every lane forms its node's features, and the warp runs
-// the network on the tensor cores (mlp_warp_tc).
-constexpr int NET_THREADS = 256;
+// largest disagreement with the plain rate, and the fallback.
+//
+// The network runs on the fifth-generation tensor cores (tcgen05): the block is
+// two groups of 128 threads, and each group takes 128 nodes at a time, one node
+// per thread and per TMEM lane. Every thread forms its node's 40 standardised
+// features, splits them into a bfloat16 high part and remainder, and writes them
+// as its row of the K-major operands in shared memory; one thread issues the
+// layer's MMAs (bf16 operands, FP32 accumulators in 64 TMEM columns) for the
+// high part and the remainder against the bfloat16 weights, and commits them to
+// the group's mbarrier. Each thread then loads its row of accumulators from TMEM,
+// adds the bias, applies GELU and writes the next layer's operand row. The
+// 64 -> 3 output layer (too narrow for the tensor cores) runs on the CUDA cores
+// in FP32. A wait that does not complete within its bound sets counter[1],
+// skips the TMEM reads (the tile falls back) and still frees the TMEM.
+constexpr int NET_GROUPS = 2;
+constexpr int NET_THREADS = 128 * NET_GROUPS;
+constexpr int NET_K1 = 48;                       // layer-1 inner size: NIN padded to 3 steps of 16
+constexpr uint32_t NET_SBO1 = NET_K1 / 8 * 128;  // operand bytes per 8 rows, K = 48
+constexpr uint32_t NET_SBO2 = NH / 8 * 128;      // K = 64
+constexpr uint32_t NET_IDESC = umma::idesc_bf16_f32(128, NH);
+constexpr uint32_t NET_MAX_POLLS = 1u << 22;
+static_assert(NIN <= NET_K1 && NH == 64 && NOUT == 3, "tensor-core tiling of the network");
+
+struct NetSmem {
+  __nv_bfloat16 w1[NH * NET_K1];                 // K-major operand layout, in >= NIN zero
+  __nv_bfloat16 w2[NH * NH];
+  __nv_bfloat16 act[NET_GROUPS][2][128 * NH];    // per group: high part and remainder rows
+  float w3[NOUT][NH];
+  float b1[NH], b2[NH], b3[NOUT];
+  float mx[NIN], rsx[NIN], mt[NOUT], st[NOUT];
+  uint64_t mbar[NET_GROUPS];
+  uint32_t tmem;
+};
+constexpr size_t net_smem_bytes() { return sizeof(NetSmem) + 128; }
+
+// Byte offset of element (r, k) in a K-major operand with sbo bytes per 8 rows.
+__host__ __device__ constexpr uint32_t op_offset(int r, int k, uint32_t sbo) {
+  return (uint32_t)(r / 8) * sbo + (uint32_t)(k / 8) * 128u + (uint32_t)(r % 8) * 16u +
+         (uint32_t)(k % 8) * 2u;
+}
+
+// Writes 8 values v[8 c .. 8 c + 7] of row r, split into high part and remainder,
+// as one 16-byte chunk of each operand.
+__device__ __forceinline__ void write_row(__nv_bfloat16* hi, __nv_bfloat16* lo, int r, const float* v,
+                                          int nchunks, uint32_t sbo) {
+  for (int c = 0; c < nchunks; ++c) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) tc_split(v[8 * c + 2 * j], v[8 * c + 2 * j + 1], h[j], l[j]);
+    const uint32_t off = op_offset(r, 8 * c, sbo);
+    *reinterpret_cast<uint4*>(reinterpret_cast<char*>(hi) + off) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(reinterpret_cast<char*>(lo) + off) = make_uint4(l[0], l[1], l[2], l[3]);
+  }
+}
+
 __global__ void __launch_bounds__(NET_THREADS) net_kernel(KernelArgs<float> a, LpmArgs l, MlpDev net) {
   extern __shared__ __align__(16) unsigned char net_smem[];
   __shared__ float red[NET_THREADS];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int g = tid >> 7, r = tid & 127;         // group, row (node) within the group
   const size_t P = a.plane;
   const int T = l.tile;
   const int tx0 = blockIdx.x * T, ty0 = blockIdx.y * T;
@@ -183,45 +236,155 @@ __global__ void __launch_bounds__(NET_THREADS) net_kernel(KernelArgs<float> a, L
     }
     return;
   }
-  MlpTc& s = *reinterpret_cast<MlpTc*>(net_smem);
-  float* Xw = reinterpret_cast<float*>(net_smem + ((sizeof(MlpTc) + 15) & ~(size_t)15)) +
-              (size_t)warp * TC_WARP_FLOATS;
-  float* Ow = Xw + TC_ROWS * TC_XLD;
-  mlp_stage_tc(s, net.master, net.wmat, tid, blockDim.x);
+  // 128-byte aligned view of the dynamic shared memory
+  NetSmem& s = *reinterpret_cast<NetSmem*>(
+      (unsigned char*)(((uintptr_t)net_smem + 127) & ~(uintptr_t)127));
+  // weights into the operand layout, the rest as FP32
+  for (int e = tid; e < NH * NET_K1; e += blockDim.x) {
+    const int o = e / NET_K1, i = e % NET_K1;
+    *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<char*>(s.w1) + op_offset(o, i, NET_SBO1)) =
+        i < NIN ? net.wmat[o * NIN + i] : __float2bfloat16(0.0f);
+  }
+  for (int e = tid; e < NH * NH; e += blockDim.x) {
+    const int o = e / NH, i = e % NH;
+    *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<char*>(s.w2) + op_offset(o, i, NET_SBO2)) =
+        net.wmat[NH * NIN + o * NH + i];
+  }
+  for (int e = tid; e < NOUT * NH; e += blockDim.x)
+    s.w3[e / NH][e % NH] = __bfloat162float(net.wmat[NH * NIN + NH * NH + e]);
+  for (int k = tid; k < NH; k += blockDim.x) {
+    s.b1[k] = net.master[OB1 + k];
+    s.b2[k] = net.master[OB2 + k];
+  }
+  for (int k = tid; k < NIN; k += blockDim.x) {
+    s.mx[k] = net.master[OMX + k];
+    s.rsx[k] = 1.0f / net.master[OSX + k];
+  }
+  for (int k = tid; k < NOUT; k += blockDim.x) {
+    s.b3[k] = net.master[OB3 + k];
+    s.mt[k] = net.master[OMT + k];
+    s.st[k] = net.master[OST + k];
+  }
+  if (tid == 0)
+    for (int q = 0; q < NET_GROUPS; ++q) umma::mbar_init(&s.mbar[q], 1);
+  if (warp == 0) umma::tmem_alloc(&s.tmem, 64 * NET_GROUPS);
+  umma::fence_proxy_async();
+  umma::fence_before_sync();
   __syncthreads();
+  umma::fence_after_sync();
+  const uint32_t tmem = s.tmem + 64u * g;                          // the group's 64 columns
+  const uint32_t tmem_row = tmem + ((uint32_t)(32 * (warp & 3)) << 16);   // this warp's lanes
+  __nv_bfloat16* ahi = s.act[g][0];
+  __nv_bfloat16* alo = s.act[g][1];
+  const uint32_t ahi_a = umma::smem_addr(ahi), alo_a = umma::smem_addr(alo);
+  const uint32_t w1_a = umma::smem_addr(s.w1), w2_a = umma::smem_addr(s.w2);
+  uint32_t phase = 0;
+  bool failed = false;
   float worst = 0.f;
-  const int nwarps = blockDim.x >> 5;
-  for (int base = warp * TC_ROWS; base < T * T; base += nwarps * TC_ROWS) {   // warp-uniform
-    const int k = base + lane;
+  const int npass = (T * T + NET_THREADS - 1) / NET_THREADS;      // same count in both groups
+  for (int pass = 0; pass < npass; ++pass) {
+    const int k = pass * NET_THREADS + g * 128 + r;
     const int x = tx0 + k % T, y = ty0 + k / T;
     const bool ok = k < T * T && x < a.nx && y < a.ny;
-    float f[NIN], cdep[3] = {0.f, 0.f, 0.f};
-    float* xr = Xw + lane * TC_XLD;
+    float f[NET_K1], cdep[3] = {0.f, 0.f, 0.f};
     if (ok) {
       node_features(a, l, x, y, f, cdep);
 #pragma unroll
-      for (int i = 0; i < NIN; ++i) xr[i] = (f[i] - s.mx[i]) * s.rsx[i];
+      for (int i = 0; i < NIN; ++i) f[i] = (f[i] - s.mx[i]) * s.rsx[i];
     } else {
 #pragma unroll
-      for (int i = 0; i < NIN; ++i) xr[i] = 0.f;
+      for (int i = 0; i < NIN; ++i) f[i] = 0.f;
     }
 #pragma unroll
-    for (int i = NIN; i < TC_K1; ++i) xr[i] = 0.f;
-    __syncwarp();
-    mlp_warp_tc(s, Xw, Ow, lane);
-    __syncwarp();
+    for (int i = NIN; i < NET_K1; ++i) f[i] = 0.f;
+    // layer 1: [128 x 48] x [48 x 64]
+    write_row(ahi, alo, r, f, NET_K1 / 8, NET_SBO1);
+    umma::fence_proxy_async();
+    umma::fence_before_sync();
+    umma::bar_sync(1 + g, 128);
+    if (r == 0) {
+      umma::fence_after_sync();
+      for (int ks = 0; ks < NET_K1 / 16; ++ks) {
+        const uint64_t bd = umma::desc_kmajor(w1_a + 256u * ks, 128u, NET_SBO1);
+        umma::mma_bf16(tmem, umma::desc_kmajor(ahi_a + 256u * ks, 128u, NET_SBO1), bd, NET_IDESC,
+                       ks > 0);
+        umma::mma_bf16(tmem, umma::desc_kmajor(alo_a + 256u * ks, 128u, NET_SBO1), bd, NET_IDESC,
+                       true);
+      }
+      umma::commit(&s.mbar[g]);
+    }
+    const bool done1 = umma::mbar_wait(&s.mbar[g], phase, NET_MAX_POLLS);
+    phase ^= 1u;
+    umma::fence_after_sync();
+    float h[NH];
+    if (done1) {
+      float v[32];
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        umma::ld_x32(tmem_row + 32u * half, v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) h[32 * half + j] = gelu(v[j] + s.b1[32 * half + j]);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < NH; ++j) h[j] = 0.f;
+    }
+    // layer 2: [128 x 64] x [64 x 64] (the layer-1 operands are consumed: reuse them)
+    write_row(ahi, alo, r, h, NH / 8, NET_SBO2);
+    umma::fence_proxy_async();
+    umma::fence_before_sync();
+    umma::bar_sync(1 + g, 128);
+    if (r == 0) {
+      umma::fence_after_sync();
+      for (int ks = 0; ks < NH / 16; ++ks) {
+        const uint64_t bd = umma::desc_kmajor(w2_a + 256u * ks, 128u, NET_SBO2);
+        umma::mma_bf16(tmem, umma::desc_kmajor(ahi_a + 256u * ks, 128u, NET_SBO2), bd, NET_IDESC,
+                       ks > 0);
+        umma::mma_bf16(tmem, umma::desc_kmajor(alo_a + 256u * ks, 128u, NET_SBO2), bd, NET_IDESC,
+                       true);
+      }
+      umma::commit(&s.mbar[g]);
+    }
+    const bool done2 = umma::mbar_wait(&s.mbar[g], phase, NET_MAX_POLLS);
+    phase ^= 1u;
+    umma::fence_after_sync();
+    float o[NOUT] = {s.b3[0], s.b3[1], s.b3[2]};
+    if (done2) {
+      float v[32];
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        umma::ld_x32(tmem_row + 32u * half, v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const float hj = gelu(v[j] + s.b2[32 * half + j]);
+#pragma unroll
+          for (int c = 0; c < NOUT; ++c) o[c] = fmaf(s.w3[c][32 * half + j], hj, o[c]);
+        }
+      }
+    }
+    // the next pass's layer-1 MMAs overwrite these TMEM columns and operands only
+    // after every thread of the group has passed its next barrier
+    umma::fence_before_sync();
+    if (!(done1 && done2)) {
+      failed = true;
+      if (r == 0) atomicExch(l.counter + 1, 1);
+    }
     if (ok) {
       const size_t n = (size_t)y * a.pitch + x;
       for (int c = 0; c < 3; ++c) {
-        const float o = Ow[lane * 4 + c] * s.st[c] + s.mt[c];
-        const float cn = cdep[c] + l.ce * o;
+        const float cn = cdep[c] + l.ce * (o[c] * s.st[c] + s.mt[c]);
         Cn[(size_t)c * P + n] = cn;
         const float c1 = C1[(size_t)c * P + n];
         const float plain = c1 + Kf * (c1 - Cp[(size_t)c * P + n]);
         worst = fmaxf(worst, fabsf(cn - plain) / l.ce);
       }
     }
-    __syncwarp();   // the next pass overwrites this warp's rows
+  }
+  if (failed) {
+    // the tile falls back; before the TMEM is freed, wait (again bounded) for the
+    // group's last MMAs to complete
+    worst = __int_as_float(0x7f800000);
+    if (r == 0) umma::mbar_wait(&s.mbar[g], phase ^ 1u, NET_MAX_POLLS);
   }
   red[tid] = worst;
   __syncthreads();
@@ -238,6 +401,9 @@ __global__ void __launch_bounds__(NET_THREADS) net_kernel(KernelArgs<float> a, L
       for (int c = 0; c < 3; ++c) Cn[(size_t)c * P + n] = C1[(size_t)c * P + n];
     }
   }
+  // every TMEM load has completed (the reduction's barriers follow them)
+  umma::fence_after_sync();
+  if (warp == 0) umma::tmem_dealloc(s.tmem, 64 * NET_GROUPS);
 }
 
 // Training features of every node (node order y-major, nx per row).
@@ -537,7 +703,7 @@ extern "C" tfkt_status tfkt_lpm_run(tfkt_ctx* cc, const tfkt_mlp* net, const tfk
   const dim3 tiles((L.nx + o->tile - 1) / o->tile, (L.ny + o->tile - 1) / o->tile);
   MlpDev nd{};
   if (net) nd = mlp_dev(net);
-  LPM_CUDA(cudaMemsetAsync(l.counter, 0, sizeof(int), st));
+  LPM_CUDA(cudaMemsetAsync(l.counter, 0, 2 * sizeof(int), st));
   for (int64_t b = 0; b < nblocks; ++b) {
     if (c->lpm_step != c->step) {
       conf_kernel<<<grid, blk, 0, st>>>(ctx_args<float>(c), l, L_CPREV);
@@ -548,7 +714,7 @@ extern "C" tfkt_status tfkt_lpm_run(tfkt_ctx* cc, const tfkt_mlp* net, const tfk
     LPM_CUDA(launch_velocity<float>(a, st));
     prepare_kernel<<<grid, blk, 0, st>>>(a, l);
     LPM_CUDA(cudaGetLastError());
-    const size_t nsm = tc_smem_bytes(NET_THREADS / 32);
+    const size_t nsm = net_smem_bytes();
     LPM_CUDA(cudaFuncSetAttribute(net_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nsm));
     net_kernel<<<tiles, NET_THREADS, nsm, st>>>(a, l, nd);
     LPM_CUDA(cudaGetLastError());
@@ -569,10 +735,13 @@ extern "C" tfkt_status tfkt_lpm_run(tfkt_ctx* cc, const tfkt_mlp* net, const tfk
     c->lpm_step = c->step;
   }
   if (flagged) {
-    int h = 0;
-    LPM_CUDA(cudaMemcpyAsync(&h, l.counter, sizeof(int), cudaMemcpyDeviceToHost, st));
+    int h[2] = {0, 0};
+    LPM_CUDA(cudaMemcpyAsync(h, l.counter, sizeof(h), cudaMemcpyDeviceToHost, st));
     LPM_CUDA(cudaStreamSynchronize(st));
-    *flagged = h;
+    *flagged = h[0];
+    if (h[1])
+      return fail(TFKT_ECUDA, "a tensor-core wait of the network kernel timed out "
+                              "(the affected tiles fell back to the plain step)");
   }
   return TFKT_OK;
 }
