@@ -557,6 +557,14 @@ def learned_sub(W, blocks: int = 6, warm: int = 40, grid: int = 512, growth_warm
     e1.record(st)
     e1.synchronize()
     block_ms = e0.elapsed_time(e1) / blocks
+    # every tile falling back (threshold 0): the block keeps the plain step's conformation
+    fl_all = 0
+    e0.record(st)
+    for _ in range(blocks):
+        fl_all += tfkt.lpm_run(s, net, 1, K=K, tile=32, threshold=0.0)
+    e1.record(st)
+    e1.synchronize()
+    fallback_ms = e0.elapsed_time(e1) / blocks
     clocks = sampler.stop()
     nq = s.info["nq"]
     s.close()
@@ -570,6 +578,8 @@ def learned_sub(W, blocks: int = 6, warm: int = 40, grid: int = 512, growth_warm
                     "speedup_vs_fp32": plain_ms / block_ms,
                     "glups_equivalent": nodes * (1 + K) / (block_ms / 1e3) / 1e9,
                     "fallback_tiles": fl, "blocks": blocks,
+                    "ms_per_block_all_tiles_falling_back": fallback_ms,
+                    "tiles_falling_back_in_that_run": fl_all,
                     "roofline": _hbm_roofline("fused (the block's plain step)", nodes * info_bytes,
                                               fused_ms,
                                               share_of_block=fused_ms / block_ms),
