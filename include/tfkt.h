@@ -89,8 +89,8 @@ typedef struct {
                             anti-diffusive in r, make the step unstable; keep the disk
                             well inside Q0. */
   int32_t qe_model;      /* tfkt_qe_model: which variables the collision holds
-                            quasi-conserved (Sec. V); the stress model takes the
-                            two-pass kernels */
+                            quasi-conserved (Sec. V); both models take the fused
+                            kernel on grids of 32 x 8 tiles */
 } tfkt_params;
 
 /* Derived lattice parameters and layout of a context. */

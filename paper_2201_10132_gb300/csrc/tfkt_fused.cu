@@ -90,8 +90,11 @@ __device__ __forceinline__ Smem<real> carve(unsigned char* base, int nq) {
 // offsets and sums the moments velocity by velocity; the single-run kernel
 // uses a table of source-plane pointers and pairwise moment sums, which cost
 // registers but fewer instructions (measured: each is faster in one kernel and
-// slower in the other).
-template <typename real, typename S, bool RESHAPE, int H, bool LEAN>
+// slower in the other). STRESS: the collision with the component stresses
+// quasi-conserved (Sec. V, Eq. quasieq2; f*_S and f**_P of Sec. VI), whose
+// targets carry the equilibrium momenta and the current stresses of f; it needs
+// the second moments of every Q-node's populations (single-run kernel only).
+template <typename real, typename S, bool RESHAPE, int H, bool LEAN, bool STRESS = false>
 __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const FusedArgs<real>& fa,
                                            int btx, int bty, int ntx, int nty,
                                            unsigned char* smem_raw) {
@@ -212,6 +215,41 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
   }
 
   // ---- solvent
+  if constexpr (STRESS) {
+    // stress quasi-equilibrium: f*_S carries rho_S U and the stress of f,
+    // P(f) - rho_S c_s^2 I = [2 tau2 (P(g) - P_eq) + tau2 (F U + U F)] / (2 tau2 + 1) + rho_S U U
+    real hs[9];
+    real drs = 0, pxx = 0, pxy = 0, pyy = 0;
+    static_for<0, 9>([&](auto I) {
+      constexpr int i = I;
+      hs[i] = from_store<real>(ssrc[(size_t)i * P + off[shift_index(-c9x(i), -c9y(i))]]);
+      drs += hs[i];
+      acc<c9x(i) * c9x(i)>(pxx, hs[i]);
+      acc<c9x(i) * c9y(i)>(pxy, hs[i]);
+      acc<c9y(i) * c9y(i)>(pyy, hs[i]);
+    });
+    const real cs2 = real(1) / real(3);
+    const real rs = real(1) + drs;
+    const real dxx = pxx - drs * cs2 - rs * Ux * Ux, dxy = pxy - rs * Ux * Uy;
+    const real dyy = pyy - drs * cs2 - rs * Uy * Uy;
+    const real fxx = (a.c2 * dxx + a.tau2 * real(2) * force * Ux) * a.inv_c2p1 + rs * Ux * Ux;
+    const real fxy = (a.c2 * dxy + a.tau2 * force * Uy) * a.inv_c2p1 + rs * Ux * Uy;
+    const real fyy = a.c2 * dyy * a.inv_c2p1 + rs * Uy * Uy;
+    const real usq = Ux * Ux + Uy * Uy;
+    static_for<0, 9>([&](auto I) {
+      constexpr int i = I;
+      constexpr real cx = real(c9x(i)), cy = real(c9y(i));
+      const real cu = cx * Ux + cy * Uy;
+      const real pneq = fxx * (cx * cx - cs2) + real(2) * fxy * cx * cy + fyy * (cy * cy - cs2);
+      const real fss_dev = real(w9(i)) * (drs + real(3) * rs * cu + real(4.5) * pneq);
+      const real feq_dev = real(w9(i)) * (drs + rs * (real(3) * cu + real(4.5) * cu * cu - real(1.5) * usq));
+      const real srcterm = real(w9(i)) * (real(3) * (cx - Ux) + real(9) * cu * cx) * force;
+      const real hp = a.om2b * hs[i] + a.tb * (a.omr * fss_dev + a.r * feq_dev) + a.omb * srcterm;
+      sdst[(size_t)i * P + n] = to_store<SS>(hp);
+      if constexpr (i == 0) ms_arr += hp;
+      else sm.hb[(i - 1) * HSZ + hcell] = hp;
+    });
+  } else
   {
     real hs[9];
     real drs = 0, jsx = 0, jsy = 0;
@@ -320,6 +358,9 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
       mn[3] = Mq[off[1]];
     }
     real dpsi = 0, rx = 0, ry = 0, qx = 0, qy = 0;
+    // STRESS: second moments of the deviations on the four axes (rx, ry, qx, qy):
+    // diagonal t[k] and the six off-diagonal pairs t2[pr], in the pair order below
+    real t[4] = {0, 0, 0, 0}, t2[6] = {0, 0, 0, 0, 0, 0};
     if constexpr (LEAN) {
       static_for<0, 25>([&](auto I) {
         constexpr int i = I;
@@ -341,7 +382,15 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
         constexpr int imp = pair_vel(ca, cb, -1, 1), imm = pair_vel(ca, cb, -1, -1);
         static_assert(ipp > 0 && ipm > 0 && imp > 0 && imm > 0, "D4Q25 pair velocities");
         const real d1 = h[ipp] - h[imm], d2 = h[ipm] - h[imp];
-        dpsi += (h[ipp] + h[imm]) + (h[ipm] + h[imp]);
+        const real s1 = h[ipp] + h[imm], s2 = h[ipm] + h[imp];
+        dpsi += s1 + s2;
+        if constexpr (STRESS) {
+          // the four velocities have c_a^2 = c_b^2 = 1 and c_a c_b = +1 (pp, mm) or -1 (pm, mp)
+          const real sg = s1 + s2;
+          t[ca] += sg;
+          t[cb] += sg;
+          t2[pr] += s1 - s2;
+        }
         const real ma = d1 + d2, mb = d1 - d2;
         auto addc = [&](auto K, real v) {
           constexpr int k = decltype(K)::value;
@@ -357,18 +406,45 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
     const real Qx = a.tab.qx[q], Qy = a.tab.qy[q], Fx = a.tab.fx[q], Fy = a.tab.fy[q];
     const real psi = a.tab.psi0[q] + dpsi;
     const real qg = Qx * dpx + Qy * dpy;
-    const real jrex = psi * Ux + a.tau2 * a.hl2h * Fx * qg;
-    const real jrey = psi * Uy + a.tau2 * a.hl2h * Fy * qg;
+    const real jrex = psi * Ux + a.tau_m * a.hl2h * Fx * qg;
+    const real jrey = psi * Uy + a.tau_m * a.hl2h * Fy * qg;
     const real jqex = psi * (Qx * G00 + Qy * G10 - a.kappa * Fx);
     const real jqey = psi * (Qx * G01 + Qy * G11 - a.kappa * Fy);
     // 3 x the momenta of the mixed equilibrium (1 - r) f* + r f^eq, times the
     // relaxation weight 2 beta w_i of the moving velocities (w_i = 1/36): a
     // moving population then takes an add per nonzero component and one FMA
     const real tw = a.tb * real(1.0 / 36.0), tw3 = real(3) * tw;
-    const real mrx = tw3 * (a.omr * (a.c2 * rx + jrex) * a.inv_c2p1 + a.r * jrex);
-    const real mry = tw3 * (a.omr * (a.c2 * ry + jrey) * a.inv_c2p1 + a.r * jrey);
-    const real mqx = tw3 * (a.omr * (a.c2 * qx + jqex) * a.inv_c2p1 + a.r * jqex);
-    const real mqy = tw3 * (a.omr * (a.c2 * qy + jqey) * a.inv_c2p1 + a.r * jqey);
+    real mrx, mry, mqx, mqy;
+    // STRESS: the second-order Hermite terms of f**, times the relaxation weight
+    // and (1 - r): per axis sk[k] = 4.5 (P(f) - P_eq)_kk, s0 = -1.5 tr, and per
+    // pair sp[pr] = 9 (P(f) - P_eq)_ab, with P(f) - P_eq = 2 tau2 (P(g) - P_eq) / (2 tau2 + 1)
+    // and P_eq = psi c_s^2 I on the diagonal blocks; a moving velocity on the pair
+    // (a, b) adds sk[a] + sk[b] + s0 + c_a c_b sp[pr], the rest velocity s0
+    real sk[4], sp[6], s0 = 0;
+    if constexpr (STRESS) {
+      // both targets carry the equilibrium momenta
+      mrx = tw3 * jrex;
+      mry = tw3 * jrey;
+      mqx = tw3 * jqex;
+      mqy = tw3 * jqey;
+      const real cs2 = real(1) / real(3);
+      const real kf = tw * a.omr * a.c2 * a.inv_c2p1;
+      real tr = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const real dk = t[k] - dpsi * cs2;
+        tr += dk;
+        sk[k] = real(4.5) * kf * dk;
+      }
+      s0 = real(-1.5) * kf * tr;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) sp[k] = real(9) * kf * t2[k];
+    } else {
+      mrx = tw3 * (a.omr * (a.c2 * rx + jrex) * a.inv_c2p1 + a.r * jrex);
+      mry = tw3 * (a.omr * (a.c2 * ry + jrey) * a.inv_c2p1 + a.r * jrey);
+      mqx = tw3 * (a.omr * (a.c2 * qx + jqex) * a.inv_c2p1 + a.r * jqex);
+      mqy = tw3 * (a.omr * (a.c2 * qy + jqey) * a.inv_c2p1 + a.r * jqey);
+    }
     const real wdpsi = tw * dpsi;
     S* dq = dst + (size_t)(9 + 25 * q) * P + n;
     real grp[9];
@@ -382,6 +458,19 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
       acc<c25(i).ry>(d, mry);
       acc<c25(i).qx>(d, mqx);
       acc<c25(i).qy>(d, mqy);
+      if constexpr (STRESS) {
+        if constexpr (i == 0) {
+          d += real(12) * s0;                       // w0 / w = 12
+        } else {
+          constexpr V4 cv = c25(i);
+          constexpr int ka = cv.rx != 0 ? 0 : (cv.ry != 0 ? 1 : 2);
+          constexpr int kb = cv.qy != 0 ? 3 : (cv.qx != 0 ? 2 : 1);
+          constexpr int pr = ka == 0 ? kb - 1 : (ka == 1 ? kb + 1 : 5);
+          constexpr int sab = comp_of(cv, ka) * comp_of(cv, kb);
+          d += sk[ka] + sk[kb] + s0;
+          acc<sab>(d, sp[pr]);
+        }
+      }
       const real hp = a.om2b * h[i] + d;
       if constexpr (std::is_same<S, real>::value) dq[(size_t)i * P] = hp;
       else dq[(size_t)i * P] = to_store<S>(hp * a.pscale);
@@ -482,12 +571,12 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
   }
 }
 
-template <typename real, typename S, bool RESHAPE>
+template <typename real, typename S, bool RESHAPE, bool STRESS = false>
 __global__ void __launch_bounds__(Geo<TY>::NT, 2)
 step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  fused_body<real, S, RESHAPE, TY, false>(a, fa, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y,
-                                          smem_raw);
+  fused_body<real, S, RESHAPE, TY, false, STRESS>(a, fa, blockIdx.x, blockIdx.y, gridDim.x,
+                                                  gridDim.y, smem_raw);
 }
 
 // Completes the border nodes of every tile: own partial sums plus the ring
@@ -707,8 +796,7 @@ bool fused_supported(int nx, int ny, int nq, size_t real_bytes, int ty) {
 }
 
 bool fused_path(const Lattice& L) {
-  return L.qe_model == TFKT_QE_MOMENTUM &&
-         fused_supported(L.nx, L.ny, L.nq, L.precision == TFKT_FP64 ? 8 : 4);
+  return fused_supported(L.nx, L.ny, L.nq, L.precision == TFKT_FP64 ? 8 : 4);
 }
 
 template <typename real, typename S>
@@ -726,6 +814,13 @@ cudaError_t launch_step_fused(const KernelArgs<real>& a, const FusedArgs<real>& 
     } else {
       return cudaErrorInvalidValue;
     }
+  }
+  if (a.qe == TFKT_QE_STRESS) {
+    cudaError_t e = cudaFuncSetAttribute(step_fused_kernel<real, S, false, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    step_fused_kernel<real, S, false, true><<<grid, block, smem, s>>>(a, f);
+    return cudaGetLastError();
   }
   cudaError_t e = cudaFuncSetAttribute(step_fused_kernel<real, S, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -274,8 +274,8 @@ template <typename real, typename S>
 cudaError_t launch_step_fused(const KernelArgs<real>& a, const FusedArgs<real>& f, cudaStream_t s);
 template <typename real>
 cudaError_t launch_fixup(const KernelArgs<real>& a, const FusedArgs<real>& f, cudaStream_t s);
-// Whether a context of this lattice takes the fused path (tile multiples, the
-// momentum quasi-equilibrium, the kernel's shared memory).
+// Whether a context of this lattice takes the fused path (tile multiples and the
+// kernel's shared memory; either quasi-equilibrium).
 bool fused_path(const Lattice& L);
 
 // Each run's single-run FP32 kernels (fused step + fix-up) without API calls

@@ -67,12 +67,14 @@ CASES = [
     (64, 32, 6, 3.0, 5.0, 2.0, 0.2, 1, 0.0, 1, 12, 3.1),     # fused path
     (64, 32, 6, 3.0, 5.0, 2.0, 0.5, 1, 0.3, 1, 12, 3.1),     # fused, tau2 > tau1
     # stress quasi-equilibrium (last entry 1; tau2 is then the faster momentum time):
-    # always the two-pass kernels
+    # two-pass kernels on ragged grids, the fused kernel on tile multiples
     (24, 16, 6, 3.0, 5.0, 0.5, 0.2, 1, 0.01, 1, 15, 0.0, 1),
-    (64, 32, 6, 3.0, 5.0, 2.0, 0.5, 1, 0.03, 1, 12, 0.0, 1),   # a grid the fused path would take
+    (64, 32, 6, 3.0, 5.0, 2.0, 0.5, 1, 0.03, 1, 12, 0.0, 1),   # fused
     (33, 9, 4, 2.0, 3.0, 0.0, 1.0, 1, 0.05, 1, 10, 0.0, 1),    # Newtonian
+    (64, 16, 8, 4.0, 4.0, 1.0, 0.2, 2, 0.005, 0, 14, 0.0, 1),  # fused, from rest, 52 Q-nodes
+    (64, 32, 6, 3.0, 5.0, 2.0, 0.5, 1, 0.03, 1, 12, 3.1, 1),   # fused, FENE springs
 ]
-FUSED = [c for c in CASES if c[0] % 32 == 0 and c[1] % 8 == 0 and (len(c) < 13 or c[12] == 0)
+FUSED = [c for c in CASES if c[0] % 32 == 0 and c[1] % 8 == 0
          and c[2] * c[2] <= 127]   # the fused kernel holds at most 127 Q-nodes
 FENE = [c for c in CASES if len(c) > 11 and c[11] > 0]
 STRESS = [c for c in CASES if len(c) > 12 and c[12] == 1]
@@ -142,7 +144,7 @@ def test_fp64_matches_oracle(T, oracle_mod, case):
 
 
 @pytest.mark.parametrize("case", [CASES[1], CASES[2], CASES[3], CASES[7], CASES[9], FENE[1],
-                                  STRESS[0], STRESS[1]])
+                                  STRESS[0], STRESS[1], STRESS[3]])
 def test_fp32_within_tolerance(T, oracle_mod, case):
     from paper_2201_10132_gb300.inputs import perturbation
     nx, ny, S, R, re, wi, beta, kp, tau2, ic, steps, fb, qe = _case(case)
@@ -178,7 +180,7 @@ def test_fp32_within_tolerance(T, oracle_mod, case):
     assert abs(diag["qrms_max"] - f["qrms"].max()) <= 2e-5 * max(f["qrms"].max(), 1e-30)
 
 
-@pytest.mark.parametrize("case", [CASES[1], CASES[7], CASES[9]])
+@pytest.mark.parametrize("case", [CASES[1], CASES[7], CASES[9], STRESS[1]])
 def test_fp16_storage_within_tolerance(T, oracle_mod, case):
     """FP16 storage (polymer deviations in half, scaled by a power of two; solvent
     deviations in float; FP32 arithmetic): each stored polymer value is rounded
