@@ -487,6 +487,7 @@ def ensemble_sub(n_runs: int, steps: int, warmup: int):
     the time is the whole step's)."""
     import torch
     from paper_2201_10132_gb300.inputs import ensemble
+    torch.cuda.empty_cache()
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     r = ensemble_throughput(n_runs, steps, warmup)
@@ -499,6 +500,79 @@ def ensemble_sub(n_runs: int, steps: int, warmup: int):
     r["workload"] = f"{n_runs} seeded runs: square grids 128-1024, Re 1-20, Wi 0.1-2, " \
                     f"beta 0.1/0.2/0.5, N_Q = {nq}, FP32"
     return r
+
+
+def slab_sub(W, steps: int, warmup: int, ref_fields: dict, fp32_ms_per_step: float, parts: int = 2):
+    """The throughput workload split into `parts` y-slabs on this one GPU (one run,
+    slab contexts with ghost rows refreshed from the neighbours before every step,
+    device-to-device halo copies on one stream): time per step with the exchange,
+    the exchange alone, its bytes, and whether the owned rows equal the FP32
+    single-domain run after the same number of steps bit for bit."""
+    import numpy as np
+    import torch
+    from paper_2201_10132_gb300 import slabs as S, tfkt
+    from paper_2201_10132_gb300.inputs import perturbation
+    torch.cuda.empty_cache()
+    p = tfkt.Params.from_workload(W, tfkt.FP32)
+    pert = perturbation(W.nx, W.ny, W.seed, W.amp, W.u0)
+    stream = torch.cuda.Stream()
+    sl, bufs, wss = [], [], []
+    for y0, n in S.partition(W.ny, parts):
+        ws = torch.empty(tfkt.slab_required_bytes(p, n), dtype=torch.uint8, device="cuda")
+        s = tfkt.Slab(p, y0, n, S.local_perturbation(pert, y0, n), workspace=ws,
+                      stream=stream.cuda_stream)
+        nb = s.halo_bytes()
+        sl.append(s)
+        wss.append(ws)
+        bufs.append((torch.empty(nb, dtype=torch.uint8, device="cuda"),
+                     torch.empty(nb, dtype=torch.uint8, device="cuda")))
+    del pert
+
+    def step():
+        for s in sl:
+            s.step(1)
+        S.exchange_local(sl, bufs)
+
+    S.exchange_local(sl, bufs)
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    # the exchange alone (it leaves the state unchanged: the ghost rows are already current)
+    e0.record(stream)
+    for _ in range(steps):
+        S.exchange_local(sl, bufs)
+    e1.record(stream)
+    e1.synchronize()
+    xms = e0.elapsed_time(e1) / steps
+    clocks = sampler.stop()
+    same = True
+    for k in SUB_FIELDS:
+        got = np.concatenate([s.owned(s.moments([k])[k]) for s in sl])
+        same = same and bool(np.array_equal(got, ref_fields[k]))
+    nb = sl[0].halo_bytes()
+    for s in sl:
+        s.close()
+    del sl, wss, bufs
+    torch.cuda.empty_cache()
+    nodes = W.nx * W.ny
+    return {"slabs": parts, "ghost_rows_per_side": S.GHOST, "ms_per_step": ms,
+            "value": nodes / (ms / 1e3) / 1e9, "unit": "GLUPS",
+            "exchange_ms_per_step": xms, "halo_bytes_per_side": nb,
+            "exchange_bytes_per_step": 2 * parts * nb,
+            "overhead_vs_single_domain": ms / fp32_ms_per_step - 1,
+            "owned_rows_bit_identical_to_single_domain": same, "steps": steps,
+            "clocks": clocks}
 
 
 def _growth_rate(t, ey2):
@@ -527,6 +601,7 @@ def learned_sub(W, blocks: int = 6, warm: int = 40, grid: int = 512, growth_warm
     from paper_2201_10132_gb300.inputs import perturbation
     vec, meta = train_lpm.load()
     K, thr = meta["K"], meta["threshold"]
+    torch.cuda.empty_cache()
     net = tfkt.Mlp(vec)
     out = {"K": K, "threshold": thr}
     # (1) speed at the full size
@@ -810,7 +885,8 @@ def main():
                 line["fp16"] = fp16_sub(W, args.steps, args.warmup, ms / args.steps,
                                         per["fused"]["ms_per_launch"], ref_fields)
                 sub_launches += line["fp16"]["gpu_launches"]
-                del ref_fields
+            line["slab"] = slab_sub(W, args.steps, args.warmup, ref_fields, ms / args.steps) \
+                if "ux" in (ref_fields or {}) else None
             line["ensemble"] = ensemble_sub(256, 4, 2)
             line["learned"] = learned_sub(W)
             line["gpu_launches_sub_records"] = sub_launches
