@@ -61,7 +61,7 @@ def _run_slabs(T, p, pert, parts, steps):
     return fields, psi, pops, kinds
 
 
-# nx, ny, slabs, precision, steps; S = 6, R = 3 (32 Q-nodes)
+# nx, ny, slabs, precision, steps[, stress quasi-equilibrium]; S = 6, R = 3 (32 Q-nodes)
 CASES = [
     (64, 48, 2, "FP64", 24),     # fused path (tile multiples), two slabs of 24 rows
     (64, 64, 3, "FP64", 21),     # fused, uneven slabs 24 / 24 / 16
@@ -69,14 +69,23 @@ CASES = [
     (70, 45, 3, "FP64", 22),     # two-pass, slabs of 15 rows (not multiples of 8)
     (64, 48, 2, "FP32", 24),
     (64, 48, 3, "FP16", 22),
+    (64, 48, 2, "FP64", 22, True),   # the stress quasi-equilibrium on the fused path
 ]
+
+
+def _params(T, nx, ny, prec, stress=False):
+    if stress:      # momentum relaxation time below 3 beta nu, as the stress model requires
+        return T.Params(nx, ny, 6, 3.0, 5.0, 2.0, 0.5, 0.05, 1, 0.03, 0.0, 1, getattr(T, prec),
+                        0.0, T.QE_STRESS)
+    return T.Params(nx, ny, 6, 3.0, 5.0, 0.5, 0.2, 0.05, 1, ic_mode=1, precision=getattr(T, prec))
 
 
 @pytest.mark.parametrize("case", CASES)
 def test_slabs_in_one_process_are_bit_identical(T, oracle_mod, case):
     from paper_2201_10132_gb300.inputs import perturbation
-    nx, ny, parts, prec, steps = case
-    p = T.Params(nx, ny, 6, 3.0, 5.0, 0.5, 0.2, 0.05, 1, ic_mode=1, precision=getattr(T, prec))
+    nx, ny, parts, prec, steps = case[:5]
+    stress = len(case) > 5 and case[5]
+    p = _params(T, nx, ny, prec, stress)
     pert = perturbation(nx, ny, 9, 0.05, 0.05)
     ref, ref_psi, ref_pops = _single(T, p, pert, steps)
     got, psi, pops, _ = _run_slabs(T, p, pert, parts, steps)
@@ -85,7 +94,8 @@ def test_slabs_in_one_process_are_bit_identical(T, oracle_mod, case):
     assert np.array_equal(psi, ref_psi)
     assert np.array_equal(pops, ref_pops)
     if prec == "FP64":
-        lat = oracle_mod.map_params(nx, ny, 6, 3.0, 5.0, 0.5, 0.2, 0.05, 1)
+        lat = (oracle_mod.map_params(nx, ny, 6, 3.0, 5.0, 2.0, 0.5, 0.05, 1, 0.03, 0.0, 0.0, 1)
+               if stress else oracle_mod.map_params(nx, ny, 6, 3.0, 5.0, 0.5, 0.2, 0.05, 1))
         o = oracle_mod.Oracle(lat)
         o.init(pert, 1)
         o.step(steps)
@@ -110,6 +120,12 @@ def test_slab_rows_and_errors(T):
     for bad in ((0, 7), (48, 8), (-1, 8)):
         with pytest.raises(T.TfktError):
             T.Slab(p, *bad)
+    # the learned block reaches further than one step: not on a slab
+    q = T.Params(64, 48, 6, 3.0, 10.0, 1.0, 0.2, 0.05, 1, precision=T.FP32)
+    with T.Slab(q, 0, 24) as s:
+        with pytest.raises(T.TfktError) as e:
+            T.lpm_run(s, None, 1, K=4, mode=T.LPM_FROZEN)
+        assert e.value.status == 1
 
 
 def _rank_run(rank, world, port, case, out):
