@@ -176,9 +176,11 @@ tfkt_status tfkt_create(const tfkt_params* p, const double* perturb, void* dev_w
 tfkt_status tfkt_step(tfkt_ctx* ctx, int64_t n);
 
 /* Same as tfkt_step, with CUDA events recorded on the context stream around
-   every kernel launch; synchronises at the end and adds the elapsed time of
-   each kernel kind, in milliseconds, to kernel_ms[TFKT_NKERNELS] (host) and
-   the launch counts to launches[TFKT_NKERNELS] (host, may be NULL). */
+   every kernel launch; adds the elapsed time of each kernel kind, in
+   milliseconds, to kernel_ms[TFKT_NKERNELS] (host) and the launch counts to
+   launches[TFKT_NKERNELS] (host, may be NULL). The launches are queued without
+   waiting in between; the host waits for the events once every 64 launches
+   and at the end, so the call returns with the stream idle. */
 tfkt_status tfkt_step_profiled(tfkt_ctx* ctx, int64_t n, double* kernel_ms, int64_t* launches);
 
 /* Macroscopic fields of the current state (see TFKT_F_*: the moments of

@@ -426,25 +426,45 @@ tfkt_status do_step(Ctx* c, int64_t n) {
 // tfkt_step with an event pair around each launch (profiling only).
 template <typename real, typename S>
 tfkt_status do_step_profiled(Ctx* c, int64_t n, double* ms, int64_t* launches) {
-  cudaEvent_t ev[2 * TFKT_NKERNELS];
-  for (auto& e : ev) TFKT_CUDA(c, cudaEventCreate(&e));
+  // An event pair around every launch, recorded without waiting, so that the
+  // launches stay queued back to back as in tfkt_step; the times are read once
+  // per CHUNK launches (and at the end), which is when the host waits.
+  constexpr int CHUNK = 64;
+  cudaEvent_t ev[2 * CHUNK];
+  int created = 0;
   struct Guard {
     cudaEvent_t* e;
+    int* n;
     ~Guard() {
-      for (int k = 0; k < 2 * TFKT_NKERNELS; ++k) cudaEventDestroy(e[k]);
+      for (int k = 0; k < *n; ++k) cudaEventDestroy(e[k]);
     }
-  } guard{ev};
+  } guard{ev, &created};
+  for (; created < 2 * CHUNK; ++created) TFKT_CUDA(c, cudaEventCreate(&ev[created]));
   double acc[TFKT_NKERNELS] = {};
   int64_t cnt[TFKT_NKERNELS] = {};
+  int kinds[CHUNK];
+  int pending = 0;
+  auto drain = [&]() -> tfkt_status {
+    if (pending == 0) return TFKT_OK;
+    TFKT_CUDA(c, cudaEventSynchronize(ev[2 * pending - 1]));
+    for (int k = 0; k < pending; ++k) {
+      float t = 0;
+      TFKT_CUDA(c, cudaEventElapsedTime(&t, ev[2 * k], ev[2 * k + 1]));
+      acc[kinds[k]] += t;
+      ++cnt[kinds[k]];
+    }
+    pending = 0;
+    return TFKT_OK;
+  };
   auto timed = [&](int kind, auto&& launch) -> tfkt_status {
-    TFKT_CUDA(c, cudaEventRecord(ev[2 * kind], c->stream));
+    if (pending == CHUNK) {
+      tfkt_status s = drain();
+      if (s != TFKT_OK) return s;
+    }
+    TFKT_CUDA(c, cudaEventRecord(ev[2 * pending], c->stream));
     TFKT_CUDA(c, launch());
-    TFKT_CUDA(c, cudaEventRecord(ev[2 * kind + 1], c->stream));
-    TFKT_CUDA(c, cudaEventSynchronize(ev[2 * kind + 1]));
-    float t = 0;
-    TFKT_CUDA(c, cudaEventElapsedTime(&t, ev[2 * kind], ev[2 * kind + 1]));
-    acc[kind] += t;
-    ++cnt[kind];
+    TFKT_CUDA(c, cudaEventRecord(ev[2 * pending + 1], c->stream));
+    kinds[pending++] = kind;
     return TFKT_OK;
   };
   for (int64_t k = 0; k < n; ++k) {
@@ -473,6 +493,8 @@ tfkt_status do_step_profiled(Ctx* c, int64_t n, double* ms, int64_t* launches) {
     c->cur ^= 1;
     ++c->step;
   }
+  tfkt_status s = drain();
+  if (s != TFKT_OK) return s;
   for (int j = 0; j < TFKT_NKERNELS; ++j) {
     ms[j] += acc[j];
     if (launches) launches[j] += cnt[j];

@@ -24,14 +24,15 @@
 
 namespace tfkt {
 namespace {
-
 // Exchange buffer: per velocity a plane of (H + 2) rows of HX = TX + 2 cells,
 // the tile plus a one-node zero halo, and two zero rows before the first and
 // after the last plane. A ring node's pull of a velocity that cannot reach it
 // from the tile falls up to two nodes out; in this layout such a read wraps
 // into a halo cell of the same or the neighbouring plane (or the end rows),
 // which all stay zero, so the ring sums need neither masks nor a wider halo.
-// (Keeping shared memory small matters: it leaves the L1 room for the pulls.)
+// Shared memory is kept small: what two blocks leave of the SM's 256 KB is the
+// L1 through which the pulls' global loads return, and the loads in flight
+// need it.
 template <typename real>
 struct Smem {
   real* hb;          // [20][H+2][HX] collided values of the r-moving velocities, zero halo
@@ -39,49 +40,77 @@ struct Smem {
   real* Ar;          // [nq][RING] ring-node arrival sums per Q-node
   real* Ux;          // [H+2][TX+2] velocity on the tile and its ring; shares the
   real* Uy;          // space of A, which is cleared only after its last use
-  const void** pptr; // [nq*25] source plane of each pull in the current source buffer,
-                     // or (lean variant) its element offset as a long long
-  real* delta;       // [nq][DQ] pull shift differences
-  int8_t* tgt;       // [nq][GQ] target Q-node of each Q-displacement group, -1: bounce-back
+  long long* ptab;   // [nq][PQ] per pull: its source plane in the current source buffer, as
+                     // a pointer, or (lean variant) as an element offset
+  real* delta;       // [nq][DG] pull shift difference of each Q-displacement group that
+                     // moves in Q (the same for the group's members; zero where the pull bounces)
+  int* aoff;         // [nq][AQ] per Q-displacement group: byte offset in A of its target
+                     // Q-node's row; a displacement that leaves the disk targets q itself
+  uint32_t* bmask;   // [nq] bit g set when displacement group g leaves the disk
 };
 
+constexpr int PQ = 26;   // per-Q-node stride of the pull table (entry pairs 16-byte aligned)
+constexpr int AQ = 12;   // per-Q-node stride of the target table (three 16-byte loads)
+
 template <typename real, int H>
-__host__ __device__ constexpr size_t smem_layout(int nq, size_t* o_A, size_t* o_Ar, size_t* o_U,
-                                                 size_t* o_poff, size_t* o_delta, size_t* o_tgt) {
+__host__ __device__ constexpr size_t smem_layout(int nq, size_t* o_A, size_t* o_Ar, size_t* o_poff,
+                                                 size_t* o_delta, size_t* o_aoff, size_t* o_bm) {
   size_t o = sizeof(real) * (20 * Geo<H>::HSZ + 2 * HPAD);
   o = (o + 15) & ~(size_t)15;
   *o_A = o;
-  *o_U = o;
   const size_t a_elems = (size_t)nq * Geo<H>::NT, u_elems = 2 * (H + 2) * (TX + 2);
   o += sizeof(real) * (a_elems > u_elems ? a_elems : u_elems);
   *o_Ar = o;
   o += sizeof(real) * (size_t)nq * Geo<H>::RING;
   o = (o + 15) & ~(size_t)15;
   *o_poff = o;
-  o += sizeof(long long) * (size_t)nq * 25;
-  o = (o + 15) & ~(size_t)15;
+  o += sizeof(long long) * (size_t)nq * PQ;
   *o_delta = o;
-  o += sizeof(real) * (size_t)nq * DQ;
+  o += sizeof(real) * (size_t)nq * DG;
   o = (o + 15) & ~(size_t)15;
-  *o_tgt = o;
-  o += (size_t)nq * GQ;
+  *o_aoff = o;
+  o += sizeof(int) * (size_t)nq * AQ;
+  *o_bm = o;
+  o += sizeof(uint32_t) * (size_t)nq;
   return o;
 }
 
 template <typename real, int H>
 __device__ __forceinline__ Smem<real> carve(unsigned char* base, int nq) {
-  size_t oA, oAr, oU, op, od, ot;
-  smem_layout<real, H>(nq, &oA, &oAr, &oU, &op, &od, &ot);
+  size_t oA, oAr, op, od, oa, ob;
+  smem_layout<real, H>(nq, &oA, &oAr, &op, &od, &oa, &ob);
   Smem<real> s;
   s.hb = (real*)base + HPAD;
   s.A = (real*)(base + oA);
   s.Ar = (real*)(base + oAr);
-  s.Ux = (real*)(base + oU);
+  s.Ux = s.A;
   s.Uy = s.Ux + (H + 2) * (TX + 2);
-  s.pptr = (const void**)(base + op);
+  s.ptab = (long long*)(base + op);
   s.delta = (real*)(base + od);
-  s.tgt = (int8_t*)(base + ot);
+  s.aoff = (int*)(base + oa);
+  s.bmask = (uint32_t*)(base + ob);
   return s;
+}
+
+// The four Q-displacement groups of the velocities that move on one Q-axis
+// (1: -Q_y, 3: -Q_x, 5: +Q_x, 7: +Q_y) and the k-th of their four members,
+// all of which also move in r. The r-diagonals with Q at rest (1..4) are
+// group 4 and the Q-diagonals with r at rest (21..24) the corner groups.
+__host__ __device__ constexpr int axis_group(int k) { return 2 * k + 1; }
+// A velocity of Q-displacement group g (g != 4).
+__host__ __device__ constexpr int group_member(int g) {
+  for (int i = 1; i < 25; ++i)
+    if (qgroup(c25(i)) == g) return i;
+  return 0;
+}
+__host__ __device__ constexpr int axis_vel(int g, int k) {
+  int seen = 0;
+  for (int i = 5; i <= 20; ++i)
+    if (qgroup(c25(i)) == g) {
+      if (seen == k) return i;
+      ++seen;
+    }
+  return -1;
 }
 
 // One tile (btx, bty) of an ntx x nty tile grid; shared by the single-run and
@@ -100,6 +129,7 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
                                            unsigned char* smem_raw) {
   constexpr int NT = Geo<H>::NT, RING = Geo<H>::RING, HSZ = Geo<H>::HSZ;
   constexpr int TY = H;     // tile height within this body
+  constexpr uint32_t AROW = NT * sizeof(real);   // bytes of one Q-node row of A (a power of two)
   const int nq = a.nq;
   Smem<real> sm = carve<real, H>(smem_raw, nq);
   const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * TX + lx;
@@ -125,17 +155,26 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
   const uint32_t n = off[4];
 
   // ---- stage: tables, zeroed accumulators and exchange halo, U on the tile and its ring
-  for (int k = tid; k < nq * GQ; k += NT) {
-    const int q = k / GQ, g = k % GQ;
-    sm.tgt[k] = (int8_t)(g < 9 ? fa.tgt[q * 9 + g] : -1);
+  for (int k = tid; k < nq; k += NT) {
+    uint32_t m = 0;
+    for (int g = 0; g < 9; ++g)
+      if (fa.tgt[k * 9 + g] < 0) m |= 1u << g;
+    sm.bmask[k] = m;
   }
-  for (int k = tid; k < nq * 25; k += NT) {
-    if constexpr (LEAN) reinterpret_cast<long long*>(sm.pptr)[k] = fa.poff[k];
-    else sm.pptr[k] = src + fa.poff[k];
+  for (int k = tid; k < nq * AQ; k += NT) {
+    const int q = k / AQ, g = k % AQ;
+    const int t = g < 9 ? fa.tgt[q * 9 + g] : -1;
+    sm.aoff[k] = (t >= 0 ? t : q) * (int)AROW;
   }
-  for (int k = tid; k < nq * DQ; k += NT) {
-    const int q = k / DQ, i = k % DQ;
-    sm.delta[k] = i < 25 ? a.tab.delta[q * 25 + i] : real(0);
+  for (int k = tid; k < nq * PQ; k += NT) {
+    const int q = k / PQ, i = k % PQ;
+    const long long e = i < 25 ? fa.poff[q * 25 + i] : 0;
+    if constexpr (LEAN) sm.ptab[k] = e;
+    else sm.ptab[k] = reinterpret_cast<long long>(src + e);
+  }
+  for (int k = tid; k < nq * DG; k += NT) {
+    const int q = k / DG, s = k % DG;
+    sm.delta[k] = a.tab.delta[q * 25 + group_member(s < 4 ? s : s + 1)];
   }
   for (int k = tid; k < 20 * HSZ + 2 * HPAD; k += NT) sm.hb[k - HPAD] = real(0);
   for (int k = tid; k < nq * RING; k += NT) sm.Ar[k] = real(0);
@@ -171,27 +210,23 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
   real jx_arr = 0, jy_arr = 0, ms_arr = 0;    // own-node arrivals (momentum, solvent mass)
   real jx_r = 0, jy_r = 0, ms_r = 0;          // ring-node arrivals
 
-  // Bounce-back mask of Q-node q: bit g set when q + displacement g leaves the disk.
-  auto bounce_mask = [&](int q) {
-    int tv[GQ];
-    load_targets(tv, sm.tgt + q * GQ);
-    uint32_t m = 0;
-#pragma unroll
-    for (int g = 0; g < 9; ++g)
-      if (tv[g] < 0) m |= 1u << g;
-    return m;
+  // The pull table's entries of Q-node q for velocities i and i + 1 (i even).
+  auto entry_pair = [&](int q, int i) {
+    return *reinterpret_cast<const longlong2*>(sm.ptab + q * PQ + i);
   };
-  // Source address of the pull of velocity i at Q-node q (bm: that Q-node's
-  // mask); the pull bounces when q - Qdot_i leaves the disk, the opposite group 8 - g.
-  auto pull_offset = [&](auto I, int q, uint32_t bm) {
+  // Source address of the pull of velocity i at a Q-node whose table entry is e
+  // and whose bounce mask is bm. The pull bounces when q - Qdot_i leaves the disk
+  // (the opposite group 8 - g): the entry then names the opposite velocity's
+  // plane, and the source is the node itself. The r-diagonals never bounce.
+  auto pull_addr = [&](auto I, long long e, uint32_t bm) -> const S* {
     constexpr int i = decltype(I)::value;
     constexpr V4 cv = c25(i);
     uint32_t o = off[shift_index(-cv.rx, -cv.ry)];
-    if constexpr (moves_r(i)) {
+    if constexpr (moves_r(i) && qgroup(cv) != 4) {
       if ((bm >> (8 - qgroup(cv))) & 1u) o = off[4];
     }
-    if constexpr (LEAN) return src + (reinterpret_cast<const long long*>(sm.pptr)[q * 25 + i] + o);
-    else return (const S*)sm.pptr[q * 25 + i] + o;
+    if constexpr (LEAN) return src + (e + o);
+    else return reinterpret_cast<const S*>(e) + o;
   };
   // The populations of a Q-node are loaded one Q-node ahead: register h[i] is
   // refilled for Q-node q + 1 as soon as the collision of Q-node q has used it,
@@ -202,11 +237,21 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
   constexpr bool RAW = std::is_same<S, real>::value;
   S hr[25];
   real h[25], mn[4];
+  long long e_odd = 0;   // the second entry of the last pair read from the pull table
   if (nq > 0) {
-    const uint32_t bm0 = bounce_mask(0);
+    const uint32_t bm0 = sm.bmask[0];
     static_for<0, 25>([&](auto I) {
-      if constexpr (RAW) h[decltype(I)::value] = *pull_offset(I, 0, bm0);
-      else hr[decltype(I)::value] = *pull_offset(I, 0, bm0);
+      constexpr int i = decltype(I)::value;
+      long long e;
+      if constexpr (i % 2 == 0) {
+        const longlong2 pr = entry_pair(0, i);
+        e = pr.x;
+        e_odd = pr.y;
+      } else {
+        e = e_odd;
+      }
+      if constexpr (RAW) h[i] = *pull_addr(I, e, bm0);
+      else hr[i] = *pull_addr(I, e, bm0);
     });
     mn[0] = Min[off[5]];
     mn[1] = Min[off[3]];
@@ -315,18 +360,24 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
     B3 = fa.rshp[3 * P + n];
     rpt0 = real(1) / a.psi_tot0;
   }
+  char* const Acol = reinterpret_cast<char*>(sm.A) + tid * sizeof(real);
 
   // ---- polymer, one Q-node at a time
   for (int q = 0; q < nq; ++q) {
-    const uint32_t bm = bounce_mask(q);
+    const uint32_t bm = sm.bmask[q];
     {
-      real dl[DQ];
-      load_vec<DQ>(dl, sm.delta + q * DQ);
-#pragma unroll
-      for (int i = 0; i < 25; ++i) {   // unscale (FP16 storage), shift to this Q-node
-        if constexpr (RAW) h[i] += dl[i];
-        else h[i] = from_store<real>(hr[i]) * a.pinv + dl[i];
-      }
+      real dl[DG];
+      load_vec<DG>(dl, sm.delta + q * DG);
+      static_for<0, 25>([&](auto I) {   // unscale (FP16 storage), shift to this Q-node
+        constexpr int i = I, g = qgroup(c25(i));
+        if constexpr (g == 4) {
+          if constexpr (!RAW) h[i] = from_store<real>(hr[i]) * a.pinv;
+        } else {
+          constexpr int sl = g < 4 ? g : g - 1;
+          if constexpr (RAW) h[i] += dl[sl];
+          else h[i] = from_store<real>(hr[i]) * a.pinv + dl[sl];
+        }
+      });
     }
     if constexpr (RESHAPE) {
       // added as the linear quasi-equilibrium w_i [dpsi + 3 (v_i . dpsi U + Qdot_i . dpsi
@@ -349,7 +400,7 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
     const real dpx = real(0.5) * (mn[0] - mn[1]);
     const real dpy = real(0.5) * (mn[2] - mn[3]);
     const bool more = q + 1 < nq;
-    const uint32_t bmn = more ? bounce_mask(q + 1) : 0u;
+    const uint32_t bmn = more ? sm.bmask[q + 1] : 0u;
     if (more) {
       const real* Mq = Min + (size_t)(q + 1) * P;
       mn[0] = Mq[off[5]];
@@ -447,6 +498,8 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
     }
     const real wdpsi = tw * dpsi;
     S* dq = dst + (size_t)(9 + 25 * q) * P + n;
+    // post-collision values that stay on this r-node, per Q-displacement group
+    // (rest velocity and Q-diagonals; a group that leaves the disk targets q)
     real grp[9];
 #pragma unroll
     for (int g = 0; g < 9; ++g) grp[g] = real(0);
@@ -474,63 +527,89 @@ __device__ __forceinline__ void fused_body(const KernelArgs<real>& a, const Fuse
       const real hp = a.om2b * h[i] + d;
       if constexpr (std::is_same<S, real>::value) dq[(size_t)i * P] = hp;
       else dq[(size_t)i * P] = to_store<S>(hp * a.pscale);
-      constexpr int g = qgroup(c25(i));
-      const bool b = (bm >> g) & 1u;
-      if constexpr (!moves_r(i)) {
-        // stays at this r-node: lands on Q-node q + Qdot, or bounces back to q
-        if constexpr (g == 4) grp[4] += hp;
-        else {
-          grp[4] += b ? hp : real(0);
-          grp[g] += b ? real(0) : hp;
+      // an r-moving value goes through the exchange buffer (whether it bounces is
+      // settled where the arrivals are summed); the others stay on this r-node
+      if constexpr (moves_r(i)) sm.hb[(i - 1) * HSZ + hcell] = hp;
+      else grp[qgroup(c25(i))] += hp;
+      if (more) {
+        long long e;
+        if constexpr (i % 2 == 0) {
+          const longlong2 pr = entry_pair(q + 1, i);
+          e = pr.x;
+          e_odd = pr.y;
+        } else {
+          e = e_odd;
         }
-      } else {
-        // a bounced value returns to (r, q) moving with -c; it is not exchanged
-        const real back = b ? hp : real(0);
-        sm.hb[(i - 1) * HSZ + hcell] = b ? real(0) : hp;
-        grp[4] += back;
-        acc<-c25(i).rx>(jx_arr, back);
-        acc<-c25(i).ry>(jy_arr, back);
-      }
-      if constexpr (RAW) {
-        if (more) h[i] = *pull_offset(I, q + 1, bmn);
-      } else {
-        if (more) hr[i] = *pull_offset(I, q + 1, bmn);
+        if constexpr (RAW) h[i] = *pull_addr(I, e, bmn);
+        else hr[i] = *pull_addr(I, e, bmn);
       }
     });
     __syncthreads();
-    // arrivals from the other r-nodes of the tile
-    static_for<1, 20>([&](auto I) {
+    // arrivals from the other r-nodes of the tile. A Q-axis group whose
+    // displacement leaves the disk bounces back: its values stay on their own
+    // r-node (and Q-node) with the r-velocity reversed, so the node takes its own
+    // values of that group, with negated momentum, and no neighbour's.
+    static_for<1, 4>([&](auto I) {   // r-diagonals, Q at rest (group 4): never bounce
       constexpr int i = I;
       constexpr V4 cv = c25(i);
       const real v = sm.hb[(i - 1) * HSZ + hcell - (cv.ry * HX + cv.rx)];
-      grp[qgroup(cv)] += v;
+      grp[4] += v;
       acc<cv.rx>(jx_arr, v);
       acc<cv.ry>(jy_arr, v);
     });
-    int tq[GQ];
-    load_targets(tq, sm.tgt + q * GQ);
+    static_for<0, 4>([&](auto GI) {
+      constexpr int g = axis_group(GI);
+      if ((bm >> g) & 1u) {
+        static_for<0, 4>([&](auto K) {
+          constexpr int i = axis_vel(g, K);
+          constexpr V4 cv = c25(i);
+          const real v = sm.hb[(i - 1) * HSZ + hcell];
+          grp[g] += v;
+          acc<-cv.rx>(jx_arr, v);
+          acc<-cv.ry>(jy_arr, v);
+        });
+      } else {
+        static_for<0, 4>([&](auto K) {
+          constexpr int i = axis_vel(g, K);
+          constexpr V4 cv = c25(i);
+          const real v = sm.hb[(i - 1) * HSZ + hcell - (cv.ry * HX + cv.rx)];
+          grp[g] += v;
+          acc<cv.rx>(jx_arr, v);
+          acc<cv.ry>(jy_arr, v);
+        });
+      }
+    });
+    int to[AQ];
+    load_vec<AQ>(to, sm.aoff + q * AQ);
 #pragma unroll
-    for (int g = 0; g < 9; ++g) {
-      const int t = g == 4 ? q : tq[g];
-      if (t >= 0) sm.A[t * NT + tid] += grp[g];
-    }
+    for (int g = 0; g < 9; ++g) *reinterpret_cast<real*>(Acol + to[g]) += grp[g];
     if (ring_thread) {
-      real gr[9];
-#pragma unroll
-      for (int g = 0; g < 9; ++g) gr[g] = real(0);
-      static_for<1, 20>([&](auto I) {
+      // a ring node takes the tile's values of the groups that do not bounce
+      real g4 = 0;
+      static_for<1, 4>([&](auto I) {
         constexpr int i = I;
         constexpr V4 cv = c25(i);
         const real v = sm.hb[(i - 1) * HSZ + rcell - (cv.ry * HX + cv.rx)];
-        gr[qgroup(cv)] += v;
+        g4 += v;
         acc<cv.rx>(jx_r, v);
         acc<cv.ry>(jy_r, v);
       });
-#pragma unroll
-      for (int g = 0; g < 9; ++g) {
-        const int t = g == 4 ? q : tq[g];
-        if (t >= 0) sm.Ar[t * RING + tid] += gr[g];
-      }
+      sm.Ar[q * RING + tid] += g4;
+      static_for<0, 4>([&](auto GI) {
+        constexpr int g = axis_group(GI);
+        if (!((bm >> g) & 1u)) {
+          real s = 0;
+          static_for<0, 4>([&](auto K) {
+            constexpr int i = axis_vel(g, K);
+            constexpr V4 cv = c25(i);
+            const real v = sm.hb[(i - 1) * HSZ + rcell - (cv.ry * HX + cv.rx)];
+            s += v;
+            acc<cv.rx>(jx_r, v);
+            acc<cv.ry>(jy_r, v);
+          });
+          sm.Ar[((uint32_t)to[g] / AROW) * RING + tid] += s;
+        }
+      });
     }
     __syncthreads();
   }
@@ -578,6 +657,7 @@ step_fused_kernel(KernelArgs<real> a, FusedArgs<real> fa) {
   fused_body<real, S, RESHAPE, TY, false, STRESS>(a, fa, blockIdx.x, blockIdx.y, gridDim.x,
                                                   gridDim.y, smem_raw);
 }
+
 
 // Completes the border nodes of every tile: own partial sums plus the ring
 // exports of the neighbouring tiles (left, right, down, up, then the four
@@ -790,8 +870,7 @@ size_t fused_export_capacity(int nx, int ny, int nq) {
 }
 
 bool fused_supported(int nx, int ny, int nq, size_t real_bytes, int ty) {
-  // nq <= 127: the target table holds Q-node indices in signed bytes
-  return nx % TX == 0 && ny % ty == 0 && nq <= 127 &&
+  return nx % TX == 0 && ny % ty == 0 &&
          fused_smem_bytes(nq, real_bytes, ty) <= 227 * 1024;
 }
 

@@ -1,5 +1,4 @@
-// Helpers shared by the fused single-pass step kernels (tfkt_fused.cu: one node
-// per thread; tfkt_fused_pair.cu: two x-adjacent nodes per thread): compile-time
+// Helpers of the fused single-pass step kernels (tfkt_fused.cu): compile-time
 // loops, the tile geometry and its ring of border nodes, D4Q25 velocity
 // properties, and the mixture velocity of a node from the moment planes.
 #pragma once
@@ -115,20 +114,11 @@ __device__ __forceinline__ void load_vec(T* out, const T* src) {
   }
 }
 
-// The GQ = 16 signed bytes of a Q-node's target table, from one 16-byte load.
-__device__ __forceinline__ void load_targets(int* out, const int8_t* src) {
-  const int4 v = *reinterpret_cast<const int4*>(src);
-  const int w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-  for (int k = 0; k < 16; ++k) out[k] = (int)(int8_t)(w[k >> 2] >> (8 * (k & 3)));
-}
-
-// Exchange buffer constants of the one-node-per-thread kernel (its layout is
-// described where the buffer is carved) and the strides of the per-Q-node tables.
+// Exchange buffer constants of the fused kernel (its layout is described where
+// the buffer is carved) and the size of the per-Q-node shift table.
 constexpr int HX = TX + 2;
 constexpr int HPAD = 2 * HX;     // zero cells before the first and after the last plane
-constexpr int DQ = 28;           // per-Q-node stride of the shift table (vector loads)
-constexpr int GQ = 16;           // per-Q-node stride of the target table (bytes, one vector load)
+constexpr int DG = 8;            // per-Q-node entries of the shift table: the groups that move in Q
 
 template <typename real>
 __device__ __forceinline__ void velocity_at(const KernelArgs<real>& a, const real* M, int x, int y,
