@@ -13,10 +13,14 @@
 // than an interior node). Every owned row is then computed exactly as in the
 // whole run, provided the ghost rows are overwritten with the neighbours'
 // current rows (current populations and moment planes) before each step. The
-// exchange moves G rows of every plane per side; packing and unpacking are
-// strided copies on the context's stream.
+// exchange moves G rows of every plane per side: G rows of a plane are one
+// contiguous chunk, and the message is the chunks back to back. Packing and
+// unpacking run on the context's stream, as one gather or scatter kernel when
+// the message is in device memory and as strided copies when it is on the host.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cstdint>
 #include <string>
 
 #include "tfkt_internal.cuh"
@@ -71,6 +75,36 @@ Blocks halo_blocks(const Ctx* c) {
   return b;
 }
 
+// Moves the chunks of a halo message between the workspace and the message
+// (pack: workspace -> message) in 16-byte words. Chunk sizes, offsets and plane
+// strides are multiples of 16 bytes (rows are padded to 32 elements).
+struct ChunkSet {
+  size_t off[3], stride[3];   // byte offset of plane 0's chunk, plane stride (bytes)
+  uint32_t words[3];          // 16-byte words per chunk
+  uint32_t first[3];          // first message word of each block
+  uint32_t total;             // words of the message (< 2^31)
+  int n;
+};
+
+__global__ void __launch_bounds__(256) halo_copy_kernel(int4* __restrict__ ws, int4* __restrict__ msg,
+                                                        ChunkSet cs, int pack) {
+  for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < cs.total; u += gridDim.x * blockDim.x) {
+    // the block of word u, selected with constant indices (the arguments stay in
+    // the parameter space)
+    const bool b2 = cs.n > 2 && u >= cs.first[2];
+    const bool b1 = !b2 && cs.n > 1 && u >= cs.first[1];
+    const uint32_t first = b2 ? cs.first[2] : (b1 ? cs.first[1] : cs.first[0]);
+    const uint32_t words = b2 ? cs.words[2] : (b1 ? cs.words[1] : cs.words[0]);
+    const size_t off = b2 ? cs.off[2] : (b1 ? cs.off[1] : cs.off[0]);
+    const size_t stride = b2 ? cs.stride[2] : (b1 ? cs.stride[1] : cs.stride[0]);
+    const uint32_t v = u - first;
+    const uint32_t p = v / words, w = v - p * words;
+    int4* cell = ws + (off + (size_t)p * stride) / 16 + w;
+    if (pack) msg[u] = *cell;
+    else *cell = msg[u];
+  }
+}
+
 size_t halo_bytes(const Ctx* c) {
   const Blocks b = halo_blocks(c);
   size_t t = 0;
@@ -92,6 +126,30 @@ tfkt_status check_slab(Ctx* c, int32_t side, const void* buf, size_t bytes) {
 // to (pack) or from (unpack) a message buffer.
 tfkt_status move_rows(Ctx* c, int r0, void* msg, bool pack, bool msg_on_device) {
   const Blocks b = halo_blocks(c);
+  // (below 2^31 words, so that the kernel's 32-bit word index cannot wrap)
+  if (msg_on_device && halo_bytes(c) / 16 < ((size_t)1 << 31)) {
+    ChunkSet cs{};
+    cs.n = b.n;
+    size_t first = 0;
+    for (int k = 0; k < b.n; ++k) {
+      const size_t width = (size_t)G * b.bytes_per_row[k];
+      cs.off[k] = b.off[k] + (size_t)r0 * b.bytes_per_row[k];
+      cs.stride[k] = b.stride[k];
+      cs.words[k] = (uint32_t)(width / 16);
+      cs.first[k] = (uint32_t)first;
+      first += (size_t)b.planes[k] * cs.words[k];
+    }
+    cs.total = (uint32_t)first;
+    if (((uintptr_t)msg & 15) != 0) return fail(TFKT_EINVAL, "device message not 16-byte aligned");
+    const int blocks = (int)std::min<size_t>((first + 255) / 256, (size_t)152 * 8);
+    halo_copy_kernel<<<blocks, 256, 0, c->stream>>>((int4*)c->ws.base, (int4*)msg, cs, pack ? 1 : 0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      c->poisoned = true;
+      return fail(TFKT_ECUDA, std::string("halo copy: ") + cudaGetErrorString(e));
+    }
+    return TFKT_OK;
+  }
   char* ws = (char*)c->ws.base;
   char* m = (char*)msg;
   const cudaMemcpyKind kind = msg_on_device ? cudaMemcpyDeviceToDevice

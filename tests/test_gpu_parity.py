@@ -103,6 +103,25 @@ def test_path_dispatch(T, case):
         assert k == {"moments": 3, "step": 4, "fused": 0, "fixup": 0}
 
 
+def test_step_profiled_over_several_event_chunks(T):
+    """tfkt_step_profiled reads its events once every 64 launches: 45 fused steps
+    (90 launches, two chunks) count every launch, time each one, and leave the same
+    state as tfkt_step."""
+    p = T.Params(64, 32, 6, 3.0, 5.0, 0.5, 0.2, 0.05, 1, 0.0, 0.0, 1, T.FP64)
+    ms = np.zeros(len(T.KERNELS))
+    n = np.zeros(len(T.KERNELS), np.int64)
+    with T.Solver(p) as a, T.Solver(p) as b:
+        a.step_profiled(45, ms, n)
+        b.step(45)
+        fa, fb = a.moments(), b.moments()
+    k = dict(zip(T.KERNELS, n.tolist()))
+    assert k == {"moments": 0, "step": 0, "fused": 45, "fixup": 45}
+    t = dict(zip(T.KERNELS, ms.tolist()))
+    assert t["fused"] > 0 and t["fixup"] > 0 and t["moments"] == 0 and t["step"] == 0
+    for name in fa:
+        assert np.array_equal(fa[name], fb[name]), name
+
+
 @pytest.mark.parametrize("case", CASES)
 def test_fp64_matches_oracle(T, oracle_mod, case):
     from paper_2201_10132_gb300.inputs import perturbation
