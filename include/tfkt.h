@@ -393,10 +393,12 @@ tfkt_status tfkt_slab_create(const tfkt_params* p, int32_t y0, int32_t ny_local,
 tfkt_status tfkt_slab_halo_bytes(const tfkt_ctx* ctx, size_t* bytes);
 
 /* Copy the TFKT_SLAB_GHOST owned rows next to `side` of the current state into
-   dst (bytes >= tfkt_slab_halo_bytes; device memory if dst_is_device, else host
-   memory, owned by the caller). Device copies are queued on the context stream;
-   host copies synchronise it. Errors: EINVAL for a non-slab context, an unknown
-   side, NULL or too small dst; ECUDA (context poisoned) if a copy fails. */
+   dst (bytes >= tfkt_slab_halo_bytes; device memory if dst_is_device, 16-byte
+   aligned, else host memory; owned by the caller). A device message is written
+   by one kernel queued on the context stream; host copies synchronise it.
+   Errors: EINVAL for a non-slab context, an unknown side, NULL or too small dst,
+   or a device dst that is not 16-byte aligned; ECUDA (context poisoned) if a
+   copy fails. */
 tfkt_status tfkt_slab_halo_pack(tfkt_ctx* ctx, int32_t side, void* dst, size_t bytes,
                                 int dst_is_device);
 
