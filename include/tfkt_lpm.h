@@ -9,7 +9,7 @@
  *     of every node K steps later from the conformation of the parcel that
  *     arrives there (C interpolated at r - K U) and the velocity-gradient
  *     stencil; the plain step's own rate of change of C, carried over the K
- *     steps, judges it tile by tile, and a tile whose largest disagreement
+ *     steps, checks it tile by tile, and a tile whose largest disagreement
  *     exceeds the threshold keeps the plain step's conformation instead;
  *  3. K solvent-only steps under the polymer stress (H/2) psi_tot C of the
  *     conformation interpolated linearly in time (Sec. III, Eq. IDef), the
@@ -87,7 +87,7 @@ tfkt_status tfkt_mlp_adam(tfkt_mlp* net, float lr, float beta1, float beta2, flo
 /* Options of the learned block. */
 typedef struct {
   int32_t K;          /* solvent sub-steps per block: even, 2 <= K <= 64 */
-  int32_t tile;       /* side of the judge's tiles, 1 <= tile <= 64 */
+  int32_t tile;       /* side of the check's tiles, 1 <= tile <= 64 */
   float threshold;    /* largest |C_net - C_plain| / c_e a tile may show */
   int32_t mode;       /* TFKT_LPM_NET, or TFKT_LPM_FROZEN: every tile keeps the plain
                          step's conformation (the block without the network) */

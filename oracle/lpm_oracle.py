@@ -19,7 +19,7 @@ steps:
     order dy, dx, then dU_x/dx, dU_y/dx, dU_x/dy, dU_y/dy), and K / lambda_H.
     A multilayer perceptron 40 -> 64 -> 64 -> 3 (GELU, BF16 weights, FP32
     biases) predicts o = (C(t + 1 + K) - C_dep) / c_e: C_new = C_dep + c_e o.
- 4. Judge and fallback: per node e = max_ab |C_new - C(t + 1) - K r| / c_e,
+ 4. Check and fallback: per node e = max_ab |C_new - C(t + 1) - K r| / c_e,
     the network's change against the plain update's rate carried over the K
     steps; every T x T tile whose largest e exceeds the threshold keeps the
     plain update's C(t + 1) (no learned change) on all its nodes instead.
@@ -334,7 +334,7 @@ def conformation(f):
 # ---------------------------------------------------------------- the block
 def block(s: Setup, o: O.Oracle, P, mode: str = "mlp"):
     """Advance the C-oracle state o by one block of 1 + K steps. mode: "mlp" (network,
-    judge and fallback), "frozen" (C_new = C(t + 1) on every tile: the plain update
+    check and fallback), "frozen" (C_new = C(t + 1) on every tile: the plain update
     alone, the method without the network), "plain" (K more plain steps).
     Returns info (flagged tiles, indicator per tile, features)."""
     C_t = conformation(o.fields())

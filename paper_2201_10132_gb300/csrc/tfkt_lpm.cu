@@ -1,6 +1,6 @@
 // Learned polymer macro-step (the paper has no learned component; the block
 // is built on the scheme of Sec. VI): one plain step, the network's
-// conformation K steps ahead judged tile by tile against the plain step's
+// conformation K steps ahead checked tile by tile against the plain step's
 // rate, K solvent-only sub-steps under the interpolated polymer stress, and
 // an equilibrium-shaped increment that moves the polymer populations to the
 // predicted conformation. FP32, Hookean springs, fused-path contexts.
@@ -159,7 +159,7 @@ __device__ __forceinline__ void node_features(const KernelArgs<float>& a, const 
   f[39] = K * l.inv_lambda;
 }
 
-// One block per judge tile: the network's C_new for every node, the tile's
+// One block per check tile: the network's C_new for every node, the tile's
 // largest disagreement with the plain rate, and the fallback.
 //
 // The network runs on the fifth-generation tensor cores (tcgen05): the block is
