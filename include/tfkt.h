@@ -44,7 +44,9 @@ typedef enum {
   TFKT_ECUDA = 3,   /* a CUDA call failed; the context is now poisoned */
   TFKT_ENAN = 4,    /* diagnostics found a non-finite value; state kept */
   TFKT_ESTATE = 5,  /* the context was poisoned by an earlier CUDA error */
-  TFKT_EIO = 6      /* a checkpoint file could not be written or read, or is corrupt */
+  TFKT_EIO = 6,     /* a checkpoint file could not be written or read, or is corrupt */
+  TFKT_ETIMEOUT = 7 /* a bounded wait inside a kernel ran out; the kernel gave up cleanly,
+                       the affected work took its documented fallback, state kept */
 } tfkt_status;
 
 typedef enum {

@@ -91,16 +91,22 @@ typedef struct {
   float threshold;    /* largest |C_net - C_plain| / c_e a tile may show */
   int32_t mode;       /* TFKT_LPM_NET, or TFKT_LPM_FROZEN: every tile keeps the plain
                          step's conformation (the block without the network) */
+  int32_t inject_wait_timeout; /* fault injection for tests, normally 0: nonzero makes
+                         the network kernel issue no tensor-core work, so that its
+                         waits for it run out after a few polls (TFKT_ETIMEOUT) */
 } tfkt_lpm_opts;
 enum { TFKT_LPM_NET = 0, TFKT_LPM_FROZEN = 1 };
 
-/* Run nblocks >= 0 blocks (asynchronous on the context's stream). The context
-   must be FP32, Hookean (fene_b = 0), with polymer, and on the fused path (nx a
-   multiple of 32, ny of 8); net may be NULL in TFKT_LPM_FROZEN mode.
-   flagged: host int64, if not NULL receives the number of tiles that fell
-   back, summed over the blocks (this synchronises the stream). Scratch
-   (about 18 planes of ny * pitch floats) is allocated on first use and freed
-   with the context. EINVAL for unsupported contexts or options. */
+/* Run nblocks >= 0 blocks on the context's stream and synchronise it at the
+   end. The context must be FP32, Hookean (fene_b = 0), with polymer, and on
+   the fused path (nx a multiple of 32, ny of 8); net may be NULL in
+   TFKT_LPM_FROZEN mode. flagged: host int64, if not NULL receives the number
+   of tiles that fell back, summed over the blocks. Scratch (about 18 planes of
+   ny * pitch floats) is allocated on first use and freed with the context.
+   Errors: EINVAL for unsupported contexts or options; ETIMEOUT when a wait of
+   the network kernel for its tensor-core work ran out (bounded; the tiles
+   concerned fell back to the plain step, so the state is that of a valid
+   block and the context stays usable); ECUDA if a launch fails. */
 tfkt_status tfkt_lpm_run(tfkt_ctx* c, const tfkt_mlp* net, const tfkt_lpm_opts* opts,
                          int64_t nblocks, int64_t* flagged);
 

@@ -840,6 +840,7 @@ const char* tfkt_status_string(tfkt_status s) {
     case TFKT_ENAN: return "non-finite value";
     case TFKT_ESTATE: return "context poisoned";
     case TFKT_EIO: return "checkpoint file error";
+    case TFKT_ETIMEOUT: return "bounded wait ran out";
   }
   return "unknown status";
 }

@@ -34,6 +34,7 @@ struct LpmArgs {
   float l2, hl2h, H, tau2, kappa, inv_lambda;
   int K, tile, mode;
   float threshold;
+  int inject_wait_timeout;  // fault injection: no tensor-core work, waits bounded to a few polls
 };
 
 __device__ __forceinline__ int wrap_i(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
@@ -278,6 +279,9 @@ __global__ void __launch_bounds__(NET_THREADS) net_kernel(KernelArgs<float> a, L
   __nv_bfloat16* alo = s.act[g][1];
   const uint32_t ahi_a = umma::smem_addr(ahi), alo_a = umma::smem_addr(alo);
   const uint32_t w1_a = umma::smem_addr(s.w1), w2_a = umma::smem_addr(s.w2);
+  // fault injection (tests): no MMA is issued, so no wait can complete
+  const bool issue = !l.inject_wait_timeout;
+  const uint32_t polls = issue ? NET_MAX_POLLS : 64u;
   uint32_t phase = 0;
   bool failed = false;
   float worst = 0.f;
@@ -302,7 +306,7 @@ __global__ void __launch_bounds__(NET_THREADS) net_kernel(KernelArgs<float> a, L
     umma::fence_proxy_async();
     umma::fence_before_sync();
     umma::bar_sync(1 + g, 128);
-    if (r == 0) {
+    if (r == 0 && issue) {
       umma::fence_after_sync();
       for (int ks = 0; ks < NET_K1 / 16; ++ks) {
         const uint64_t bd = umma::desc_kmajor(w1_a + 256u * ks, 128u, NET_SBO1);
@@ -313,7 +317,7 @@ __global__ void __launch_bounds__(NET_THREADS) net_kernel(KernelArgs<float> a, L
       }
       umma::commit(&s.mbar[g]);
     }
-    const bool done1 = umma::mbar_wait(&s.mbar[g], phase, NET_MAX_POLLS);
+    const bool done1 = umma::mbar_wait(&s.mbar[g], phase, polls);
     phase ^= 1u;
     umma::fence_after_sync();
     float h[NH];
@@ -334,7 +338,7 @@ __global__ void __launch_bounds__(NET_THREADS) net_kernel(KernelArgs<float> a, L
     umma::fence_proxy_async();
     umma::fence_before_sync();
     umma::bar_sync(1 + g, 128);
-    if (r == 0) {
+    if (r == 0 && issue) {
       umma::fence_after_sync();
       for (int ks = 0; ks < NH / 16; ++ks) {
         const uint64_t bd = umma::desc_kmajor(w2_a + 256u * ks, 128u, NET_SBO2);
@@ -345,7 +349,7 @@ __global__ void __launch_bounds__(NET_THREADS) net_kernel(KernelArgs<float> a, L
       }
       umma::commit(&s.mbar[g]);
     }
-    const bool done2 = umma::mbar_wait(&s.mbar[g], phase, NET_MAX_POLLS);
+    const bool done2 = umma::mbar_wait(&s.mbar[g], phase, polls);
     phase ^= 1u;
     umma::fence_after_sync();
     float o[NOUT] = {s.b3[0], s.b3[1], s.b3[2]};
@@ -384,7 +388,7 @@ __global__ void __launch_bounds__(NET_THREADS) net_kernel(KernelArgs<float> a, L
     // the tile falls back; before the TMEM is freed, wait (again bounded) for the
     // group's last MMAs to complete
     worst = __int_as_float(0x7f800000);
-    if (r == 0) umma::mbar_wait(&s.mbar[g], phase ^ 1u, NET_MAX_POLLS);
+    if (r == 0) umma::mbar_wait(&s.mbar[g], phase ^ 1u, polls);
   }
   red[tid] = worst;
   __syncthreads();
@@ -696,6 +700,7 @@ extern "C" tfkt_status tfkt_lpm_run(tfkt_ctx* cc, const tfkt_mlp* net, const tfk
   l.tile = o->tile;
   l.mode = o->mode;
   l.threshold = o->threshold;
+  l.inject_wait_timeout = o->inject_wait_timeout != 0;
   if ((s = ctx_ensure_moments_f32(c)) != TFKT_OK) return s;
   const Lattice& L = c->L;
   cudaStream_t st = c->stream;
@@ -734,15 +739,13 @@ extern "C" tfkt_status tfkt_lpm_run(tfkt_ctx* cc, const tfkt_mlp* net, const tfk
     c->step += o->K;
     c->lpm_step = c->step;
   }
-  if (flagged) {
-    int h[2] = {0, 0};
-    LPM_CUDA(cudaMemcpyAsync(h, l.counter, sizeof(h), cudaMemcpyDeviceToHost, st));
-    LPM_CUDA(cudaStreamSynchronize(st));
-    *flagged = h[0];
-    if (h[1])
-      return fail(TFKT_ECUDA, "a tensor-core wait of the network kernel timed out "
-                              "(the affected tiles fell back to the plain step)");
-  }
+  int h[2] = {0, 0};
+  LPM_CUDA(cudaMemcpyAsync(h, l.counter, sizeof(h), cudaMemcpyDeviceToHost, st));
+  LPM_CUDA(cudaStreamSynchronize(st));
+  if (flagged) *flagged = h[0];
+  if (h[1])
+    return fail(TFKT_ETIMEOUT, "a tensor-core wait of the network kernel ran out "
+                               "(the affected tiles fell back to the plain step)");
   return TFKT_OK;
 }
 

@@ -22,8 +22,8 @@ KERNELS = ["moments", "step", "fused", "fixup"]
 DIAGS = ["mass_s", "mass_p", "px", "py", "ke", "enstrophy", "qrms_mean", "ey2", "umax",
          "qrms_max"]
 STATUS = {0: "TFKT_OK", 1: "TFKT_EINVAL", 2: "TFKT_ENOMEM", 3: "TFKT_ECUDA", 4: "TFKT_ENAN",
-          5: "TFKT_ESTATE", 6: "TFKT_EIO"}
-EINVAL, ENAN, EIO = 1, 4, 6
+          5: "TFKT_ESTATE", 6: "TFKT_EIO", 7: "TFKT_ETIMEOUT"}
+EINVAL, ENAN, EIO, ETIMEOUT = 1, 4, 6, 7
 
 
 class TfktError(RuntimeError):
@@ -58,7 +58,7 @@ class _Info(ctypes.Structure):
 class LpmOpts(ctypes.Structure):
     """Mirror of tfkt_lpm_opts."""
     _fields_ = [("K", ctypes.c_int32), ("tile", ctypes.c_int32), ("threshold", ctypes.c_float),
-                ("mode", ctypes.c_int32)]
+                ("mode", ctypes.c_int32), ("inject_wait_timeout", ctypes.c_int32)]
 
 
 LPM_NET, LPM_FROZEN = 0, 1
@@ -558,9 +558,10 @@ class Mlp:
 
 
 def lpm_run(solver: Solver, net: Mlp | None, nblocks: int, K: int = 8, tile: int = 32,
-            threshold: float = 0.25, mode: int = LPM_NET) -> int:
-    """Run learned blocks on a solver; returns the number of tiles that fell back."""
-    o = LpmOpts(K, tile, threshold, mode)
+            threshold: float = 0.25, mode: int = LPM_NET, inject_wait_timeout: bool = False) -> int:
+    """Run learned blocks on a solver; returns the number of tiles that fell back.
+    inject_wait_timeout (tests only): the network kernel's waits run out (TFKT_ETIMEOUT)."""
+    o = LpmOpts(K, tile, threshold, mode, int(inject_wait_timeout))
     flagged = ctypes.c_int64()
     _check(lib().tfkt_lpm_run(solver._h, net._h if net is not None else None, ctypes.byref(o),
                               nblocks, ctypes.byref(flagged)), "tfkt_lpm_run")

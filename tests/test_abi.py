@@ -35,6 +35,21 @@ def test_exports_every_declared_symbol(T):
         assert hasattr(lib, n), n
 
 
+def test_every_status_has_a_name(T):
+    """The statuses of include/tfkt.h, the binding's names and tfkt_status_string
+    agree; an unknown code has its own text."""
+    lib = ctypes.CDLL(T.LIB_PATH)
+    lib.tfkt_status_string.restype = ctypes.c_char_p
+    lib.tfkt_status_string.argtypes = [ctypes.c_int]
+    hdr = open(os.path.join(ROOT, "include", "tfkt.h")).read()
+    codes = {int(v): n for n, v in re.findall(r"\b(TFKT_[A-Z]+) = (\d+)", hdr)}
+    assert codes == T.STATUS
+    texts = {lib.tfkt_status_string(c).decode() for c in codes}
+    assert len(texts) == len(codes) and "unknown status" not in texts
+    assert lib.tfkt_status_string(99).decode() == "unknown status"
+    assert T.ETIMEOUT == 7 and codes[T.ETIMEOUT] == "TFKT_ETIMEOUT"
+
+
 def test_lattice_order_is_a_velocity_set(T):
     import numpy as np
     c9, c25 = T.lattice()

@@ -132,6 +132,36 @@ def _pair(T, O, L, nx, ny, wi, steps0, seed, K=4, tile=16, threshold=1e9):
     return o, s, setup
 
 
+def test_network_wait_timeout_is_reported_and_leaves_a_valid_block(T, L):
+    """The network kernel bounds its waits for the tensor cores. With the fault
+    injection it issues no tensor-core work, so every wait runs out after a few
+    polls: tfkt_lpm_run returns TFKT_ETIMEOUT, every tile has fallen back to the
+    plain step's conformation (the state is then bit-identical to a block without
+    the network), and the context stays usable."""
+    from paper_2201_10132_gb300.inputs import perturbation
+    vec, _, _ = _random_net(L, T, 7, out_scale=0.2)
+    pert = perturbation(64, 32, 3, 0.3, 0.05)
+    p = T.Params(64, 32, 6, 3.0, 10.0, 1.0, 0.2, 0.05, 1, 0.0, 0.0, 1, T.FP32)
+    m = T.Mlp(vec)
+    with T.Solver(p, pert) as a, T.Solver(p, pert) as b:
+        a.step(5)
+        b.step(5)
+        with pytest.raises(T.TfktError) as e:
+            T.lpm_run(a, m, 1, K=4, tile=16, threshold=1e9, inject_wait_timeout=True)
+        assert e.value.status == T.ETIMEOUT
+        assert T.lpm_run(b, None, 1, K=4, tile=16, threshold=1e9, mode=T.LPM_FROZEN) == 0
+        assert a.get_info()["step"] == b.get_info()["step"] == 5 + 5
+        fa, fb = a.moments(), b.moments()
+        for k in fa:
+            assert np.array_equal(fa[k], fb[k]), k
+        # the context is not poisoned: a normal block and plain steps follow
+        assert T.lpm_run(a, m, 1, K=4, tile=16, threshold=1e9) == 0
+        a.step(2)
+        d = a.diagnostics()
+        assert all(np.isfinite(v) for v in d.values())
+    m.close()
+
+
 def _compare(o, s, L):
     f = o.fields()
     g = s.moments()
