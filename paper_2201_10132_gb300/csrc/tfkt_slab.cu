@@ -141,6 +141,7 @@ tfkt_status move_rows(Ctx* c, int r0, void* msg, bool pack, bool msg_on_device) 
     }
     cs.total = (uint32_t)first;
     if (((uintptr_t)msg & 15) != 0) return fail(TFKT_EINVAL, "device message not 16-byte aligned");
+    // a grid-stride loop: eight 256-thread blocks per SM of the 152 fill the GPU
     const int blocks = (int)std::min<size_t>((first + 255) / 256, (size_t)152 * 8);
     halo_copy_kernel<<<blocks, 256, 0, c->stream>>>((int4*)c->ws.base, (int4*)msg, cs, pack ? 1 : 0);
     cudaError_t e = cudaGetLastError();
