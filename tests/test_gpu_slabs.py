@@ -113,6 +113,16 @@ def test_slab_rows_and_errors(T):
             s.pack(T.SLAB_HIGH, 0, s.halo_bytes(), True)          # NULL buffer
         with pytest.raises(T.TfktError):
             s.pack(2, 1, s.halo_bytes(), True)                     # unknown side
+        # a device message must start on a 16-byte boundary (checked before any launch)
+        import torch
+        nb = s.halo_bytes()
+        buf = torch.zeros(nb + 16, dtype=torch.uint8, device="cuda")
+        with pytest.raises(T.TfktError) as e:
+            s.pack(T.SLAB_LOW, buf.data_ptr() + 8, nb, True)
+        assert e.value.status == T.EINVAL
+        s.pack(T.SLAB_LOW, buf.data_ptr(), nb, True)               # the context is still usable
+        s.unpack(T.SLAB_HIGH, buf.data_ptr(), nb, True)
+        s.step(1)
     import ctypes
     with T.Solver(p) as s:                                         # not a slab context
         n = ctypes.c_size_t()
