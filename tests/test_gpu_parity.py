@@ -75,7 +75,7 @@ CASES = [
     (64, 32, 6, 3.0, 5.0, 2.0, 0.5, 1, 0.03, 1, 12, 3.1, 1),   # fused, FENE springs
 ]
 FUSED = [c for c in CASES if c[0] % 32 == 0 and c[1] % 8 == 0
-         and c[2] * c[2] <= 127]   # the fused kernel holds at most 127 Q-nodes
+         and c[2] <= 8]   # in FP64 the fused kernel's shared memory holds up to ~57 Q-nodes
 FENE = [c for c in CASES if len(c) > 11 and c[11] > 0]
 STRESS = [c for c in CASES if len(c) > 12 and c[12] == 1]
 
@@ -208,14 +208,19 @@ def test_fp32_within_tolerance(T, oracle_mod, case):
     assert abs(diag["qrms_max"] - f["qrms"].max()) <= 2e-5 * max(f["qrms"].max(), 1e-30)
 
 
-@pytest.mark.parametrize("case", [CASES[1], CASES[7], CASES[9], STRESS[1]])
+@pytest.mark.parametrize("case", [CASES[1], CASES[2], CASES[7], CASES[9], CASES[12], FENE[0],
+                                  FENE[1], STRESS[0], STRESS[1], STRESS[4]])
 def test_fp16_storage_within_tolerance(T, oracle_mod, case):
     """FP16 storage (polymer deviations in half, scaled by a power of two; solvent
     deviations in float; FP32 arithmetic): each stored polymer value is rounded
     to 11 bits every step, so the conformation error after n steps is about
     sqrt(n) 2^-12 times the deviation scale summed over 25 nq terms; allowed:
-    3e-3 of the velocity scale and 3e-3 of each other field's largest magnitude
-    for n <= 25."""
+    3e-3 of the velocity scale, of the conformation and stress tensors' scales
+    (the largest of their three components: the storage error is a fraction of
+    the tensor, not of one component, and an off-diagonal component starting
+    from rest is still small) and of each other field's largest magnitude for
+    n <= 25; each tensor component is also held to 3e-2 of its own largest
+    magnitude."""
     from paper_2201_10132_gb300.inputs import perturbation
     nx, ny, S, R, re, wi, beta, kp, tau2, ic, steps, fb, qe = _case(case)
     pert = perturbation(nx, ny, 7, 0.05, 0.05)
@@ -226,11 +231,16 @@ def test_fp16_storage_within_tolerance(T, oracle_mod, case):
         g = s.moments()
     f = o.fields()
     uscale = max(np.abs(f["ux"]).max(), np.abs(f["uy"]).max())
+    tensors = {"c": ("cxx", "cxy", "cyy"), "th": ("thxx", "thxy", "thyy")}
+    tscale = {k: max(np.abs(f[c]).max() for c in comps) for comps in tensors.values() for k in comps}
     errs = {}
     for k in FIELDS:
-        scale = uscale if k in ("ux", "uy", "vort") else np.abs(f[k]).max()
+        scale = uscale if k in ("ux", "uy", "vort") else tscale.get(k, np.abs(f[k]).max())
         errs[k] = np.abs(g[k] - f[k]).max() / scale
-    assert max(errs.values()) < 3e-3, errs
+        if k in tscale:
+            own = np.abs(g[k] - f[k]).max() / np.abs(f[k]).max()
+            assert own < 3e-2, (k, own)
+    assert max(errs.values()) < 3e-3, " ".join(f"{k}={v:.2e}" for k, v in errs.items())
 
 
 @pytest.mark.parametrize("size,storage,tol", [(4096, "FP32", 2e-5), (4096, "FP16", 3e-3),
