@@ -35,6 +35,23 @@ def test_exports_every_declared_symbol(T):
         assert hasattr(lib, n), n
 
 
+@pytest.mark.parametrize("header", ["tfkt.h", "tfkt_lpm.h"])
+def test_headers_are_plain_c(header, tmp_path):
+    """The boundary's headers compile on their own as strict C99 (no torch or C++
+    types in the interface) and as C++."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "h.c"
+    src.write_text(f'#include "{header}"\n')
+    inc = os.path.join(ROOT, "include")
+    for cmd in (["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only"],
+                ["g++", "-std=c++17", "-Wall", "-Wextra", "-Werror", "-fsyntax-only", "-x", "c++"]):
+        r = subprocess.run(cmd + ["-I", inc, str(src)], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+
+
 def test_every_status_has_a_name(T):
     """The statuses of include/tfkt.h, the binding's names and tfkt_status_string
     agree; an unknown code has its own text."""
